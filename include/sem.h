@@ -1,0 +1,226 @@
+/*
+ * sem.h - C ABI of the GB300 spectral-element Poisson library (libsem.so).
+ *
+ * The library evaluates the matrix-free spectral-element (SEM) Laplace
+ * operator and runs conjugate gradient on it, following Karp et al., "A
+ * High-Fidelity Flow Solver for Unstructured Meshes on FPGAs" (HPC Asia
+ * 2022): Section 3 (Eqs. 1-5), Section 3.2 (Algorithm 1) and Section 5.1
+ * (geometric factors recomputed on the fly, "rematerialisation").
+ *
+ * Problem (Eqs. 1-2, read as -lap(u) = f with u = 0 on the Dirichlet part of
+ * the boundary): E trilinear hexahedra, order N (Np = N + 1 Gauss-Lobatto-
+ * Legendre points per direction), P = Np^3 points per element.
+ *
+ * Conventions shared by every call:
+ *  - Every call returns a sem_status and never aborts; sem_last_error() gives
+ *    a thread-local message for the last non-OK status of the calling thread.
+ *  - Vectors live on the "local" (replicated) layout of Section 3.1,
+ *    u_L = Q u: n = E * P entries indexed ((e * Np + k) * Np + j) * Np + i,
+ *    i fastest (i along xi, j along eta, k along gamma). FP64 vectors are
+ *    double*, FP32 vectors float* (sem_prec says which).
+ *  - Pointers named *_dev are device pointers owned by the caller (for
+ *    example torch tensor data_ptr()); they must be 16-byte aligned and hold
+ *    n elements of the stated precision. The library never frees caller
+ *    memory and keeps no reference to it after the call returns.
+ *  - Pointers named *_host are host pointers read or written synchronously.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream). Calls marked
+ *    "async" only enqueue work on `stream` and do not synchronise the host.
+ *  - A mesh is used on the CUDA device that was current when it was
+ *    created; calls made with another device current return SEM_ERR_ARG.
+ *  - Calls on one mesh from several host threads must be serialised by the
+ *    caller; different meshes are independent.
+ */
+#ifndef SEM_H
+#define SEM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SEM_OK = 0,
+  SEM_ERR_ARG = 1,           /* invalid argument (null pointer, size, precision not prepared, ...) */
+  SEM_ERR_MESH = 2,          /* invalid mesh: bad vertex id, repeated vertex, det J <= 0, non-manifold face */
+  SEM_ERR_OOM = 3,           /* device or host allocation failed */
+  SEM_ERR_CUDA = 4,          /* a CUDA runtime call failed; the message names it */
+  SEM_ERR_NOT_CONVERGED = 5, /* CG stopped at max_iter; the result holds the last iterate */
+  SEM_ERR_BREAKDOWN = 6,     /* CG breakdown: <p, A p, c> <= 0 or a non-finite scalar */
+  SEM_ERR_TIMEOUT = 7,       /* a bounded wait ran out */
+  SEM_ERR_BUSY = 8,          /* resource temporarily unavailable (admission refused / not done yet) */
+  SEM_ERR_UNSUPPORTED = 9    /* e.g. polynomial order outside [1, SEM_MAX_N] */
+} sem_status;
+
+typedef enum { SEM_F64 = 0, SEM_F32 = 1 } sem_prec;
+
+/* Variants of the local operator A_L (Section 5.1):
+ * STORED reads the six geometric factors per point from device memory;
+ * OTF recomputes them per point from 21 per-element trilinear-map coefficients. */
+typedef enum { SEM_AX_STORED = 0, SEM_AX_OTF = 1 } sem_ax_variant;
+
+#define SEM_MAX_N 11 /* polynomial orders 1..11 are compiled in */
+
+/* Flags for sem_mesh_create: which stored-factor arrays to keep on the device.
+ * The per-element coefficients for the OTF variant are always kept (FP64 and FP32). */
+#define SEM_MESH_F64_STORED 1u /* G in FP64: 48 bytes per local point */
+#define SEM_MESH_F32_STORED 2u /* G in FP32: 24 bytes per local point */
+
+typedef struct sem_mesh_s* sem_mesh;
+typedef struct sem_cg_s* sem_cg;
+
+typedef struct {
+  int N;           /* polynomial order */
+  int Np;          /* N + 1 */
+  int64_t E;       /* elements */
+  int64_t n_local; /* E * Np^3 local (replicated) points */
+  int64_t n_glob;  /* distinct global nodes */
+  int64_t n_seg;   /* gather-scatter segments (global nodes on element boundaries) */
+  int64_t n_gs;    /* local points on element boundaries: E((N+1)^3 - (N-1)^3), Eq. 9 */
+  unsigned flags;  /* SEM_MESH_* flags the mesh was created with */
+  int device;      /* CUDA device ordinal */
+  size_t device_bytes; /* device memory held by the mesh */
+} sem_mesh_info_t;
+
+/* Create a mesh (Section 3: E hexahedra, GLL points of order N).
+ *  vert_xyz_host    [num_vertices][3] FP64 vertex coordinates.
+ *  elem_verts_host  [E][8] vertex ids; local vertex a + 2b + 4c (a, b, c in
+ *                   {0,1}) sits at reference corner (2a-1, 2b-1, 2c-1), a along
+ *                   xi, b along eta, c along gamma. The map must be orientation
+ *                   preserving (det J > 0 at every GLL point) or SEM_ERR_MESH.
+ *  dirichlet_vertex_flags_host  NULL: every boundary face (a face owned by one
+ *                   element) is Dirichlet. Otherwise [num_vertices] bytes; a
+ *                   boundary face is Dirichlet iff its four vertices are flagged.
+ * Global numbering (Section 3.1's Q): two local points are one global node iff
+ * they sit on the same vertex, edge or face at the same position; global ids
+ * follow the first occurrence in the local order. The call validates the mesh
+ * on the host, builds numbering, gather-scatter segments and mask, copies the
+ * per-element data to the device, computes geometric factors (kernel) and
+ * synchronises `stream`. The host arrays are copied; the caller keeps them.
+ * Limits: 1 <= N <= SEM_MAX_N, E >= 1, E * (N+1)^3 < 2^31. */
+sem_status sem_mesh_create(int N, int64_t num_vertices, const double* vert_xyz_host, int64_t E,
+                           const int64_t* elem_verts_host, const uint8_t* dirichlet_vertex_flags_host,
+                           unsigned flags, void* stream, sem_mesh* out);
+sem_status sem_mesh_destroy(sem_mesh mesh); /* NULL is a no-op; synchronises the device */
+/* Host-only: the numbering and mask sem_mesh_create would build (Section 3.1's Q), without
+ * touching a GPU. glo_num_host [E*(N+1)^3] int64, mask_host [E*(N+1)^3] uint8 (either may be
+ * NULL), n_glob_host receives the number of global nodes. Same validation as sem_mesh_create
+ * except for the geometry (det J) check, which needs the device. */
+sem_status sem_mesh_numbering(int N, int64_t num_vertices, int64_t E, const int64_t* elem_verts_host,
+                              const uint8_t* dirichlet_vertex_flags_host, int64_t* glo_num_host, uint8_t* mask_host,
+                              int64_t* n_glob_host);
+
+sem_status sem_mesh_get_info(sem_mesh mesh, sem_mesh_info_t* info_host);
+
+/* Test hooks: copy the numbering (int64 [n_local]), the Dirichlet mask (uint8
+ * [n_local], 1 = zeroed) and the gather-scatter segments to host buffers.
+ * Segments: global nodes on element boundaries in ascending global id;
+ * seg_off [n_seg + 1] int32 offsets into seg_idx [n_gs] int32 local indices
+ * (ascending within a segment); seg_mask [n_seg] uint8. Any pointer may be NULL. */
+sem_status sem_mesh_get_glo_num(sem_mesh mesh, int64_t* glo_num_host);
+sem_status sem_mesh_get_mask(sem_mesh mesh, uint8_t* mask_host);
+sem_status sem_mesh_get_segments(sem_mesh mesh, int32_t* seg_off_host, int32_t* seg_idx_host,
+                                 uint8_t* seg_mask_host);
+
+/* Physical coordinates of the local points (trilinear map, Section 5.1):
+ * xyz_dev [3][n_local] FP64 (all x, then all y, then all z). Async. */
+sem_status sem_mesh_coords(sem_mesh mesh, double* xyz_dev, void* stream);
+
+/* The six geometric factors G = w_i w_j w_k |det J| J^-1 J^-T of Eq. 4
+ * (Section 4.2), G_dev [E][6][P] in the order G11, G12, G13, G22, G23, G33,
+ * and the mass B = w_i w_j w_k |det J| in B_dev [E][P] (either may be NULL).
+ * Computed from the element coefficients in FP64 (prec F64) or FP64 rounded
+ * to FP32 (prec F32). Async. */
+sem_status sem_mesh_geometry(sem_mesh mesh, sem_prec prec, void* G_dev, void* B_dev, void* stream);
+
+/* Q (Section 3.1): u_local[i] = u_glob[glo_num[i]]; u_glob_dev has n_glob entries. Async. */
+sem_status sem_scatter(sem_mesh mesh, sem_prec prec, const void* u_glob_dev, void* u_local_dev, void* stream);
+
+/* Ax (Section 3.1): w = A_L u (Eq. 4, element by element); with assemble != 0
+ * also the gather-scatter QQ^T and the Dirichlet mask (Algorithm 1 steps 6-7).
+ * u and w must not overlap. STORED needs the factors of that precision
+ * (SEM_MESH_F64_STORED / SEM_MESH_F32_STORED) else SEM_ERR_ARG. Async. */
+sem_status sem_ax(sem_mesh mesh, sem_ax_variant variant, sem_prec prec, const void* u_dev, void* w_dev,
+                  int assemble, void* stream);
+
+/* Gather-scatter QQ^T in place (Eq. 5, Section 4.3): every local copy of a
+ * global node receives the sum of all copies, added left to right in
+ * ascending local index (so the result is bit-reproducible); with
+ * apply_mask != 0 Dirichlet copies are then set to 0. Async. */
+sem_status sem_dssum(sem_mesh mesh, sem_prec prec, void* u_dev, int apply_mask, void* stream);
+
+/* Weighted inner product <a, b, c> = sum_i a_i b_i c_i with c_i = 1 /
+ * multiplicity (Algorithm 1), accumulated in FP64; writes one double to
+ * result_dev. Deterministic for a given mesh. Async. */
+sem_status sem_glsc3(sem_mesh mesh, sem_prec prec, const void* a_dev, const void* b_dev, double* result_dev,
+                     void* stream);
+
+/* Jacobi preconditioner: minv_dev = 1 / diag(QQ^T A_L) on unmasked points, 0 on
+ * Dirichlet points (exact diagonal of the assembled operator). Async. */
+sem_status sem_jacobi(sem_mesh mesh, sem_prec prec, void* minv_dev, void* stream);
+
+/* Right-hand side for the manufactured solution u = sin(a pi x) sin(b pi y)
+ * sin(c pi z): rhs = mask(QQ^T (B f)) with f = (a^2+b^2+c^2) pi^2 u evaluated
+ * at the mapped GLL points (Eq. 2's right side by GLL quadrature). Async. */
+sem_status sem_rhs_sine(sem_mesh mesh, int a, int b, int c, sem_prec prec, void* rhs_dev, void* stream);
+
+/* ---- Conjugate gradient (Algorithm 1 + Jacobi z = M^-1 r) ---- */
+
+typedef struct {
+  double rtol;        /* stop when sqrt(<r,r,c> / <b,b,c>) <= rtol (checked after the r update) */
+  int max_iter;       /* FP64 CG: iteration limit; mixed: limit on inner iterations in total */
+  int precond;        /* 0: none, 1: Jacobi */
+  int variant;        /* sem_ax_variant of the FP64 operator */
+  int mixed;          /* 0: FP64 CG; 1: FP32 inner CG + FP64 iterative refinement */
+  int inner_variant;  /* sem_ax_variant of the FP32 inner operator (mixed) */
+  double inner_rtol;  /* relative tolerance of each inner solve (mixed) */
+  int max_outer;      /* refinement steps limit (mixed) */
+  int check_every;    /* iterations between host reads of the device convergence flag (>= 1) */
+  int use_graph;      /* 1: replay check_every iterations as one captured CUDA graph */
+} sem_cg_opts;
+
+typedef struct {
+  int iters;       /* operator applications inside the CG loop(s) */
+  int outer_iters; /* refinement steps (mixed), else 0 */
+  double rel_res;  /* final sqrt(<r,r,c> / <b,b,c>) as tracked by the solver */
+  double time_ms;  /* wall time of the solve on the host clock */
+  int status;      /* sem_status of the solve */
+} sem_cg_result;
+
+/* Fill opts with defaults: rtol 1e-10, max_iter 100000, Jacobi, STORED FP64,
+ * not mixed, inner OTF with inner_rtol 1e-5, max_outer 50, check_every 50, graph on. */
+sem_status sem_cg_default_opts(sem_cg_opts* opts_host);
+
+/* Solve A x = b to rtol. b_dev, x_dev: FP64 [n_local]; x_dev holds x0 on entry
+ * and the solution on return (also on NOT_CONVERGED / BREAKDOWN). b must be
+ * assembled and masked (e.g. from sem_rhs_sine). Blocks the host until done;
+ * allocates its work vectors for the duration of the call. */
+sem_status sem_cg_solve(sem_mesh mesh, const double* b_dev, double* x_dev, const sem_cg_opts* opts,
+                        sem_cg_result* result_host, void* stream);
+
+/* Stateful FP64 CG for step-wise use (benchmarks, servers):
+ *  sem_cg_create   allocates work vectors and device scalars (FP64, non-mixed opts only);
+ *  sem_cg_start    r = b - A x0, z, rho; async;
+ *  sem_cg_iterate  enqueues k iterations (a captured graph when opts.use_graph);
+ *                  iterations after convergence are no-ops; async;
+ *  sem_cg_query    synchronises `stream` and reports iterations, residual, status;
+ *  sem_cg_destroy  frees the handle. x_dev passed to sem_cg_start is updated in place
+ *  and must stay valid until the last sem_cg_iterate has completed. */
+sem_status sem_cg_create(sem_mesh mesh, const sem_cg_opts* opts, sem_cg* out);
+sem_status sem_cg_start(sem_cg cg, const double* b_dev, double* x_dev, void* stream);
+sem_status sem_cg_iterate(sem_cg cg, int k, void* stream);
+sem_status sem_cg_query(sem_cg cg, sem_cg_result* result_host, void* stream);
+sem_status sem_cg_destroy(sem_cg cg);
+
+/* Number of kernel launches the library enqueued since load (all entry points). */
+uint64_t sem_launch_count(void);
+
+const char* sem_last_error(void);
+const char* sem_status_string(sem_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SEM_H */

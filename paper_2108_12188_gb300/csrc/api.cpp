@@ -1,0 +1,779 @@
+// C ABI of libsem: mesh lifecycle, operator entry points and the conjugate-gradient
+// drivers (Algorithm 1 with Jacobi, FP64; and FP32-inner / FP64-outer iterative refinement).
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <memory>
+
+#include "sem_internal.h"
+
+namespace sem {
+
+namespace {
+thread_local std::string t_last_error;
+thread_local bool t_capturing = false;
+std::atomic<uint64_t> g_launches{0};
+}  // namespace
+
+sem_status fail(sem_status s, const std::string& msg) {
+  t_last_error = msg;
+  return s;
+}
+
+sem_status cuda_fail(cudaError_t e, const char* what) {
+  t_last_error = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+  if (e == cudaErrorMemoryAllocation) return SEM_ERR_OOM;
+  return SEM_ERR_CUDA;
+}
+
+void count_launch(int k) {
+  if (!t_capturing) g_launches.fetch_add(static_cast<uint64_t>(k), std::memory_order_relaxed);
+}
+
+namespace {
+
+template <typename T>
+sem_status dmalloc(T** p, size_t count, size_t* acc) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  const size_t bytes = count * sizeof(T);
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(e == cudaErrorMemoryAllocation ? SEM_ERR_OOM : SEM_ERR_CUDA,
+                "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e));
+  }
+  if (acc) *acc += bytes;
+  return SEM_OK;
+}
+
+template <typename T>
+void dfree(T*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+#define SEM_TRY(expr)                 \
+  do {                                \
+    sem_status _s = (expr);           \
+    if (_s != SEM_OK) return _s;      \
+  } while (0)
+
+sem_status check_mesh(sem_mesh m) {
+  if (!m) return fail(SEM_ERR_ARG, "null mesh");
+  int dev = -1;
+  SEM_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev != m->device) return fail(SEM_ERR_ARG, "the mesh belongs to another CUDA device than the current one");
+  return SEM_OK;
+}
+
+sem_status check_ptr(const void* p, const char* name) {
+  if (!p) return fail(SEM_ERR_ARG, std::string(name) + " is null");
+  if (reinterpret_cast<uintptr_t>(p) % 16 != 0) return fail(SEM_ERR_ARG, std::string(name) + " is not 16-byte aligned");
+  return SEM_OK;
+}
+
+sem_status check_prec(int prec) {
+  if (prec != SEM_F64 && prec != SEM_F32) return fail(SEM_ERR_ARG, "precision must be SEM_F64 or SEM_F32");
+  return SEM_OK;
+}
+
+void free_mesh(sem_mesh m) {
+  dfree(m->coef64);
+  dfree(m->coef32);
+  dfree(m->G64);
+  dfree(m->G32);
+  dfree(m->seg_off);
+  dfree(m->seg_idx);
+  dfree(m->seg_mask);
+  dfree(m->mult);
+  dfree(m->minv64);
+  dfree(m->minv32);
+  dfree(m->ctab);
+  dfree(m->partials);
+  dfree(m->ticket);
+}
+
+sem_status launch_ax_any(sem_mesh m, sem_prec prec, sem_ax_variant v, bool cg, AxLaunch a, cudaStream_t s) {
+  a.E = m->E;
+  a.coef = prec == SEM_F64 ? static_cast<const void*>(m->coef64) : static_cast<const void*>(m->coef32);
+  a.G = prec == SEM_F64 ? static_cast<const void*>(m->G64) : static_cast<const void*>(m->G32);
+  if (v == SEM_AX_STORED && !a.G)
+    return fail(SEM_ERR_ARG, "stored factors of this precision were not requested at mesh creation");
+  return prec == SEM_F64 ? launch_ax_f64(m->N, v, cg, a, s) : launch_ax_f32(m->N, v, cg, a, s);
+}
+
+// Jacobi inverse diagonal, built once per mesh in FP64 (and rounded to FP32).
+sem_status ensure_jacobi(sem_mesh m, cudaStream_t s) {
+  if (m->minv64) return SEM_OK;
+  double* d = nullptr;
+  SEM_TRY(dmalloc(&d, m->n, nullptr));
+  sem_status st = SEM_OK;
+  size_t bytes = 0;
+  if ((st = dmalloc(&m->minv64, m->n, &bytes)) == SEM_OK && (st = dmalloc(&m->minv32, m->n, &bytes)) == SEM_OK &&
+      (st = launch_local_diag(m->N, m->E, m->coef64, d, s)) == SEM_OK &&
+      (st = launch_invert(m->n, d, m->minv64, m->minv32, s)) == SEM_OK &&
+      (st = launch_dssum_invert(m->n_seg, m->seg_off, m->seg_idx, m->seg_mask, d, m->minv64, m->minv32, s)) ==
+          SEM_OK) {
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = cuda_fail(e, "cudaStreamSynchronize (Jacobi set-up)");
+  }
+  cudaFree(d);
+  if (st != SEM_OK) {
+    dfree(m->minv64);
+    dfree(m->minv32);
+    return st;
+  }
+  m->device_bytes += bytes;
+  return SEM_OK;
+}
+
+}  // namespace
+}  // namespace sem
+
+using namespace sem;
+
+// ---------------------------------------------------------------------------
+// mesh
+// ---------------------------------------------------------------------------
+
+extern "C" sem_status sem_mesh_create(int N, int64_t nv, const double* vert_xyz, int64_t E, const int64_t* elem_verts,
+                                      const uint8_t* dflags, unsigned flags, void* stream, sem_mesh* out) {
+  if (!out) return fail(SEM_ERR_ARG, "out is null");
+  *out = nullptr;
+  if (!vert_xyz || !elem_verts) return fail(SEM_ERR_ARG, "vert_xyz and elem_verts must be given");
+  if (flags & ~(SEM_MESH_F64_STORED | SEM_MESH_F32_STORED)) return fail(SEM_ERR_ARG, "unknown mesh flags");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Topology T;
+  SEM_TRY(build_topology(N, nv, E, elem_verts, dflags, T));
+  for (int64_t v = 0; v < nv; ++v)
+    for (int c = 0; c < 3; ++c)
+      if (!std::isfinite(vert_xyz[3 * v + c])) return fail(SEM_ERR_MESH, "non-finite vertex coordinate");
+
+  auto m = std::make_unique<sem_mesh_s>();
+  SEM_CUDA_TRY(cudaGetDevice(&m->device));
+  m->N = N;
+  m->Np = N + 1;
+  m->flags = flags;
+  m->E = E;
+  m->n = T.n;
+  m->n_glob = T.n_glob;
+  m->n_seg = static_cast<int64_t>(T.seg_mask.size());
+  m->n_gs = static_cast<int64_t>(T.seg_idx.size());
+  const int64_t P = static_cast<int64_t>(m->Np) * m->Np * m->Np;
+
+  std::vector<double> X(static_cast<size_t>(E) * 24);
+  for (int64_t e = 0; e < E; ++e)
+    for (int v = 0; v < 8; ++v)
+      for (int c = 0; c < 3; ++c) X[e * 24 + v * 3 + c] = vert_xyz[3 * elem_verts[e * 8 + v] + c];
+  std::vector<double> ctab(256, 0.0);
+  for (int k = 1; k < 256; ++k) ctab[k] = 1.0 / k;
+
+  double* Xd = nullptr;
+  int* bad = nullptr;
+  auto cleanup = [&](sem_status st) {
+    if (Xd) cudaFree(Xd);
+    if (bad) cudaFree(bad);
+    if (st != SEM_OK) free_mesh(m.get());
+    return st;
+  };
+  size_t& acc = m->device_bytes;
+  sem_status st = SEM_OK;
+#define SEM_STEP(expr)               \
+  do {                               \
+    st = (expr);                     \
+    if (st != SEM_OK) return cleanup(st); \
+  } while (0)
+#define SEM_CSTEP(expr)                                  \
+  do {                                                   \
+    cudaError_t _e = (expr);                             \
+    if (_e != cudaSuccess) return cleanup(cuda_fail(_e, #expr)); \
+  } while (0)
+  SEM_STEP(dmalloc(&Xd, X.size(), nullptr));
+  SEM_STEP(dmalloc(&bad, 1, nullptr));
+  SEM_STEP(dmalloc(&m->coef64, static_cast<size_t>(E) * 24, &acc));
+  SEM_STEP(dmalloc(&m->coef32, static_cast<size_t>(E) * 24, &acc));
+  if (flags & SEM_MESH_F64_STORED) SEM_STEP(dmalloc(&m->G64, static_cast<size_t>(E * 6 * P), &acc));
+  if (flags & SEM_MESH_F32_STORED) SEM_STEP(dmalloc(&m->G32, static_cast<size_t>(E * 6 * P), &acc));
+  SEM_STEP(dmalloc(&m->seg_off, T.seg_off.size(), &acc));
+  SEM_STEP(dmalloc(&m->seg_idx, T.seg_idx.size(), &acc));
+  SEM_STEP(dmalloc(&m->seg_mask, T.seg_mask.size(), &acc));
+  SEM_STEP(dmalloc(&m->mult, T.mult.size(), &acc));
+  SEM_STEP(dmalloc(&m->ctab, 256, &acc));
+  SEM_STEP(dmalloc(&m->partials, kRedMax, &acc));
+  SEM_STEP(dmalloc(&m->ticket, 1, &acc));
+  SEM_CSTEP(cudaMemcpyAsync(Xd, X.data(), X.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+  SEM_CSTEP(cudaMemcpyAsync(m->seg_off, T.seg_off.data(), T.seg_off.size() * 4, cudaMemcpyHostToDevice, s));
+  SEM_CSTEP(cudaMemcpyAsync(m->seg_idx, T.seg_idx.data(), T.seg_idx.size() * 4, cudaMemcpyHostToDevice, s));
+  SEM_CSTEP(cudaMemcpyAsync(m->seg_mask, T.seg_mask.data(), T.seg_mask.size(), cudaMemcpyHostToDevice, s));
+  SEM_CSTEP(cudaMemcpyAsync(m->mult, T.mult.data(), T.mult.size(), cudaMemcpyHostToDevice, s));
+  SEM_CSTEP(cudaMemcpyAsync(m->ctab, ctab.data(), 256 * sizeof(double), cudaMemcpyHostToDevice, s));
+  SEM_CSTEP(cudaMemsetAsync(m->ticket, 0, sizeof(unsigned int), s));
+  SEM_CSTEP(cudaMemsetAsync(bad, 0, sizeof(int), s));
+  SEM_STEP(launch_coefficients(E, Xd, m->coef64, m->coef32, s));
+  // geometric factors (and the det J > 0 check at every GLL point)
+  SEM_STEP(launch_geometry(N, E, m->coef64, m->G64, m->G32, nullptr, nullptr, bad, s));
+  int bad_h = 0;
+  SEM_CSTEP(cudaMemcpyAsync(&bad_h, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+  SEM_CSTEP(cudaStreamSynchronize(s));
+  if (bad_h) return cleanup(fail(SEM_ERR_MESH, "det J <= 0 (inverted or degenerate element)"));
+#undef SEM_STEP
+#undef SEM_CSTEP
+  cleanup(SEM_OK);
+  m->glo = std::move(T.glo);
+  m->mask = std::move(T.mask);
+  *out = m.release();
+  return SEM_OK;
+}
+
+extern "C" sem_status sem_mesh_numbering(int N, int64_t nv, int64_t E, const int64_t* elem_verts,
+                                         const uint8_t* dflags, int64_t* glo_out, uint8_t* mask_out,
+                                         int64_t* n_glob_out) {
+  Topology T;
+  SEM_TRY(build_topology(N, nv, E, elem_verts, dflags, T));
+  if (glo_out) std::memcpy(glo_out, T.glo.data(), T.glo.size() * sizeof(int64_t));
+  if (mask_out) std::memcpy(mask_out, T.mask.data(), T.mask.size());
+  if (n_glob_out) *n_glob_out = T.n_glob;
+  return SEM_OK;
+}
+
+extern "C" sem_status sem_mesh_destroy(sem_mesh m) {
+  if (!m) return SEM_OK;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  if (cur != m->device) cudaSetDevice(m->device);
+  cudaDeviceSynchronize();
+  free_mesh(m);
+  if (cur != m->device) cudaSetDevice(cur);
+  delete m;
+  return SEM_OK;
+}
+
+extern "C" sem_status sem_mesh_get_info(sem_mesh m, sem_mesh_info_t* info) {
+  if (!m || !info) return fail(SEM_ERR_ARG, "null argument");
+  info->N = m->N;
+  info->Np = m->Np;
+  info->E = m->E;
+  info->n_local = m->n;
+  info->n_glob = m->n_glob;
+  info->n_seg = m->n_seg;
+  info->n_gs = m->n_gs;
+  info->flags = m->flags;
+  info->device = m->device;
+  info->device_bytes = m->device_bytes;
+  return SEM_OK;
+}
+
+extern "C" sem_status sem_mesh_get_glo_num(sem_mesh m, int64_t* out) {
+  if (!m || !out) return fail(SEM_ERR_ARG, "null argument");
+  std::memcpy(out, m->glo.data(), m->glo.size() * sizeof(int64_t));
+  return SEM_OK;
+}
+
+extern "C" sem_status sem_mesh_get_mask(sem_mesh m, uint8_t* out) {
+  if (!m || !out) return fail(SEM_ERR_ARG, "null argument");
+  std::memcpy(out, m->mask.data(), m->mask.size());
+  return SEM_OK;
+}
+
+extern "C" sem_status sem_mesh_get_segments(sem_mesh m, int32_t* off, int32_t* idx, uint8_t* smask) {
+  SEM_TRY(check_mesh(m));
+  if (off) SEM_CUDA_TRY(cudaMemcpy(off, m->seg_off, (m->n_seg + 1) * 4, cudaMemcpyDeviceToHost));
+  if (idx) SEM_CUDA_TRY(cudaMemcpy(idx, m->seg_idx, m->n_gs * 4, cudaMemcpyDeviceToHost));
+  if (smask) SEM_CUDA_TRY(cudaMemcpy(smask, m->seg_mask, m->n_seg, cudaMemcpyDeviceToHost));
+  return SEM_OK;
+}
+
+extern "C" sem_status sem_mesh_coords(sem_mesh m, double* xyz, void* stream) {
+  SEM_TRY(check_mesh(m));
+  SEM_TRY(check_ptr(xyz, "xyz_dev"));
+  return launch_coords(m->N, m->E, m->coef64, xyz, m->n, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" sem_status sem_mesh_geometry(sem_mesh m, sem_prec prec, void* G, void* B, void* stream) {
+  SEM_TRY(check_mesh(m));
+  SEM_TRY(check_prec(prec));
+  if (G) SEM_TRY(check_ptr(G, "G_dev"));
+  if (B) SEM_TRY(check_ptr(B, "B_dev"));
+  if (!G && !B) return SEM_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int* bad = nullptr;
+  SEM_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&bad), sizeof(int), s));
+  sem_status st = launch_geometry(m->N, m->E, m->coef64, prec == SEM_F64 ? static_cast<double*>(G) : nullptr,
+                                  prec == SEM_F32 ? static_cast<float*>(G) : nullptr,
+                                  prec == SEM_F64 ? static_cast<double*>(B) : nullptr,
+                                  prec == SEM_F32 ? static_cast<float*>(B) : nullptr, bad, s);
+  cudaFreeAsync(bad, s);
+  return st;
+}
+
+extern "C" sem_status sem_scatter(sem_mesh m, sem_prec prec, const void* ug, void* ul, void* stream) {
+  SEM_TRY(check_mesh(m));
+  SEM_TRY(check_prec(prec));
+  SEM_TRY(check_ptr(ug, "u_glob_dev"));
+  SEM_TRY(check_ptr(ul, "u_local_dev"));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::vector<int32_t> g32(m->glo.begin(), m->glo.end());
+  int32_t* gd = nullptr;
+  SEM_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&gd), g32.size() * 4, s));
+  sem_status st = SEM_OK;
+  cudaError_t e = cudaMemcpyAsync(gd, g32.data(), g32.size() * 4, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) st = cuda_fail(e, "cudaMemcpyAsync (numbering)");
+  if (st == SEM_OK) st = launch_scatter(prec, m->n, gd, ug, ul, s);
+  // the host copy must outlive the transfer
+  e = cudaStreamSynchronize(s);
+  if (st == SEM_OK && e != cudaSuccess) st = cuda_fail(e, "cudaStreamSynchronize");
+  cudaFreeAsync(gd, s);
+  return st;
+}
+
+extern "C" sem_status sem_ax(sem_mesh m, sem_ax_variant v, sem_prec prec, const void* u, void* w, int assemble,
+                             void* stream) {
+  SEM_TRY(check_mesh(m));
+  SEM_TRY(check_prec(prec));
+  if (v != SEM_AX_STORED && v != SEM_AX_OTF) return fail(SEM_ERR_ARG, "unknown Ax variant");
+  SEM_TRY(check_ptr(u, "u_dev"));
+  SEM_TRY(check_ptr(w, "w_dev"));
+  if (u == w) return fail(SEM_ERR_ARG, "u and w must not overlap");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  AxLaunch a{};
+  a.u = u;
+  a.w = w;
+  SEM_TRY(launch_ax_any(m, prec, v, false, a, s));
+  if (assemble) SEM_TRY(launch_dssum(prec, m->n_seg, m->seg_off, m->seg_idx, m->seg_mask, w, 1, s));
+  return SEM_OK;
+}
+
+extern "C" sem_status sem_dssum(sem_mesh m, sem_prec prec, void* u, int apply_mask, void* stream) {
+  SEM_TRY(check_mesh(m));
+  SEM_TRY(check_prec(prec));
+  SEM_TRY(check_ptr(u, "u_dev"));
+  return launch_dssum(prec, m->n_seg, m->seg_off, m->seg_idx, m->seg_mask, u, apply_mask,
+                      static_cast<cudaStream_t>(stream));
+}
+
+extern "C" sem_status sem_glsc3(sem_mesh m, sem_prec prec, const void* a, const void* b, double* result,
+                                void* stream) {
+  SEM_TRY(check_mesh(m));
+  SEM_TRY(check_prec(prec));
+  SEM_TRY(check_ptr(a, "a_dev"));
+  SEM_TRY(check_ptr(b, "b_dev"));
+  if (!result) return fail(SEM_ERR_ARG, "result_dev is null");
+  return launch_glsc3(prec, m->n, a, b, m->mult, m->ctab, m->partials, m->ticket, result,
+                      static_cast<cudaStream_t>(stream));
+}
+
+extern "C" sem_status sem_jacobi(sem_mesh m, sem_prec prec, void* minv, void* stream) {
+  SEM_TRY(check_mesh(m));
+  SEM_TRY(check_prec(prec));
+  SEM_TRY(check_ptr(minv, "minv_dev"));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  SEM_TRY(ensure_jacobi(m, s));
+  const size_t bytes = m->n * (prec == SEM_F64 ? sizeof(double) : sizeof(float));
+  SEM_CUDA_TRY(cudaMemcpyAsync(minv, prec == SEM_F64 ? static_cast<void*>(m->minv64) : static_cast<void*>(m->minv32),
+                               bytes, cudaMemcpyDeviceToDevice, s));
+  return SEM_OK;
+}
+
+extern "C" sem_status sem_rhs_sine(sem_mesh m, int a, int b, int c, sem_prec prec, void* rhs, void* stream) {
+  SEM_TRY(check_mesh(m));
+  SEM_TRY(check_prec(prec));
+  SEM_TRY(check_ptr(rhs, "rhs_dev"));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  double* tmp = static_cast<double*>(rhs);
+  if (prec == SEM_F32) SEM_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&tmp), m->n * sizeof(double), s));
+  sem_status st = launch_rhs_local(m->N, m->E, m->coef64, a, b, c, tmp, s);
+  if (st == SEM_OK) st = launch_dssum(SEM_F64, m->n_seg, m->seg_off, m->seg_idx, m->seg_mask, tmp, 1, s);
+  if (prec == SEM_F32) {
+    if (st == SEM_OK) st = launch_cast(m->n, tmp, static_cast<float*>(rhs), s);
+    cudaFreeAsync(tmp, s);
+  }
+  return st;
+}
+
+// ---------------------------------------------------------------------------
+// conjugate gradient
+// ---------------------------------------------------------------------------
+
+struct sem_cg_s {
+  sem_mesh m = nullptr;
+  sem_prec prec = SEM_F64;
+  sem_ax_variant variant = SEM_AX_STORED;
+  int precond = 1, max_iter = 0, use_graph = 1;
+  double rtol = 0;
+  void *r = nullptr, *z = nullptr, *p = nullptr, *w = nullptr;
+  void* x = nullptr;
+  const void* b = nullptr;
+  CgScalars* st = nullptr;
+  CgScalars* st_host = nullptr;  // pinned
+  double *ax_part = nullptr, *gs_part = nullptr, *upd_part = nullptr, *init_part = nullptr;
+  int ax_blocks = 0;
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int exec_k = 0;
+  void* exec_x = nullptr;
+};
+
+namespace sem {
+namespace {
+
+const void* minv_of(sem_cg c) {
+  if (!c->precond) return nullptr;
+  return c->prec == SEM_F64 ? static_cast<const void*>(c->m->minv64) : static_cast<const void*>(c->m->minv32);
+}
+
+void cg_free(sem_cg c) {
+  if (c->exec) cudaGraphExecDestroy(c->exec);
+  if (c->cap) cudaStreamDestroy(c->cap);
+  for (void* q : {c->r, c->z, c->p, c->w}) if (q) cudaFree(q);
+  for (double* q : {c->ax_part, c->gs_part, c->upd_part, c->init_part}) if (q) cudaFree(q);
+  if (c->st) cudaFree(c->st);
+  if (c->st_host) cudaFreeHost(c->st_host);
+  delete c;
+}
+
+sem_status cg_alloc(sem_mesh m, sem_prec prec, sem_ax_variant v, int precond, double rtol, int max_iter, int use_graph,
+                    sem_cg* out) {
+  *out = nullptr;
+  if (v == SEM_AX_STORED && !(prec == SEM_F64 ? m->G64 != nullptr : m->G32 != nullptr))
+    return fail(SEM_ERR_ARG, "stored factors of this precision were not requested at mesh creation");
+  sem_cg c = new sem_cg_s();
+  c->m = m;
+  c->prec = prec;
+  c->variant = v;
+  c->precond = precond;
+  c->rtol = rtol;
+  c->max_iter = max_iter;
+  c->use_graph = use_graph;
+  const size_t es = prec == SEM_F64 ? sizeof(double) : sizeof(float);
+  sem_status st = SEM_OK;
+  for (void** q : {&c->r, &c->z, &c->p, &c->w}) {
+    cudaError_t e = cudaMalloc(q, m->n * es);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      st = fail(SEM_ERR_OOM, "cudaMalloc of CG work vectors failed");
+      break;
+    }
+  }
+  if (st == SEM_OK) st = dmalloc(&c->ax_part, kRedMax, nullptr);
+  if (st == SEM_OK) st = dmalloc(&c->gs_part, kRedMax, nullptr);
+  if (st == SEM_OK) st = dmalloc(&c->upd_part, 2 * kRedMax, nullptr);
+  if (st == SEM_OK) st = dmalloc(&c->init_part, 3 * kRedMax, nullptr);
+  if (st == SEM_OK) st = dmalloc(&c->st, 1, nullptr);
+  if (st == SEM_OK) {
+    cudaError_t e = cudaMallocHost(reinterpret_cast<void**>(&c->st_host), sizeof(CgScalars));
+    if (e != cudaSuccess) st = cuda_fail(e, "cudaMallocHost");
+  }
+  if (st == SEM_OK) {
+    cudaError_t e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) st = cuda_fail(e, "cudaStreamCreate");
+  }
+  if (st != SEM_OK) {
+    cg_free(c);
+    return st;
+  }
+  *out = c;
+  return SEM_OK;
+}
+
+// Host-side state reset + r0 = b - A x0, z0, rho0 (device).
+sem_status cg_start(sem_cg c, const void* b, void* x, bool x0_is_zero, cudaStream_t s) {
+  sem_mesh m = c->m;
+  if (c->precond) SEM_TRY(ensure_jacobi(m, s));
+  CgScalars init{};
+  init.rtol2 = c->rtol * c->rtol;
+  init.max_iter = c->max_iter;
+  *c->st_host = init;
+  SEM_CUDA_TRY(cudaMemcpyAsync(c->st, c->st_host, sizeof(CgScalars), cudaMemcpyHostToDevice, s));
+  c->b = b;
+  c->x = x;
+  const void* ax0 = nullptr;
+  if (!x0_is_zero) {
+    AxLaunch a{};
+    a.u = x;
+    a.w = c->w;
+    SEM_TRY(launch_ax_any(m, c->prec, c->variant, false, a, s));
+    SEM_TRY(launch_dssum(c->prec, m->n_seg, m->seg_off, m->seg_idx, m->seg_mask, c->w, 1, s));
+    ax0 = c->w;
+  }
+  SEM_TRY(launch_cg_init(c->prec, m->n, b, ax0, c->r, c->z, c->p, minv_of(c), m->mult, m->ctab, c->st, c->init_part,
+                         s));
+  // the host struct is reused by query: make sure the copy above has been consumed
+  SEM_CUDA_TRY(cudaStreamSynchronize(s));
+  return SEM_OK;
+}
+
+// One iteration of Algorithm 1: [p = z + beta p; w = A_L p; interior <p,w>] -> [QQ^T, mask,
+// boundary <p,w>, alpha] -> [x, r, z updates, <r,z,c>, <r,r,c>, beta, stop test].
+sem_status cg_enqueue_iteration(sem_cg c, cudaStream_t s) {
+  sem_mesh m = c->m;
+  AxLaunch a{};
+  a.w = c->w;
+  a.z = c->z;
+  a.p = c->p;
+  a.st = c->st;
+  a.partials = c->ax_part;
+  a.grid_out = &c->ax_blocks;
+  SEM_TRY(launch_ax_any(m, c->prec, c->variant, true, a, s));
+  SEM_TRY(launch_dssum_cg(c->prec, m->n_seg, m->seg_off, m->seg_idx, m->seg_mask, c->w, c->p, c->st, c->ax_part,
+                          c->ax_blocks, c->gs_part, s));
+  SEM_TRY(launch_cg_update(c->prec, m->n, c->x, c->p, c->r, c->w, c->z, minv_of(c), m->mult, m->ctab, c->st,
+                           c->upd_part, s));
+  return SEM_OK;
+}
+
+sem_status cg_iterate(sem_cg c, int k, cudaStream_t s) {
+  if (k <= 0) return SEM_OK;
+  if (!c->use_graph) {
+    for (int q = 0; q < k; ++q) SEM_TRY(cg_enqueue_iteration(c, s));
+    return SEM_OK;
+  }
+  if (!c->exec || c->exec_k != k || c->exec_x != c->x) {
+    if (c->exec) {
+      cudaGraphExecDestroy(c->exec);
+      c->exec = nullptr;
+    }
+    SEM_CUDA_TRY(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+    t_capturing = true;
+    sem_status st = SEM_OK;
+    for (int q = 0; q < k && st == SEM_OK; ++q) st = cg_enqueue_iteration(c, c->cap);
+    t_capturing = false;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->cap, &g);
+    if (st != SEM_OK) {
+      if (g) cudaGraphDestroy(g);
+      return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&c->exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      c->exec = nullptr;
+      return cuda_fail(e, "cudaGraphInstantiate");
+    }
+    c->exec_k = k;
+    c->exec_x = c->x;
+  }
+  SEM_CUDA_TRY(cudaGraphLaunch(c->exec, s));
+  count_launch(3 * k);
+  return SEM_OK;
+}
+
+sem_status cg_query(sem_cg c, sem_cg_result* res, cudaStream_t s) {
+  SEM_CUDA_TRY(cudaMemcpyAsync(c->st_host, c->st, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
+  SEM_CUDA_TRY(cudaStreamSynchronize(s));
+  const CgScalars& h = *c->st_host;
+  if (res) {
+    res->iters = h.iter;
+    res->outer_iters = 0;
+    res->rel_res = h.bb > 0 ? std::sqrt(h.rr / h.bb) : std::sqrt(h.rr);
+    res->status = h.done ? h.status : SEM_ERR_BUSY;
+  }
+  return SEM_OK;
+}
+
+sem_status check_opts(const sem_cg_opts* o) {
+  if (!o) return fail(SEM_ERR_ARG, "opts is null");
+  if (!(o->rtol >= 0) || o->max_iter < 0 || o->check_every < 1 || (o->precond != 0 && o->precond != 1) ||
+      (o->variant != SEM_AX_STORED && o->variant != SEM_AX_OTF) ||
+      (o->inner_variant != SEM_AX_STORED && o->inner_variant != SEM_AX_OTF))
+    return fail(SEM_ERR_ARG, "invalid CG options");
+  if (o->mixed && (!(o->inner_rtol > 0 && o->inner_rtol < 1) || o->max_outer < 1))
+    return fail(SEM_ERR_ARG, "mixed precision needs 0 < inner_rtol < 1 and max_outer >= 1");
+  return SEM_OK;
+}
+
+double now_ms() {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// Runs a started solver until its device flag says done; polls every check_every iterations.
+sem_status cg_run(sem_cg c, int check_every, sem_cg_result* r, cudaStream_t s) {
+  for (;;) {
+    SEM_TRY(cg_iterate(c, check_every, s));
+    SEM_TRY(cg_query(c, r, s));
+    if (r->status != SEM_ERR_BUSY) return SEM_OK;
+  }
+}
+
+// FP32 inner CG (on-the-fly or stored factors) inside FP64 iterative refinement:
+//   r = b - A x (FP64 operator, FP64 dots); stop if ||r||_c / ||b||_c <= rtol;
+//   solve A d = r in FP32 to inner_rtol; x += d.
+sem_status solve_mixed(sem_mesh m, const double* b, double* x, const sem_cg_opts* o, sem_cg_result* res,
+                       cudaStream_t s) {
+  sem_cg inner = nullptr;
+  SEM_TRY(cg_alloc(m, SEM_F32, static_cast<sem_ax_variant>(o->inner_variant), o->precond, o->inner_rtol,
+                   o->max_iter, o->use_graph, &inner));
+  std::unique_ptr<sem_cg_s, void (*)(sem_cg)> inner_guard(inner, cg_free);
+  double* w64 = nullptr;
+  double* r64 = nullptr;
+  float* r32 = nullptr;
+  float* d32 = nullptr;
+  CgScalars* ost = nullptr;
+  double* opart = nullptr;
+  auto release = [&] {
+    for (void* q : {static_cast<void*>(w64), static_cast<void*>(r64), static_cast<void*>(r32),
+                    static_cast<void*>(d32), static_cast<void*>(ost), static_cast<void*>(opart)})
+      if (q) cudaFree(q);
+  };
+  sem_status st = SEM_OK;
+  if ((st = dmalloc(&w64, m->n, nullptr)) != SEM_OK || (st = dmalloc(&r64, m->n, nullptr)) != SEM_OK ||
+      (st = dmalloc(&r32, m->n, nullptr)) != SEM_OK || (st = dmalloc(&d32, m->n, nullptr)) != SEM_OK ||
+      (st = dmalloc(&ost, 1, nullptr)) != SEM_OK || (st = dmalloc(&opart, 2 * kRedMax, nullptr)) != SEM_OK) {
+    release();
+    return st;
+  }
+  CgScalars oinit{};
+  oinit.rtol2 = o->rtol * o->rtol;
+  int total_inner = 0, outer = 0;
+  res->status = SEM_ERR_NOT_CONVERGED;
+  for (;;) {
+    // FP64 residual
+    AxLaunch a{};
+    a.u = x;
+    a.w = w64;
+    if ((st = launch_ax_any(m, SEM_F64, static_cast<sem_ax_variant>(o->variant), false, a, s)) != SEM_OK) break;
+    if ((st = launch_dssum(SEM_F64, m->n_seg, m->seg_off, m->seg_idx, m->seg_mask, w64, 1, s)) != SEM_OK) break;
+    cudaError_t e = cudaMemcpyAsync(ost, &oinit, sizeof(CgScalars), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) { st = cuda_fail(e, "cudaMemcpyAsync"); break; }
+    if ((st = launch_ir_residual(m->n, b, w64, r64, r32, m->mult, m->ctab, ost, opart, s)) != SEM_OK) break;
+    CgScalars oh{};
+    e = cudaMemcpyAsync(&oh, ost, sizeof(CgScalars), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) { st = cuda_fail(e, "reading the refinement residual"); break; }
+    res->rel_res = oh.bb > 0 ? std::sqrt(oh.rr / oh.bb) : std::sqrt(oh.rr);
+    if (oh.done) {
+      res->status = oh.status;
+      break;
+    }
+    if (outer >= o->max_outer || total_inner >= o->max_iter) {
+      res->status = SEM_ERR_NOT_CONVERGED;
+      break;
+    }
+    // FP32 inner solve from d = 0
+    inner->max_iter = o->max_iter - total_inner;
+    if ((e = cudaMemsetAsync(d32, 0, m->n * sizeof(float), s)) != cudaSuccess) { st = cuda_fail(e, "memset"); break; }
+    if ((st = cg_start(inner, r32, d32, true, s)) != SEM_OK) break;
+    sem_cg_result ir{};
+    if ((st = cg_run(inner, o->check_every, &ir, s)) != SEM_OK) break;
+    total_inner += ir.iters;
+    ++outer;
+    if (ir.status == SEM_ERR_BREAKDOWN && ir.iters == 0) {
+      res->status = SEM_ERR_BREAKDOWN;
+      break;
+    }
+    if ((st = launch_ir_correct(m->n, x, d32, s)) != SEM_OK) break;
+  }
+  res->iters = total_inner;
+  res->outer_iters = outer;
+  release();
+  return st;
+}
+
+}  // namespace
+}  // namespace sem
+
+extern "C" sem_status sem_cg_default_opts(sem_cg_opts* o) {
+  if (!o) return fail(SEM_ERR_ARG, "opts is null");
+  o->rtol = 1e-10;
+  o->max_iter = 100000;
+  o->precond = 1;
+  o->variant = SEM_AX_STORED;
+  o->mixed = 0;
+  o->inner_variant = SEM_AX_OTF;
+  o->inner_rtol = 1e-5;
+  o->max_outer = 50;
+  o->check_every = 50;
+  o->use_graph = 1;
+  return SEM_OK;
+}
+
+extern "C" sem_status sem_cg_create(sem_mesh m, const sem_cg_opts* o, sem_cg* out) {
+  if (!out) return fail(SEM_ERR_ARG, "out is null");
+  *out = nullptr;
+  SEM_TRY(check_mesh(m));
+  SEM_TRY(check_opts(o));
+  if (o->mixed) return fail(SEM_ERR_ARG, "the stateful CG handle runs FP64 CG only (mixed=0)");
+  return cg_alloc(m, SEM_F64, static_cast<sem_ax_variant>(o->variant), o->precond, o->rtol, o->max_iter, o->use_graph,
+                  out);
+}
+
+extern "C" sem_status sem_cg_start(sem_cg c, const double* b, double* x, void* stream) {
+  if (!c) return fail(SEM_ERR_ARG, "null CG handle");
+  SEM_TRY(check_mesh(c->m));
+  SEM_TRY(check_ptr(b, "b_dev"));
+  SEM_TRY(check_ptr(x, "x_dev"));
+  return cg_start(c, b, x, false, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" sem_status sem_cg_iterate(sem_cg c, int k, void* stream) {
+  if (!c) return fail(SEM_ERR_ARG, "null CG handle");
+  if (!c->x) return fail(SEM_ERR_ARG, "sem_cg_start has not been called");
+  return cg_iterate(c, k, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" sem_status sem_cg_query(sem_cg c, sem_cg_result* res, void* stream) {
+  if (!c || !res) return fail(SEM_ERR_ARG, "null argument");
+  res->time_ms = 0;
+  return cg_query(c, res, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" sem_status sem_cg_destroy(sem_cg c) {
+  if (!c) return SEM_OK;
+  cudaDeviceSynchronize();
+  cg_free(c);
+  return SEM_OK;
+}
+
+extern "C" sem_status sem_cg_solve(sem_mesh m, const double* b, double* x, const sem_cg_opts* o, sem_cg_result* res,
+                                   void* stream) {
+  SEM_TRY(check_mesh(m));
+  SEM_TRY(check_opts(o));
+  SEM_TRY(check_ptr(b, "b_dev"));
+  SEM_TRY(check_ptr(x, "x_dev"));
+  if (!res) return fail(SEM_ERR_ARG, "result is null");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const double t0 = now_ms();
+  *res = sem_cg_result{};
+  sem_status st;
+  if (o->mixed) {
+    st = solve_mixed(m, b, x, o, res, s);
+  } else {
+    sem_cg c = nullptr;
+    SEM_TRY(cg_alloc(m, SEM_F64, static_cast<sem_ax_variant>(o->variant), o->precond, o->rtol, o->max_iter,
+                     o->use_graph, &c));
+    st = cg_start(c, b, x, false, s);
+    if (st == SEM_OK) st = cg_run(c, o->check_every, res, s);
+    cudaStreamSynchronize(s);
+    cg_free(c);
+  }
+  res->time_ms = now_ms() - t0;
+  if (st != SEM_OK) {
+    res->status = st;
+    return st;
+  }
+  if (res->status == SEM_ERR_NOT_CONVERGED) return fail(SEM_ERR_NOT_CONVERGED, "CG reached max_iter");
+  if (res->status == SEM_ERR_BREAKDOWN) return fail(SEM_ERR_BREAKDOWN, "CG breakdown (<p,Ap,c> <= 0 or non-finite)");
+  return static_cast<sem_status>(res->status);
+}
+
+extern "C" uint64_t sem_launch_count(void) { return g_launches.load(); }
+
+extern "C" const char* sem_last_error(void) { return t_last_error.c_str(); }
+
+extern "C" const char* sem_status_string(sem_status s) {
+  switch (s) {
+    case SEM_OK: return "SEM_OK";
+    case SEM_ERR_ARG: return "SEM_ERR_ARG";
+    case SEM_ERR_MESH: return "SEM_ERR_MESH";
+    case SEM_ERR_OOM: return "SEM_ERR_OOM";
+    case SEM_ERR_CUDA: return "SEM_ERR_CUDA";
+    case SEM_ERR_NOT_CONVERGED: return "SEM_ERR_NOT_CONVERGED";
+    case SEM_ERR_BREAKDOWN: return "SEM_ERR_BREAKDOWN";
+    case SEM_ERR_TIMEOUT: return "SEM_ERR_TIMEOUT";
+    case SEM_ERR_BUSY: return "SEM_ERR_BUSY";
+    case SEM_ERR_UNSUPPORTED: return "SEM_ERR_UNSUPPORTED";
+  }
+  return "unknown";
+}

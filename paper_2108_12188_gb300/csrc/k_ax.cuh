@@ -1,0 +1,245 @@
+// Local SEM operator w = A_L u = D^T G D u (Eq. 4, Section 3.1), one element per NP x NP
+// thread tile, EPB elements per block, grid-stride over element groups.
+//
+// Thread (i, j) of an element holds the column u(i, j, 0..NP-1) in registers and
+// the element field in shared memory:
+//   forward:   ur = sum_l D_il u(l,j,k), us = sum_l D_jl u(i,l,k), ut = sum_l D_kl u(i,j,l)
+//   geometry:  (vr, vs, vt) = G (ur, us, ut), G read from memory (STORED) or rebuilt from
+//              the element's trilinear coefficients (OTF, Section 5.1's rematerialisation)
+//   transpose: w = sum_l D_li vr(l,j,k) + sum_l D_lj vs(i,l,k) + sum_l D_lk vt(i,j,l)
+// The k-direction contractions stay in registers; D for it comes from the constant bank.
+//
+// OTF geometry without forming G: with g_b = dx/dxi_b (columns of J) and the cofactor
+// rows c_0 = g_1 x g_2, c_1 = g_2 x g_0, c_2 = g_0 x g_1 (c_b = det J * row b of J^-1),
+//   G v = (w_i w_j w_k / det J) C (C^T v),  C^T v = sum_b c_b v_b,
+// which costs 21 multiply-adds instead of building six factors and applying them.
+//
+// CG mode (Algorithm 1, steps 5-6 fused, Section 5.1): the prologue forms p = z + beta p
+// and stores it, and the epilogue adds p.w over element-interior points (those points are
+// untouched by the gather-scatter) into a per-block partial of <p, w, c>.
+#pragma once
+
+#include "k_common.cuh"
+
+namespace sem {
+
+template <int NP>
+__host__ __device__ constexpr int ax_epb() {
+  return NP <= 2 ? 32 : NP == 3 ? 16 : NP == 4 ? 8 : NP == 5 ? 5 : NP <= 7 ? (NP == 6 ? 4 : 3) : NP <= 9 ? 2 : 1;
+}
+
+template <typename T>
+struct Vec3 {
+  T x, y, z;
+};
+template <typename T>
+__device__ __forceinline__ Vec3<T> cross(const Vec3<T>& a, const Vec3<T>& b) {
+  return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+template <typename T>
+__device__ __forceinline__ T dot3(const Vec3<T>& a, const Vec3<T>& b) {
+  return a.x * b.x + a.y * b.y + a.z * b.z;
+}
+template <typename T>
+__device__ __forceinline__ T div_fast(T a, T b) {
+  return a / b;
+}
+template <>
+__device__ __forceinline__ float div_fast<float>(float a, float b) {
+  return __fdividef(a, b);
+}
+
+template <int NP, typename T, bool OTF, bool CG>
+__global__ void __launch_bounds__(NP * NP * ax_epb<NP>())
+    k_ax(const __grid_constant__ GllParam<NP, T> tab, int64_t E, const T* __restrict__ u, T* __restrict__ w,
+         const T* __restrict__ G, const T* __restrict__ coef, const T* __restrict__ z, T* __restrict__ p,
+         const CgScalars* __restrict__ st, double* __restrict__ partials) {
+  constexpr int NP2 = NP * NP, P = NP2 * NP, EPB = ax_epb<NP>();
+  __shared__ T sD[NP2];
+  __shared__ T sXi[NP], sW[NP];
+  __shared__ T sA[EPB][P];
+  __shared__ T sB[EPB][P];
+  __shared__ double sRed[32];
+
+  T beta = T(0);
+  if constexpr (CG) {
+    if (st->done) return;  // uniform over the grid: set by an earlier launch
+    beta = static_cast<T>(st->beta);
+  }
+  for (int q = threadIdx.x; q < NP2; q += blockDim.x) sD[q] = tab.D[q];
+  for (int q = threadIdx.x; q < NP; q += blockDim.x) {
+    sXi[q] = tab.xi[q];
+    sW[q] = tab.w[q];
+  }
+  const int slot = threadIdx.x / NP2, tid = threadIdx.x % NP2;
+  const int i = tid % NP, j = tid / NP;
+  double dot = 0.0;
+  __syncthreads();
+
+  for (int64_t grp = blockIdx.x; grp * EPB < E; grp += gridDim.x) {
+    const int64_t e = grp * EPB + slot;
+    const bool valid = e < E;
+    const int64_t base = e * P + tid;
+    T rU[NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      T val = T(0);
+      if (valid) {
+        if constexpr (CG) {
+          val = z[base + k * NP2] + beta * p[base + k * NP2];
+          p[base + k * NP2] = val;
+        } else {
+          val = u[base + k * NP2];
+        }
+      }
+      rU[k] = val;
+      sA[slot][k * NP2 + tid] = val;
+    }
+
+    // OTF: per-thread parts of the Jacobian columns that do not depend on k
+    Vec3<T> g2{}, P0{}, Q0{}, P1{}, Q1{};
+    T wij = T(0);
+    if constexpr (OTF) {
+      if (valid) {
+        const T* a = coef + e * 24;  // a0..a7, each (x, y, z); a0 (the centroid) is not needed
+        const T xi = sXi[i], eta = sXi[j];
+        const Vec3<T> a1{a[3], a[4], a[5]}, a2{a[6], a[7], a[8]}, a3{a[9], a[10], a[11]};
+        const Vec3<T> a4{a[12], a[13], a[14]}, a5{a[15], a[16], a[17]}, a6{a[18], a[19], a[20]};
+        const Vec3<T> a7{a[21], a[22], a[23]};
+        // x(xi,eta,gam) = a0 + a1 xi + a2 eta + a3 gam + a4 xi eta + a5 xi gam + a6 eta gam + a7 xi eta gam
+        g2 = {a3.x + a5.x * xi + a6.x * eta + a7.x * xi * eta, a3.y + a5.y * xi + a6.y * eta + a7.y * xi * eta,
+              a3.z + a5.z * xi + a6.z * eta + a7.z * xi * eta};
+        P0 = {a1.x + a4.x * eta, a1.y + a4.y * eta, a1.z + a4.z * eta};
+        Q0 = {a5.x + a7.x * eta, a5.y + a7.y * eta, a5.z + a7.z * eta};
+        P1 = {a2.x + a4.x * xi, a2.y + a4.y * xi, a2.z + a4.z * xi};
+        Q1 = {a6.x + a7.x * xi, a6.y + a7.y * xi, a6.z + a7.z * xi};
+        wij = sW[i] * sW[j];
+      }
+    }
+    __syncthreads();
+
+    T rR[NP], rS[NP], rT[NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      T ur = T(0), us = T(0), ut = T(0);
+#pragma unroll
+      for (int l = 0; l < NP; ++l) {
+        ur += sD[i * NP + l] * sA[slot][k * NP2 + j * NP + l];
+        us += sD[j * NP + l] * sA[slot][k * NP2 + l * NP + i];
+        ut += tab.D[k * NP + l] * rU[l];
+      }
+      if constexpr (OTF) {
+        const T gam = tab.xi[k];
+        const Vec3<T> g0{P0.x + gam * Q0.x, P0.y + gam * Q0.y, P0.z + gam * Q0.z};
+        const Vec3<T> g1{P1.x + gam * Q1.x, P1.y + gam * Q1.y, P1.z + gam * Q1.z};
+        const Vec3<T> c0 = cross(g1, g2), c1 = cross(g2, g0), c2 = cross(g0, g1);
+        const T det = dot3(g0, c0);
+        const T s = valid ? div_fast(wij * tab.w[k], det) : T(0);
+        const Vec3<T> q{c0.x * ur + c1.x * us + c2.x * ut, c0.y * ur + c1.y * us + c2.y * ut,
+                        c0.z * ur + c1.z * us + c2.z * ut};
+        rR[k] = s * dot3(c0, q);
+        rS[k] = s * dot3(c1, q);
+        rT[k] = s * dot3(c2, q);
+      } else {
+        T g11 = T(0), g12 = T(0), g13 = T(0), g22 = T(0), g23 = T(0), g33 = T(0);
+        if (valid) {
+          const T* gp = G + e * 6 * P + k * NP2 + tid;
+          g11 = gp[0 * P];
+          g12 = gp[1 * P];
+          g13 = gp[2 * P];
+          g22 = gp[3 * P];
+          g23 = gp[4 * P];
+          g33 = gp[5 * P];
+        }
+        rR[k] = g11 * ur + g12 * us + g13 * ut;
+        rS[k] = g12 * ur + g22 * us + g23 * ut;
+        rT[k] = g13 * ur + g23 * us + g33 * ut;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      sA[slot][k * NP2 + tid] = rR[k];
+      sB[slot][k * NP2 + tid] = rS[k];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      T acc = T(0);
+#pragma unroll
+      for (int l = 0; l < NP; ++l) {
+        acc += sD[l * NP + i] * sA[slot][k * NP2 + j * NP + l];
+        acc += sD[l * NP + j] * sB[slot][k * NP2 + l * NP + i];
+        acc += tab.D[l * NP + k] * rT[l];
+      }
+      if (valid) w[base + k * NP2] = acc;
+      if constexpr (CG) {
+        const bool interior = i > 0 && i < NP - 1 && j > 0 && j < NP - 1 && k > 0 && k < NP - 1;
+        if (valid && interior) dot += static_cast<double>(rU[k]) * static_cast<double>(acc);
+      }
+    }
+    __syncthreads();
+  }
+  if constexpr (CG) {
+    const double s = block_sum(dot, sRed);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+  }
+}
+
+template <int NP, typename T, bool OTF, bool CG>
+int ax_max_blocks() {
+  static int cached = 0;
+  if (cached == 0) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ax<NP, T, OTF, CG>, NP * NP * ax_epb<NP>(), 0);
+    cached = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+  }
+  return cached;
+}
+
+template <int NP, typename T, bool OTF, bool CG>
+sem_status launch_ax_t(int N, const AxLaunch& a, cudaStream_t s) {
+  constexpr int EPB = ax_epb<NP>();
+  const int64_t groups = (a.E + EPB - 1) / EPB;
+  int grid = ax_max_blocks<NP, T, OTF, CG>();
+  if (grid > kRedMax) grid = kRedMax;
+  if (groups < grid) grid = static_cast<int>(groups);
+  if (a.grid_out) *a.grid_out = grid;
+  const GllParam<NP, T> tab = make_gll_param<NP, T>(N);
+  k_ax<NP, T, OTF, CG><<<grid, NP * NP * EPB, 0, s>>>(
+      tab, a.E, static_cast<const T*>(a.u), static_cast<T*>(a.w), static_cast<const T*>(a.G),
+      static_cast<const T*>(a.coef), static_cast<const T*>(a.z), static_cast<T*>(a.p), a.st, a.partials);
+  count_launch();
+  SEM_CUDA_TRY(cudaGetLastError());
+  return SEM_OK;
+}
+
+// Dispatch over the variant and the mode for one order and precision.
+template <int NP, typename T>
+sem_status launch_ax_np(int N, sem_ax_variant v, bool cg, const AxLaunch& a, cudaStream_t s) {
+  if (v == SEM_AX_OTF)
+    return cg ? launch_ax_t<NP, T, true, true>(N, a, s) : launch_ax_t<NP, T, true, false>(N, a, s);
+  return cg ? launch_ax_t<NP, T, false, true>(N, a, s) : launch_ax_t<NP, T, false, false>(N, a, s);
+}
+
+template <typename T>
+sem_status launch_ax_prec(int N, sem_ax_variant v, bool cg, const AxLaunch& a, cudaStream_t s) {
+  switch (N + 1) {
+    case 2: return launch_ax_np<2, T>(N, v, cg, a, s);
+    case 3: return launch_ax_np<3, T>(N, v, cg, a, s);
+    case 4: return launch_ax_np<4, T>(N, v, cg, a, s);
+    case 5: return launch_ax_np<5, T>(N, v, cg, a, s);
+    case 6: return launch_ax_np<6, T>(N, v, cg, a, s);
+    case 7: return launch_ax_np<7, T>(N, v, cg, a, s);
+    case 8: return launch_ax_np<8, T>(N, v, cg, a, s);
+    case 9: return launch_ax_np<9, T>(N, v, cg, a, s);
+    case 10: return launch_ax_np<10, T>(N, v, cg, a, s);
+    case 11: return launch_ax_np<11, T>(N, v, cg, a, s);
+    case 12: return launch_ax_np<12, T>(N, v, cg, a, s);
+    default: return fail(SEM_ERR_UNSUPPORTED, "polynomial order not compiled in");
+  }
+}
+
+}  // namespace sem

@@ -1,0 +1,258 @@
+// Conjugate-gradient vector kernels (Algorithm 1 with z = M^-1 r for the Jacobi
+// preconditioner). Steps 9-11 are fused into one pass (Section 5.1's loop fusion):
+//   x += alpha p;  r -= alpha w;  z = M^-1 r;  partials of <r, z, c> and <r, r, c>,
+// and the last block to finish forms rho, beta, the iteration count and the stopping
+// decision on the device, so the host never waits inside an iteration.
+//
+// Weights c = 1 / multiplicity come from a per-point multiplicity byte and a 256-entry
+// table of exact reciprocals (interior points have multiplicity 1). Dot products are
+// accumulated in FP64 per thread and combined in a fixed order, so they are bitwise
+// reproducible for a given mesh and launch.
+#include "k_common.cuh"
+
+namespace sem {
+namespace {
+
+constexpr int kThreads = 256;
+
+int vec_grid(int64_t n) {
+  const int64_t b = (n + kThreads - 1) / kThreads;
+  const int64_t cap = 152 * 8;
+  return static_cast<int>(b < cap ? (b > 0 ? b : 1) : cap);
+}
+
+__device__ __forceinline__ double weight(const uint8_t* __restrict__ mult, const double* __restrict__ ctab, int64_t i) {
+  const unsigned m = mult[i];
+  return m == 1u ? 1.0 : __ldg(ctab + m);
+}
+
+template <typename T>
+__global__ void k_glsc3(int64_t n, const T* __restrict__ a, const T* __restrict__ b, const uint8_t* __restrict__ mult,
+                        const double* __restrict__ ctab, double* __restrict__ partials, unsigned int* ticket,
+                        double* __restrict__ result) {
+  __shared__ double sRed[kThreads / 32];
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    acc += static_cast<double>(a[i]) * static_cast<double>(b[i]) * weight(mult, ctab, i);
+  const double v[1] = {block_sum(acc, sRed)};
+  if (publish_partials<1>(v, partials, ticket)) {
+    const double s = sum_partials(partials, gridDim.x, 1, 0, sRed);
+    if (threadIdx.x == 0) *result = s;
+  }
+}
+
+// r = b - A x0 (A x0 assembled and masked; null for x0 = 0), z = M^-1 r, p = 0;
+// rho = <r,z,c>, <r,r,c>, <b,b,c>.
+template <typename T>
+__global__ void k_cg_init(int64_t n, const T* __restrict__ b, const T* __restrict__ ax0, T* __restrict__ r,
+                          T* __restrict__ z, T* __restrict__ p, const T* __restrict__ minv,
+                          const uint8_t* __restrict__ mult, const double* __restrict__ ctab, CgScalars* st,
+                          double* __restrict__ partials) {
+  __shared__ double sRed[kThreads / 32];
+  double rz = 0.0, rr = 0.0, bb = 0.0;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const T bi = b[i];
+    const T ri = ax0 ? bi - ax0[i] : bi;  // ax0 == nullptr: x0 = 0
+    const T zi = minv ? minv[i] * ri : ri;
+    r[i] = ri;
+    z[i] = zi;
+    p[i] = T(0);
+    const double c = weight(mult, ctab, i);
+    rz += c * static_cast<double>(ri) * static_cast<double>(zi);
+    rr += c * static_cast<double>(ri) * static_cast<double>(ri);
+    bb += c * static_cast<double>(bi) * static_cast<double>(bi);
+  }
+  const double v[3] = {block_sum(rz, sRed), block_sum(rr, sRed), block_sum(bb, sRed)};
+  if (publish_partials<3>(v, partials, &st->ticket[2])) {
+    const double srz = sum_partials(partials, gridDim.x, 3, 0, sRed);
+    const double srr = sum_partials(partials, gridDim.x, 3, 1, sRed);
+    const double sbb = sum_partials(partials, gridDim.x, 3, 2, sRed);
+    if (threadIdx.x == 0) {
+      st->rho = srz;
+      st->rz = srz;
+      st->rr = srr;
+      st->bb = sbb;
+      st->beta = 0.0;
+      st->alpha = 0.0;
+      st->iter = 0;
+      if (!isfinite(srz) || !isfinite(srr) || !isfinite(sbb)) {
+        st->status = SEM_ERR_BREAKDOWN;
+        st->done = 1;
+      } else if (srr <= st->rtol2 * sbb) {
+        st->status = SEM_OK;
+        st->done = 1;
+      } else if (st->max_iter <= 0) {
+        st->status = SEM_ERR_NOT_CONVERGED;
+        st->done = 1;
+      } else {
+        st->status = 0;
+        st->done = 0;
+      }
+    }
+  }
+}
+
+// Algorithm 1 steps 9-13 with z = M^-1 r.
+template <typename T>
+__global__ void k_cg_update(int64_t n, T* __restrict__ x, const T* __restrict__ p, T* __restrict__ r,
+                            const T* __restrict__ w, T* __restrict__ z, const T* __restrict__ minv,
+                            const uint8_t* __restrict__ mult, const double* __restrict__ ctab, CgScalars* st,
+                            double* __restrict__ partials) {
+  __shared__ double sRed[kThreads / 32];
+  if (st->done) return;
+  const T alpha = static_cast<T>(st->alpha);
+  double rz = 0.0, rr = 0.0;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    x[i] += alpha * p[i];
+    const T ri = r[i] - alpha * w[i];
+    const T zi = minv ? minv[i] * ri : ri;
+    r[i] = ri;
+    z[i] = zi;
+    const double c = weight(mult, ctab, i);
+    rz += c * static_cast<double>(ri) * static_cast<double>(zi);
+    rr += c * static_cast<double>(ri) * static_cast<double>(ri);
+  }
+  const double v[2] = {block_sum(rz, sRed), block_sum(rr, sRed)};
+  if (publish_partials<2>(v, partials, &st->ticket[1])) {
+    const double srz = sum_partials(partials, gridDim.x, 2, 0, sRed);
+    const double srr = sum_partials(partials, gridDim.x, 2, 1, sRed);
+    if (threadIdx.x == 0) {
+      const int it = st->iter + 1;
+      st->iter = it;
+      st->rz = srz;
+      st->rr = srr;
+      if (!isfinite(srz) || !isfinite(srr)) {
+        st->status = SEM_ERR_BREAKDOWN;
+        st->done = 1;
+      } else if (srr <= st->rtol2 * st->bb) {
+        st->status = SEM_OK;
+        st->done = 1;
+      } else if (it >= st->max_iter) {
+        st->status = SEM_ERR_NOT_CONVERGED;
+        st->done = 1;
+      } else {
+        st->beta = srz / st->rho;
+        st->rho = srz;
+      }
+    }
+  }
+}
+
+}  // namespace
+
+sem_status launch_glsc3(sem_prec prec, int64_t n, const void* a, const void* b, const uint8_t* mult,
+                        const double* ctab, double* partials, unsigned int* ticket, double* result, cudaStream_t s) {
+  const int grid = vec_grid(n);
+  if (prec == SEM_F64)
+    k_glsc3<double><<<grid, kThreads, 0, s>>>(n, static_cast<const double*>(a), static_cast<const double*>(b), mult,
+                                              ctab, partials, ticket, result);
+  else
+    k_glsc3<float><<<grid, kThreads, 0, s>>>(n, static_cast<const float*>(a), static_cast<const float*>(b), mult,
+                                             ctab, partials, ticket, result);
+  count_launch();
+  SEM_CUDA_TRY(cudaGetLastError());
+  return SEM_OK;
+}
+
+sem_status launch_cg_init(sem_prec prec, int64_t n, const void* b, const void* ax0, void* r, void* z, void* p,
+                          const void* minv, const uint8_t* mult, const double* ctab, CgScalars* st, double* partials,
+                          cudaStream_t s) {
+  const int grid = vec_grid(n);
+  if (prec == SEM_F64)
+    k_cg_init<double><<<grid, kThreads, 0, s>>>(n, static_cast<const double*>(b), static_cast<const double*>(ax0),
+                                                static_cast<double*>(r), static_cast<double*>(z),
+                                                static_cast<double*>(p), static_cast<const double*>(minv), mult, ctab,
+                                                st, partials);
+  else
+    k_cg_init<float><<<grid, kThreads, 0, s>>>(n, static_cast<const float*>(b), static_cast<const float*>(ax0),
+                                               static_cast<float*>(r), static_cast<float*>(z), static_cast<float*>(p),
+                                               static_cast<const float*>(minv), mult, ctab, st, partials);
+  count_launch();
+  SEM_CUDA_TRY(cudaGetLastError());
+  return SEM_OK;
+}
+
+sem_status launch_cg_update(sem_prec prec, int64_t n, void* x, const void* p, void* r, const void* w, void* z,
+                            const void* minv, const uint8_t* mult, const double* ctab, CgScalars* st,
+                            double* partials, cudaStream_t s) {
+  const int grid = vec_grid(n);
+  if (prec == SEM_F64)
+    k_cg_update<double><<<grid, kThreads, 0, s>>>(n, static_cast<double*>(x), static_cast<const double*>(p),
+                                                  static_cast<double*>(r), static_cast<const double*>(w),
+                                                  static_cast<double*>(z), static_cast<const double*>(minv), mult,
+                                                  ctab, st, partials);
+  else
+    k_cg_update<float><<<grid, kThreads, 0, s>>>(n, static_cast<float*>(x), static_cast<const float*>(p),
+                                                 static_cast<float*>(r), static_cast<const float*>(w),
+                                                 static_cast<float*>(z), static_cast<const float*>(minv), mult, ctab,
+                                                 st, partials);
+  count_launch();
+  SEM_CUDA_TRY(cudaGetLastError());
+  return SEM_OK;
+}
+
+}  // namespace sem
+
+namespace sem {
+namespace {
+
+__global__ void k_ir_residual(int64_t n, const double* __restrict__ b, const double* __restrict__ w,
+                              double* __restrict__ r64, float* __restrict__ r32, const uint8_t* __restrict__ mult,
+                              const double* __restrict__ ctab, CgScalars* st, double* __restrict__ partials) {
+  __shared__ double sRed[kThreads / 32];
+  double rr = 0.0, bb = 0.0;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const double bi = b[i], ri = bi - w[i];
+    r64[i] = ri;
+    r32[i] = static_cast<float>(ri);
+    const double c = weight(mult, ctab, i);
+    rr += c * ri * ri;
+    bb += c * bi * bi;
+  }
+  const double v[2] = {block_sum(rr, sRed), block_sum(bb, sRed)};
+  if (publish_partials<2>(v, partials, &st->ticket[3])) {
+    const double srr = sum_partials(partials, gridDim.x, 2, 0, sRed);
+    const double sbb = sum_partials(partials, gridDim.x, 2, 1, sRed);
+    if (threadIdx.x == 0) {
+      st->rr = srr;
+      st->bb = sbb;
+      if (!isfinite(srr) || !isfinite(sbb)) {
+        st->status = SEM_ERR_BREAKDOWN;
+        st->done = 1;
+      } else if (srr <= st->rtol2 * sbb) {
+        st->status = SEM_OK;
+        st->done = 1;
+      }
+    }
+  }
+}
+
+__global__ void k_ir_correct(int64_t n, double* __restrict__ x, const float* __restrict__ d) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    x[i] += static_cast<double>(d[i]);
+}
+
+}  // namespace
+
+sem_status launch_ir_residual(int64_t n, const double* b, const double* w, double* r64, float* r32,
+                              const uint8_t* mult, const double* ctab, CgScalars* st, double* partials,
+                              cudaStream_t s) {
+  k_ir_residual<<<vec_grid(n), kThreads, 0, s>>>(n, b, w, r64, r32, mult, ctab, st, partials);
+  count_launch();
+  SEM_CUDA_TRY(cudaGetLastError());
+  return SEM_OK;
+}
+
+sem_status launch_ir_correct(int64_t n, double* x, const float* d, cudaStream_t s) {
+  k_ir_correct<<<vec_grid(n), kThreads, 0, s>>>(n, x, d);
+  count_launch();
+  SEM_CUDA_TRY(cudaGetLastError());
+  return SEM_OK;
+}
+
+}  // namespace sem

@@ -1,0 +1,143 @@
+// Internal declarations shared by the host (C++) and device (CUDA) parts of libsem.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/sem.h"
+
+namespace sem {
+
+constexpr int kMaxNp = SEM_MAX_N + 1;  // 12 points per direction at most
+
+// Sets the thread-local error message and returns `s`.
+sem_status fail(sem_status s, const std::string& msg);
+sem_status cuda_fail(cudaError_t e, const char* what);
+void count_launch(int k = 1);
+
+#define SEM_CUDA_TRY(expr)                                    \
+  do {                                                        \
+    cudaError_t _e = (expr);                                  \
+    if (_e != cudaSuccess) return ::sem::cuda_fail(_e, #expr); \
+  } while (0)
+
+// ---- host GLL tables (gll.cpp) ----
+struct GllTable {
+  double xi[kMaxNp], w[kMaxNp], D[kMaxNp * kMaxNp];  // D[i*Np + j] = l_j'(xi_i)
+};
+const GllTable& gll_table(int N);  // N in [1, SEM_MAX_N]
+
+// ---- host topology builder (topology.cpp) ----
+struct Topology {
+  int N = 0, Np = 0;
+  int64_t E = 0, n = 0, n_glob = 0;
+  std::vector<int64_t> glo;      // [n]
+  std::vector<uint8_t> mask;     // [n]
+  std::vector<uint8_t> mult;     // [n] multiplicity of the node's global id (<= 255)
+  std::vector<int32_t> seg_off;  // [n_seg + 1]
+  std::vector<int32_t> seg_idx;  // [n_gs]
+  std::vector<uint8_t> seg_mask; // [n_seg]
+};
+sem_status build_topology(int N, int64_t num_vertices, int64_t E, const int64_t* elem_verts,
+                          const uint8_t* dirichlet_flags, Topology& out);
+
+// ---- device-side CG scalars ----
+struct CgScalars {
+  double rho, alpha, beta, pw, rz, rr, bb, rtol2;
+  int iter, max_iter, done, status;  // status: 0 running, SEM_OK converged, else sem_status
+  unsigned int ticket[4];            // last-block-done counters (reset by the last block)
+};
+
+// ---- reduction scratch ----
+constexpr int kRedMax = 8192;  // upper bound of blocks of any reducing launch
+
+}  // namespace sem
+
+// The mesh object behind the opaque handle.
+struct sem_mesh_s {
+  int N = 0, Np = 0, device = 0;
+  unsigned flags = 0;
+  int64_t E = 0, n = 0, n_glob = 0, n_seg = 0, n_gs = 0;
+  std::vector<int64_t> glo;   // host copy for the test hooks
+  std::vector<uint8_t> mask;  // host copy
+  // device arrays
+  double* coef64 = nullptr;   // [E][24] trilinear coefficients a0..a7 (x, y, z)
+  float* coef32 = nullptr;    // [E][24] rounded to FP32
+  double* G64 = nullptr;      // [E][6][P] or null
+  float* G32 = nullptr;       // [E][6][P] or null
+  int32_t* seg_off = nullptr;
+  int32_t* seg_idx = nullptr;
+  uint8_t* seg_mask = nullptr;
+  uint8_t* mult = nullptr;    // [n]
+  double* minv64 = nullptr;   // lazily built Jacobi inverse
+  float* minv32 = nullptr;
+  double* ctab = nullptr;     // [256] exact reciprocals 1/m (weights c = 1/multiplicity)
+  double* partials = nullptr; // reduction scratch [kRedMax] for sem_glsc3
+  unsigned int* ticket = nullptr;
+  size_t device_bytes = 0;
+};
+
+namespace sem {
+
+// ---- kernel launchers (CUDA translation units) ----
+struct AxLaunch {
+  int64_t E;
+  const void* u;      // input (plain mode)
+  void* w;            // output
+  const void* G;      // stored factors or null
+  const void* coef;   // trilinear coefficients (otf)
+  // CG mode (p = z + beta p prologue, interior part of <p, w> in the epilogue)
+  const void* z;
+  void* p;
+  CgScalars* st;
+  double* partials;   // [gridDim.x] interior partial dots
+  int* grid_out;      // receives gridDim.x used
+};
+sem_status launch_ax_f64(int N, sem_ax_variant v, bool cg_mode, const AxLaunch& a, cudaStream_t s);
+sem_status launch_ax_f32(int N, sem_ax_variant v, bool cg_mode, const AxLaunch& a, cudaStream_t s);
+
+// element geometry (k_mesh.cu)
+sem_status launch_coefficients(int64_t E, const double* X, double* coef64, float* coef32, cudaStream_t s);
+sem_status launch_geometry(int N, int64_t E, const double* coef64, double* G64, float* G32, double* B64,
+                           float* B32, int* bad_flag, cudaStream_t s);
+sem_status launch_coords(int N, int64_t E, const double* coef64, double* xyz, int64_t n, cudaStream_t s);
+sem_status launch_local_diag(int N, int64_t E, const double* coef64, double* d, cudaStream_t s);
+sem_status launch_rhs_local(int N, int64_t E, const double* coef64, int a, int b, int c, double* out,
+                            cudaStream_t s);
+sem_status launch_scatter(sem_prec prec, int64_t n, const int32_t* glo, const void* ug, void* ul, cudaStream_t s);
+sem_status launch_invert(int64_t n, const double* d, double* m64, float* m32, cudaStream_t s);
+sem_status launch_cast(int64_t n, const double* in, float* out, cudaStream_t s);
+
+// gather-scatter (k_gs.cu)
+sem_status launch_dssum(sem_prec prec, int64_t n_seg, const int32_t* off, const int32_t* idx,
+                        const uint8_t* smask, void* u, int apply_mask, cudaStream_t s);
+// CG variant: also the boundary part of <p, w, c>; the last block combines it with
+// the Ax kernel's interior partials and sets alpha (or a breakdown status).
+sem_status launch_dssum_cg(sem_prec prec, int64_t n_seg, const int32_t* off, const int32_t* idx,
+                           const uint8_t* smask, void* w, const void* p, CgScalars* st, const double* ax_partials,
+                           int ax_blocks, double* partials, cudaStream_t s);
+// Jacobi: assembled diagonal inverted (0 on Dirichlet nodes) on every element-boundary copy.
+sem_status launch_dssum_invert(int64_t n_seg, const int32_t* off, const int32_t* idx, const uint8_t* smask,
+                               const double* d, double* m64, float* m32, cudaStream_t s);
+
+// CG vector kernels (k_cg.cu)
+sem_status launch_glsc3(sem_prec prec, int64_t n, const void* a, const void* b, const uint8_t* mult,
+                        const double* ctab, double* partials, unsigned int* ticket, double* result, cudaStream_t s);
+sem_status launch_cg_init(sem_prec prec, int64_t n, const void* b, const void* ax0, void* r, void* z, void* p,
+                          const void* minv, const uint8_t* mult, const double* ctab, CgScalars* st, double* partials,
+                          cudaStream_t s);
+sem_status launch_cg_update(sem_prec prec, int64_t n, void* x, const void* p, void* r, const void* w, void* z,
+                            const void* minv, const uint8_t* mult, const double* ctab, CgScalars* st,
+                            double* partials, cudaStream_t s);
+// Iterative refinement (FP64 outer loop around an FP32 inner solve):
+// r64 = b - w64, r32 = (float) r64, <r,r,c> and <b,b,c> into st (done when converged).
+sem_status launch_ir_residual(int64_t n, const double* b, const double* w, double* r64, float* r32,
+                              const uint8_t* mult, const double* ctab, CgScalars* st, double* partials,
+                              cudaStream_t s);
+// x64 += (double) d32
+sem_status launch_ir_correct(int64_t n, double* x, const float* d, cudaStream_t s);
+
+}  // namespace sem

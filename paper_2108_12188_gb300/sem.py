@@ -1,0 +1,346 @@
+"""Thin ctypes binding of libsem (include/sem.h): same names, argument marshalling only.
+
+Every computation happens in the library's CUDA kernels. Device buffers are torch
+CUDA tensors (contiguous, of the precision the call names); the stream defaults to
+torch's current stream. A missing or unloadable library raises immediately: there
+is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libsem.so")
+
+SEM_OK, SEM_ERR_ARG, SEM_ERR_MESH, SEM_ERR_OOM, SEM_ERR_CUDA = 0, 1, 2, 3, 4
+SEM_ERR_NOT_CONVERGED, SEM_ERR_BREAKDOWN, SEM_ERR_TIMEOUT, SEM_ERR_BUSY, SEM_ERR_UNSUPPORTED = 5, 6, 7, 8, 9
+SEM_F64, SEM_F32 = 0, 1
+SEM_AX_STORED, SEM_AX_OTF = 0, 1
+SEM_MESH_F64_STORED, SEM_MESH_F32_STORED = 1, 2
+SEM_MAX_N = 11
+
+# every symbol include/sem.h declares (checked by the tests)
+EXPORTS = [
+    "sem_mesh_create", "sem_mesh_numbering", "sem_mesh_destroy", "sem_mesh_get_info", "sem_mesh_get_glo_num", "sem_mesh_get_mask",
+    "sem_mesh_get_segments", "sem_mesh_coords", "sem_mesh_geometry", "sem_scatter", "sem_ax", "sem_dssum",
+    "sem_glsc3", "sem_jacobi", "sem_rhs_sine", "sem_cg_default_opts", "sem_cg_solve", "sem_cg_create",
+    "sem_cg_start", "sem_cg_iterate", "sem_cg_query", "sem_cg_destroy", "sem_launch_count", "sem_last_error",
+    "sem_status_string",
+]
+
+
+class SemError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_status_name(status)}: {message}")
+        self.status = status
+
+
+class MeshInfo(C.Structure):
+    _fields_ = [("N", C.c_int), ("Np", C.c_int), ("E", C.c_int64), ("n_local", C.c_int64),
+                ("n_glob", C.c_int64), ("n_seg", C.c_int64), ("n_gs", C.c_int64), ("flags", C.c_uint),
+                ("device", C.c_int), ("device_bytes", C.c_size_t)]
+
+
+class CgOpts(C.Structure):
+    _fields_ = [("rtol", C.c_double), ("max_iter", C.c_int), ("precond", C.c_int), ("variant", C.c_int),
+                ("mixed", C.c_int), ("inner_variant", C.c_int), ("inner_rtol", C.c_double),
+                ("max_outer", C.c_int), ("check_every", C.c_int), ("use_graph", C.c_int)]
+
+
+class CgResult(C.Structure):
+    _fields_ = [("iters", C.c_int), ("outer_iters", C.c_int), ("rel_res", C.c_double), ("time_ms", C.c_double),
+                ("status", C.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+_VP, _I, _I64, _D, _U = C.c_void_p, C.c_int, C.c_int64, C.c_double, C.c_uint
+
+
+def load_library(path: str | None = None):
+    """Loads libsem.so (built in-tree by build_lib); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"libsem.so not found at {path}: build it first (python -m paper_2108_12188_gb300.build_lib)")
+    lib = C.CDLL(path)
+    sig = {
+        "sem_mesh_create": [_I, _I64, _VP, _I64, _VP, _VP, _U, _VP, C.POINTER(_VP)],
+        "sem_mesh_destroy": [_VP],
+        "sem_mesh_numbering": [_I, _I64, _I64, _VP, _VP, _VP, _VP, C.POINTER(_I64)],
+        "sem_mesh_get_info": [_VP, C.POINTER(MeshInfo)],
+        "sem_mesh_get_glo_num": [_VP, _VP],
+        "sem_mesh_get_mask": [_VP, _VP],
+        "sem_mesh_get_segments": [_VP, _VP, _VP, _VP],
+        "sem_mesh_coords": [_VP, _VP, _VP],
+        "sem_mesh_geometry": [_VP, _I, _VP, _VP, _VP],
+        "sem_scatter": [_VP, _I, _VP, _VP, _VP],
+        "sem_ax": [_VP, _I, _I, _VP, _VP, _I, _VP],
+        "sem_dssum": [_VP, _I, _VP, _I, _VP],
+        "sem_glsc3": [_VP, _I, _VP, _VP, _VP, _VP],
+        "sem_jacobi": [_VP, _I, _VP, _VP],
+        "sem_rhs_sine": [_VP, _I, _I, _I, _I, _VP, _VP],
+        "sem_cg_default_opts": [C.POINTER(CgOpts)],
+        "sem_cg_solve": [_VP, _VP, _VP, C.POINTER(CgOpts), C.POINTER(CgResult), _VP],
+        "sem_cg_create": [_VP, C.POINTER(CgOpts), C.POINTER(_VP)],
+        "sem_cg_start": [_VP, _VP, _VP, _VP],
+        "sem_cg_iterate": [_VP, _I, _VP],
+        "sem_cg_query": [_VP, C.POINTER(CgResult), _VP],
+        "sem_cg_destroy": [_VP],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = _I
+    lib.sem_launch_count.argtypes, lib.sem_launch_count.restype = [], C.c_uint64
+    lib.sem_last_error.argtypes, lib.sem_last_error.restype = [], C.c_char_p
+    lib.sem_status_string.argtypes, lib.sem_status_string.restype = [_I], C.c_char_p
+    _lib = lib
+    return lib
+
+
+def _status_name(s: int) -> str:
+    names = {0: "SEM_OK", 1: "SEM_ERR_ARG", 2: "SEM_ERR_MESH", 3: "SEM_ERR_OOM", 4: "SEM_ERR_CUDA",
+             5: "SEM_ERR_NOT_CONVERGED", 6: "SEM_ERR_BREAKDOWN", 7: "SEM_ERR_TIMEOUT", 8: "SEM_ERR_BUSY",
+             9: "SEM_ERR_UNSUPPORTED"}
+    return names.get(s, str(s))
+
+
+def _check(status: int, ok=(SEM_OK,)):
+    if status not in ok:
+        raise SemError(status, load_library().sem_last_error().decode())
+    return status
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _dev(t, dtype=None, numel=None, name="tensor"):
+    """Device pointer of a contiguous CUDA tensor, after checking dtype and size."""
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} must have {numel} elements, got {t.numel()}")
+    return t.data_ptr()
+
+
+def _torch_dtype(prec):
+    import torch
+    return torch.float64 if prec == SEM_F64 else torch.float32
+
+
+# ---------------------------------------------------------------------------
+# mesh
+# ---------------------------------------------------------------------------
+
+def sem_mesh_create(N, vert_xyz, elem_verts, dirichlet_vertex_flags=None, flags=SEM_MESH_F64_STORED, stream=None):
+    lib = load_library()
+    vx = np.ascontiguousarray(vert_xyz, dtype=np.float64)
+    ev = np.ascontiguousarray(elem_verts, dtype=np.int64)
+    if vx.ndim != 2 or vx.shape[1] != 3 or ev.ndim != 2 or ev.shape[1] != 8:
+        raise ValueError("vert_xyz must be [nv, 3] and elem_verts [E, 8]")
+    df = None if dirichlet_vertex_flags is None else np.ascontiguousarray(dirichlet_vertex_flags, dtype=np.uint8)
+    out = _VP()
+    _check(lib.sem_mesh_create(int(N), vx.shape[0], vx.ctypes.data, ev.shape[0], ev.ctypes.data,
+                               None if df is None else df.ctypes.data, int(flags), _stream(stream), C.byref(out)))
+    return out
+
+
+def sem_mesh_numbering(N, num_vertices, elem_verts, dirichlet_vertex_flags=None):
+    """Host-only numbering: returns (glo_num int64 [n], mask uint8 [n], n_glob)."""
+    lib = load_library()
+    ev = np.ascontiguousarray(elem_verts, dtype=np.int64)
+    n = ev.shape[0] * (int(N) + 1) ** 3
+    glo = np.empty(n, dtype=np.int64)
+    msk = np.empty(n, dtype=np.uint8)
+    df = None if dirichlet_vertex_flags is None else np.ascontiguousarray(dirichlet_vertex_flags, dtype=np.uint8)
+    ng = C.c_int64()
+    _check(lib.sem_mesh_numbering(int(N), int(num_vertices), ev.shape[0], ev.ctypes.data,
+                                  None if df is None else df.ctypes.data, glo.ctypes.data, msk.ctypes.data,
+                                  C.byref(ng)))
+    return glo, msk, int(ng.value)
+
+
+def sem_mesh_destroy(mesh):
+    _check(load_library().sem_mesh_destroy(mesh))
+
+
+def sem_mesh_get_info(mesh) -> dict:
+    info = MeshInfo()
+    _check(load_library().sem_mesh_get_info(mesh, C.byref(info)))
+    return {f: getattr(info, f) for f, _ in MeshInfo._fields_}
+
+
+def sem_mesh_get_glo_num(mesh) -> np.ndarray:
+    n = sem_mesh_get_info(mesh)["n_local"]
+    out = np.empty(n, dtype=np.int64)
+    _check(load_library().sem_mesh_get_glo_num(mesh, out.ctypes.data))
+    return out
+
+
+def sem_mesh_get_mask(mesh) -> np.ndarray:
+    n = sem_mesh_get_info(mesh)["n_local"]
+    out = np.empty(n, dtype=np.uint8)
+    _check(load_library().sem_mesh_get_mask(mesh, out.ctypes.data))
+    return out
+
+
+def sem_mesh_get_segments(mesh):
+    info = sem_mesh_get_info(mesh)
+    off = np.empty(info["n_seg"] + 1, dtype=np.int32)
+    idx = np.empty(info["n_gs"], dtype=np.int32)
+    msk = np.empty(info["n_seg"], dtype=np.uint8)
+    _check(load_library().sem_mesh_get_segments(mesh, off.ctypes.data, idx.ctypes.data, msk.ctypes.data))
+    return off, idx, msk
+
+
+def sem_mesh_coords(mesh, xyz, stream=None):
+    import torch
+    n = sem_mesh_get_info(mesh)["n_local"]
+    _check(load_library().sem_mesh_coords(mesh, _dev(xyz, torch.float64, 3 * n, "xyz"), _stream(stream)))
+
+
+def sem_mesh_geometry(mesh, prec, G=None, B=None, stream=None):
+    info = sem_mesh_get_info(mesh)
+    P = info["Np"] ** 3
+    dt = _torch_dtype(prec)
+    _check(load_library().sem_mesh_geometry(mesh, prec, _dev(G, dt, info["E"] * 6 * P, "G"),
+                                            _dev(B, dt, info["E"] * P, "B"), _stream(stream)))
+
+
+def sem_scatter(mesh, prec, u_glob, u_local, stream=None):
+    info = sem_mesh_get_info(mesh)
+    dt = _torch_dtype(prec)
+    _check(load_library().sem_scatter(mesh, prec, _dev(u_glob, dt, info["n_glob"], "u_glob"),
+                                      _dev(u_local, dt, info["n_local"], "u_local"), _stream(stream)))
+
+
+def sem_ax(mesh, variant, prec, u, w, assemble=True, stream=None, n_local=None):
+    n = n_local if n_local is not None else sem_mesh_get_info(mesh)["n_local"]
+    dt = _torch_dtype(prec)
+    _check(load_library().sem_ax(mesh, variant, prec, _dev(u, dt, n, "u"), _dev(w, dt, n, "w"), int(bool(assemble)),
+                                 _stream(stream)))
+
+
+def sem_dssum(mesh, prec, u, apply_mask=True, stream=None):
+    n = sem_mesh_get_info(mesh)["n_local"]
+    _check(load_library().sem_dssum(mesh, prec, _dev(u, _torch_dtype(prec), n, "u"), int(bool(apply_mask)),
+                                    _stream(stream)))
+
+
+def sem_glsc3(mesh, prec, a, b, result, stream=None):
+    import torch
+    n = sem_mesh_get_info(mesh)["n_local"]
+    dt = _torch_dtype(prec)
+    _check(load_library().sem_glsc3(mesh, prec, _dev(a, dt, n, "a"), _dev(b, dt, n, "b"),
+                                    _dev(result, torch.float64, 1, "result"), _stream(stream)))
+
+
+def sem_jacobi(mesh, prec, minv, stream=None):
+    n = sem_mesh_get_info(mesh)["n_local"]
+    _check(load_library().sem_jacobi(mesh, prec, _dev(minv, _torch_dtype(prec), n, "minv"), _stream(stream)))
+
+
+def sem_rhs_sine(mesh, a, b, c, prec, rhs, stream=None):
+    n = sem_mesh_get_info(mesh)["n_local"]
+    _check(load_library().sem_rhs_sine(mesh, int(a), int(b), int(c), prec, _dev(rhs, _torch_dtype(prec), n, "rhs"),
+                                       _stream(stream)))
+
+
+# ---------------------------------------------------------------------------
+# conjugate gradient
+# ---------------------------------------------------------------------------
+
+def sem_cg_default_opts(**overrides) -> CgOpts:
+    o = CgOpts()
+    _check(load_library().sem_cg_default_opts(C.byref(o)))
+    for k, v in overrides.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def sem_cg_solve(mesh, b, x, opts=None, stream=None, raise_on=(SEM_ERR_ARG, SEM_ERR_MESH, SEM_ERR_OOM,
+                                                            SEM_ERR_CUDA, SEM_ERR_UNSUPPORTED)) -> dict:
+    """Runs sem_cg_solve; returns the result as a dict (its 'status' tells convergence)."""
+    import torch
+    n = sem_mesh_get_info(mesh)["n_local"]
+    opts = opts or sem_cg_default_opts()
+    res = CgResult()
+    st = load_library().sem_cg_solve(mesh, _dev(b, torch.float64, n, "b"), _dev(x, torch.float64, n, "x"),
+                                     C.byref(opts), C.byref(res), _stream(stream))
+    if st in raise_on:
+        _check(st)
+    return res.as_dict()
+
+
+def sem_cg_create(mesh, opts=None):
+    out = _VP()
+    _check(load_library().sem_cg_create(mesh, C.byref(opts or sem_cg_default_opts()), C.byref(out)))
+    return out
+
+
+def sem_cg_start(cg, b, x, stream=None):
+    import torch
+    _check(load_library().sem_cg_start(cg, _dev(b, torch.float64, None, "b"), _dev(x, torch.float64, None, "x"),
+                                       _stream(stream)))
+
+
+def sem_cg_iterate(cg, k, stream=None):
+    _check(load_library().sem_cg_iterate(cg, int(k), _stream(stream)))
+
+
+def sem_cg_query(cg, stream=None) -> dict:
+    res = CgResult()
+    _check(load_library().sem_cg_query(cg, C.byref(res), _stream(stream)))
+    return res.as_dict()
+
+
+def sem_cg_destroy(cg):
+    _check(load_library().sem_cg_destroy(cg))
+
+
+def sem_launch_count() -> int:
+    return int(load_library().sem_launch_count())
+
+
+def sem_status_string(s: int) -> str:
+    return load_library().sem_status_string(int(s)).decode()
+
+
+class Mesh:
+    """Owns a sem_mesh handle; frees it on close() or garbage collection."""
+
+    def __init__(self, N, vert_xyz, elem_verts, dirichlet_vertex_flags=None, flags=SEM_MESH_F64_STORED, stream=None):
+        self.handle = sem_mesh_create(N, vert_xyz, elem_verts, dirichlet_vertex_flags, flags, stream)
+        self.info = sem_mesh_get_info(self.handle)
+        self.n = self.info["n_local"]
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            sem_mesh_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

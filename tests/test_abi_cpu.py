@@ -1,0 +1,102 @@
+"""CPU-side checks of the C ABI: the library builds and loads, exports every symbol
+include/sem.h declares, and its host mesh builder (Section 3.1's numbering Q, the
+Dirichlet mask of Algorithm 1 step 7) matches the oracle bit for bit."""
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from oracle import sem_oracle as so
+from synthetic import BoxMesh
+from tests.test_oracle_numbering import _reorient
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="session")
+def sem():
+    from paper_2108_12188_gb300 import build_lib, sem as sem_mod
+    build_lib.build()
+    sem_mod.load_library()
+    return sem_mod
+
+
+def _header_symbols():
+    text = open(os.path.join(ROOT, "include", "sem.h")).read()
+    return set(re.findall(r"^\s*(?:sem_status|uint64_t|const char\*)\s+(sem_\w+)\s*\(", text, flags=re.M))
+
+
+def test_exports_every_declared_symbol(sem):
+    declared = _header_symbols()
+    assert len(declared) >= 20
+    out = subprocess.run(["nm", "-D", "--defined-only", sem.LIB_PATH], capture_output=True, text=True, check=True)
+    exported = {line.split()[-1] for line in out.stdout.splitlines() if " T " in line}
+    assert declared <= exported, declared - exported
+    assert declared == set(sem.EXPORTS)
+
+
+@pytest.mark.parametrize("n,N,jitter", [((1, 1, 1), 1, 0.0), ((2, 1, 1), 2, 0.0), ((3, 2, 2), 3, 0.2),
+                                         ((4, 4, 4), 7, 0.1), ((2, 3, 2), 11, 0.1)])
+def test_host_numbering_matches_oracle(sem, n, N, jitter):
+    m = BoxMesh(*n, jitter=jitter, seed=3)
+    glo, mask, n_glob = sem.sem_mesh_numbering(N, m.num_vertices, m.elem_verts)
+    num = so.number_nodes(N, m.elem_verts)
+    assert n_glob == num.n_glob
+    np.testing.assert_array_equal(glo, num.glo_num)
+    np.testing.assert_array_equal(mask, num.mask)
+
+
+@pytest.mark.parametrize("N", [2, 3, 6])
+def test_host_numbering_reoriented_elements(sem, N):
+    m = BoxMesh(3, 3, 2, jitter=0.2, seed=9)
+    ev = _reorient(m.elem_verts, np.random.default_rng(100 + N))
+    glo, mask, n_glob = sem.sem_mesh_numbering(N, m.num_vertices, ev)
+    num = so.number_nodes(N, ev)
+    np.testing.assert_array_equal(glo, num.glo_num)
+    np.testing.assert_array_equal(mask, num.mask)
+
+
+def test_host_numbering_dirichlet_flags(sem):
+    m = BoxMesh(2, 2, 3)
+    flags = (m.vert_xyz[:, 0] == 0.0).astype(np.uint8) | (m.vert_xyz[:, 2] == 1.0).astype(np.uint8)
+    glo, mask, _ = sem.sem_mesh_numbering(4, m.num_vertices, m.elem_verts, flags)
+    num = so.number_nodes(4, m.elem_verts, flags)
+    np.testing.assert_array_equal(glo, num.glo_num)
+    np.testing.assert_array_equal(mask, num.mask)
+
+
+def test_host_numbering_full_size_properties(sem):
+    # the 32^3, N = 7 Ax-throughput mesh: counts and first-occurrence order (Eq. 9)
+    m = BoxMesh(32, 32, 32, jitter=0.15, seed=1)
+    glo, mask, n_glob = sem.sem_mesh_numbering(7, m.num_vertices, m.elem_verts)
+    assert n_glob == 225 ** 3
+    first = np.maximum.accumulate(glo)
+    assert first[0] == 0 and np.all(np.diff(first) <= 1) and first[-1] == n_glob - 1
+    mult = np.bincount(glo, minlength=n_glob)
+    assert int((mult == 8).sum()) == 31 ** 3 and set(np.unique(mult)) == {1, 2, 4, 8}
+    assert int((mult == 1).sum()) == 32 ** 3 * 6 ** 3 + 6 * 32 ** 2 * 6 ** 2 + 12 * 32 * 6 + 8
+    assert len(np.unique(glo[mask == 0])) == 223 ** 3
+
+
+def test_host_errors(sem):
+    m = BoxMesh(1, 1, 1)
+    ev = m.elem_verts.copy()
+    ev[0, 1] = ev[0, 0]
+    with pytest.raises(sem.SemError) as e:
+        sem.sem_mesh_numbering(3, m.num_vertices, ev)
+    assert e.value.status == sem.SEM_ERR_MESH
+    ev = m.elem_verts.copy()
+    ev[0, 2] = 99
+    with pytest.raises(sem.SemError) as e:
+        sem.sem_mesh_numbering(3, m.num_vertices, ev)
+    assert e.value.status == sem.SEM_ERR_MESH
+    for N in (0, 12):
+        with pytest.raises(sem.SemError) as e:
+            sem.sem_mesh_numbering(N, m.num_vertices, m.elem_verts)
+        assert e.value.status == sem.SEM_ERR_UNSUPPORTED
+    # three hexahedra on one face: not a manifold mesh
+    ev3 = np.concatenate([m.elem_verts, m.elem_verts[:, [0, 1, 2, 3, 4, 5, 6, 7]] + 0], axis=0)
+    with pytest.raises(sem.SemError):
+        sem.sem_mesh_numbering(2, m.num_vertices, np.concatenate([ev3, m.elem_verts]))
