@@ -100,3 +100,27 @@ def test_host_errors(sem):
     ev3 = np.concatenate([m.elem_verts, m.elem_verts[:, [0, 1, 2, 3, 4, 5, 6, 7]] + 0], axis=0)
     with pytest.raises(sem.SemError):
         sem.sem_mesh_numbering(2, m.num_vertices, np.concatenate([ev3, m.elem_verts]))
+
+
+def _golden_hashes():
+    out = {}
+    with open(os.path.join(ROOT, "tests", "golden", "numbering_hashes.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            n, N, n_glob, hg, hm = line.split()
+            out[(int(n), int(N))] = (int(n_glob), hg, hm)
+    return out
+
+
+@pytest.mark.parametrize("n,N", [(32, 7), (20, 3), (9, 11)])
+def test_host_numbering_full_size_hash(sem, n, N):
+    # the oracle's numbering of these full-size meshes, pinned by SHA-256
+    # (tests/golden/make_numbering_hashes.py, which calls only the oracle)
+    import hashlib
+    n_glob, hg, hm = _golden_hashes()[(n, N)]
+    m = BoxMesh(n, n, n, jitter=0.15, seed=1)
+    glo, mask, ng = sem.sem_mesh_numbering(N, m.num_vertices, m.elem_verts)
+    assert ng == n_glob
+    assert hashlib.sha256(glo.astype("<i8").tobytes()).hexdigest() == hg
+    assert hashlib.sha256(mask.tobytes()).hexdigest() == hm
