@@ -1,0 +1,460 @@
+"""Benchmark of the spectral-element hot path on GB300.
+
+Workload: the Ax-throughput configuration - a 32 x 32 x 32 box of hexahedra on [0,1]^3,
+interior vertices jittered by U(-0.15h, 0.15h) (seed 1), order N = 7, 16,777,216 local
+points. One step = one Jacobi-preconditioned CG iteration (Algorithm 1) on the device:
+the local operator A_L with FP64 stored geometric factors and the fused p = z + beta p
+prologue, the gather-scatter QQ^T with the Dirichlet mask and <p, w, c>, and the fused
+x / r / z update with <r, z, c> and <r, r, c>. Every step moves more than L2 (1.1 GB).
+value = local points per step / device time per step (GDOF/s), aggregated over ranks.
+
+Also reported: the local operator alone for FP64/FP32 x stored/on-the-fly factors (with
+L2 flushed between timed calls) with its error against the FP64 oracle on sampled
+elements; the end-to-end rate through sem_cg_solve with pinned host buffers; the oracle
+on the host cores (cpu_baseline); SM clocks during the timed region.
+
+python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Ax GDOF/s & %roofline (FP64/FP32); CG time to 1e-10; served p50/p99 latency"
+WORKLOAD = ("32x32x32 hexahedra on [0,1]^3, interior vertices jittered +-0.15h (seed 1), N=7, "
+            "16,777,216 local points; step = one Jacobi-PCG iteration, FP64 stored geometric factors")
+NEL, NORD, JITTER, SEED = 32, 7, 0.15, 1
+HBM_FALLBACK_GBS = 6800.0
+# FP64 / FP32 FMA issue rates of a GB300 SM (2 and 128 per clock; the FP64 rate was
+# measured at 1.91 FMA/clk/SM with an FMA-chain probe) x 152 SMs x 2070 MHz x 2 flop.
+SMS, CLK_MHZ = 152, 2070.0
+PEAK_FP64_TFLOPS = SMS * 2 * 2 * CLK_MHZ * 1e6 / 1e12      # 1.259
+PEAK_FP32_TFLOPS = SMS * 128 * 2 * CLK_MHZ * 1e6 / 1e12    # 80.5
+
+
+def flops_eq11(N: int) -> int:
+    """Eq. 11: flops of A_L per local point, 12(N+1) + 15."""
+    return 12 * (N + 1) + 15
+
+
+def ax_bytes_per_point(variant: str, prec: str, N: int) -> float:
+    """Algorithmic bytes of one A_L application per local point (u read, w written, factors)."""
+    word = 8 if prec == "f64" else 4
+    P = (N + 1) ** 3
+    if variant == "stored":
+        return word * (1 + 1 + 6)
+    return word * (1 + 1) + word * 21 / P  # 21 trilinear coefficients per element
+
+
+def cg_bytes_per_point(N: int) -> float:
+    """Algorithmic bytes per local point of one fused Jacobi-PCG iteration (FP64, stored):
+    Ax kernel z, p in, p, w out, G (10 words); gather-scatter 2 n_gs/n words of w and p at
+    one copy per segment; update x, p, r, w, M^-1 in, x, r, z out (8 words) + 1 byte of
+    multiplicity."""
+    Np = N + 1
+    ngs_frac = (Np ** 3 - (N - 1) ** 3) / Np ** 3
+    return 8 * (10 + 2 * ngs_frac + 8) + 1
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+def ncu_traffic(kernel_key: str):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel source is unchanged."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    src = os.path.join(ROOT, "paper_2108_12188_gb300", "csrc", "k_ax.cuh")
+    try:
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        with open(path) as f:
+            for line in f:
+                parts = line.split()
+                if len(parts) == 3 and parts[0] == kernel_key and parts[1] == digest:
+                    return float(parts[2])
+    except OSError:
+        pass
+    return None
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            f = [x.strip() for x in ln.split(",")]
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except (ValueError, IndexError):
+                continue
+            for name, val in zip(names, f[4:8]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle on a bounded sample
+# ---------------------------------------------------------------------------
+
+def oracle_cg_sample(nel: int = 12, budget_s: float = 10.0) -> dict:
+    """Oracle Jacobi-PCG iterations on an nel^3 sub-box of the workload (same order, jitter,
+    seed); returns local points per second of CG iterations (setup excluded)."""
+    from oracle import sem_oracle as so
+    from synthetic import BoxMesh
+    m = BoxMesh(nel, nel, nel, jitter=JITTER, seed=SEED)
+    prob = so.SemProblem(NORD, m.vert_xyz, m.elem_verts)
+    b = prob.rhs()
+    t0 = time.perf_counter()
+    so.pcg(prob, b, rtol=0.0, max_iter=1)
+    t1 = time.perf_counter()
+    per_iter_guess = max(t1 - t0, 1e-3)
+    iters = max(2, min(2000, int(budget_s / per_iter_guess)))
+    t2 = time.perf_counter()
+    so.pcg(prob, b, rtol=0.0, max_iter=1 + iters)
+    t3 = time.perf_counter()
+    dt = ((t3 - t2) - (t1 - t0)) / iters
+    return {"n_local": prob.n, "iters": iters, "s_per_iter": dt, "gdof_s": prob.n / dt / 1e9,
+            "sample": f"{nel}^3 elements of the same jittered box (N={NORD}, {prob.n} local points), "
+                      f"{iters} oracle Jacobi-PCG iterations"}
+
+
+def run_cpu_baseline(budget_s: float = 10.0) -> dict:
+    """Runs oracle_cg_sample in a fresh single-threaded process (no CUDA state inherited)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ("import json, bench; print('RESULT ' + json.dumps(bench.oracle_cg_sample(budget_s=%r)))" % budget_s)
+    p = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    for ln in p.stdout.splitlines():
+        if ln.startswith("RESULT "):
+            r = json.loads(ln[7:])
+            return {"value": r["gdof_s"], "unit": "GDOF/s", "cores": 1, "kind": "oracle", "sample": r["sample"],
+                    "s_per_iter": r["s_per_iter"]}
+    raise RuntimeError("cpu baseline failed: " + p.stderr[-2000:])
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the oracle as it stands, on the host cores
+# ---------------------------------------------------------------------------
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import sem_oracle as so
+    from synthetic import BoxMesh, global_field
+    nel = 12
+    m = BoxMesh(nel, nel, nel, jitter=JITTER, seed=SEED)
+    prob = so.SemProblem(NORD, m.vert_xyz, m.elem_verts)
+    b = prob.rhs()
+    # one step = one oracle Jacobi-PCG iteration on the 8^3 sample of the workload
+    shape = prob.shape()
+    c = prob.c.reshape(shape)
+    Minv = prob.jacobi_inverse()
+    x = so.scatter_local(global_field(prob.num.n_glob, SEED), prob.glo_num).reshape(shape)
+    r = b - prob.ax(x)
+    z = Minv * r
+    p = z.copy()
+    rho = so.glsc3(r, z, c)
+
+    def step():
+        nonlocal x, r, z, p, rho
+        w = prob.ax(p)
+        alpha = rho / so.glsc3(p, w, c)
+        x = x + alpha * p
+        r = r - alpha * w
+        z = Minv * r
+        rho_new = so.glsc3(r, z, c)
+        so.glsc3(r, r, c)
+        p = z + (rho_new / rho) * p
+        rho = rho_new
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = (time.perf_counter() - t0) / args.steps
+    val = prob.n / dt / 1e9
+    sample = f"{nel}^3 elements of the same jittered box (N={NORD}, {prob.n} local points), one iteration per step"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "GDOF/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "reference_sample": sample},
+        "cpu_baseline": {"value": val, "unit": "GDOF/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": val, "unit": "GDOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+# ---------------------------------------------------------------------------
+# the GPU arm
+# ---------------------------------------------------------------------------
+
+def flush_l2(buf):
+    buf.add_(1.0)  # writes more bytes than L2 holds
+
+
+def time_ax(sem, mesh, variant, prec, u, w, flush_buf, reps, warmup, assemble):
+    import torch
+    for _ in range(warmup):
+        sem.sem_ax(mesh.handle, variant, prec, u, w, assemble=assemble, n_local=mesh.n)
+    times = []
+    s = torch.cuda.current_stream()
+    for _ in range(reps):
+        flush_l2(flush_buf)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        sem.sem_ax(mesh.handle, variant, prec, u, w, assemble=assemble, n_local=mesh.n)
+        e1.record(s)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    return statistics.median(times), min(times), max(times)
+
+
+def ax_error_vs_oracle(sem, mesh, m, variant, prec, n_sample=48):
+    """Relative 2-norm error of A_L against the FP64 oracle on sampled elements (local input)."""
+    import numpy as np
+    import torch
+    from oracle import sem_oracle as so
+    from synthetic import local_field
+    P = (NORD + 1) ** 3
+    u = local_field(mesh.n, seed=SEED + 17)
+    dt = torch.float64 if prec == 0 else torch.float32
+    ud = torch.tensor(u, dtype=dt, device="cuda")
+    wd = torch.empty_like(ud)
+    sem.sem_ax(mesh.handle, variant, prec, ud, wd, assemble=False, n_local=mesh.n)
+    rng = np.random.default_rng(5)
+    els = np.sort(rng.choice(m.num_elements, size=n_sample, replace=False))
+    xi, wq = so.gll_nodes_weights(NORD)
+    D = so.lagrange_derivative_matrix(xi)
+    X = so.element_vertices(m.vert_xyz, m.elem_verts[els])
+    G, _ = so.geometric_factors(X, xi, wq)
+    ue = u.reshape(-1, P)[els].reshape(n_sample, NORD + 1, NORD + 1, NORD + 1)
+    want = so.ax_local(ue, G, D).ravel()
+    got = wd.double().cpu().numpy().reshape(-1, P)[els].ravel()
+    return float(np.linalg.norm(got - want) / np.linalg.norm(want))
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(v: float) -> float:
+        if world == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    from paper_2108_12188_gb300 import build_lib, sem
+    from synthetic import BoxMesh, global_field
+    build_lib.build()
+    sem.load_library()
+    hbm_gbs, peak_src = measured_peaks()
+
+    m = BoxMesh(NEL, NEL, NEL, jitter=JITTER, seed=SEED)
+    mesh = sem.Mesh(NORD, m.vert_xyz, m.elem_verts, flags=sem.SEM_MESH_F64_STORED | sem.SEM_MESH_F32_STORED)
+    n = mesh.n
+    info = mesh.info
+    u_glob = torch.tensor(global_field(info["n_glob"], SEED, start=m.draws_used), dtype=torch.float64, device="cuda")
+    x0 = torch.empty(n, dtype=torch.float64, device="cuda")
+    sem.sem_scatter(mesh.handle, sem.SEM_F64, u_glob, x0)
+    b = torch.empty(n, dtype=torch.float64, device="cuda")
+    sem.sem_rhs_sine(mesh.handle, 1, 1, 1, sem.SEM_F64, b)
+    x = x0.clone()
+
+    # ---- timed region: K device-resident CG iterations
+    opts = sem.sem_cg_default_opts(rtol=0.0, max_iter=1 << 30, use_graph=0, check_every=1)
+    cg = sem.sem_cg_create(mesh.handle, opts)
+    sem.sem_cg_start(cg, b, x)
+    sem.sem_cg_iterate_timed(cg, args.warmup)
+    barrier()
+    l0 = sem.sem_launch_count()
+    with ClockSampler(local_rank) as clk:
+        total_ms, kernel_ms = sem.sem_cg_iterate_timed(cg, args.steps)
+        barrier()
+    launches = sem.sem_launch_count() - l0
+    q = sem.sem_cg_query(cg)
+    if q["status"] != sem.SEM_ERR_BUSY or q["iters"] != args.warmup + args.steps:
+        raise RuntimeError(f"CG stopped early during the benchmark: {q}")
+    sem.sem_cg_destroy(cg)
+    total_ms = max_over_ranks(total_ms)
+    ms_step = total_ms / args.steps
+    value = world * n / (ms_step * 1e-3) / 1e9
+
+    # roofline of the dominant kernel (the local operator, FP64 stored, CG mode)
+    ax_ms = kernel_ms[0]
+    ax_flops = flops_eq11(NORD) * n
+    ax_bytes = ax_bytes_per_point("stored", "f64", NORD) * n + 8 * 2 * n  # + p = z + beta p prologue
+    achieved_tf = ax_flops / (ax_ms * 1e-3) / 1e12
+    traffic = ncu_traffic("ax_f64_stored_cg")
+    roofline = {"bound": "alu", "achieved": achieved_tf, "peak": PEAK_FP64_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved_tf / PEAK_FP64_TFLOPS, "traffic": traffic,
+                "kernel": "k_ax<8,double,stored,CG>", "kernel_ms": ax_ms,
+                "hbm_achieved_gbs": ax_bytes / (ax_ms * 1e-3) / 1e9, "hbm_peak_gbs": hbm_gbs,
+                "hbm_frac": ax_bytes / (ax_ms * 1e-3) / 1e9 / hbm_gbs,
+                "peak_source": f"FP64 FMA issue rate (2/clk/SM) x 152 SMs x 2070 MHz; HBM {peak_src}",
+                "per_kernel_ms": {"ax": kernel_ms[0], "gather_scatter": kernel_ms[1], "update": kernel_ms[2]},
+                "step_bytes_algorithmic": cg_bytes_per_point(NORD) * n,
+                "step_hbm_frac": cg_bytes_per_point(NORD) * n / (ms_step * 1e-3) / 1e9 / hbm_gbs}
+
+    # ---- the local operator alone, per variant (rank 0 reports)
+    ax = {}
+    flush = torch.zeros(96 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 384 MB > L2
+    for vname, variant in (("stored", sem.SEM_AX_STORED), ("otf", sem.SEM_AX_OTF)):
+        for pname, prec in (("f64", sem.SEM_F64), ("f32", sem.SEM_F32)):
+            dt = torch.float64 if prec == sem.SEM_F64 else torch.float32
+            u = x0.to(dt)
+            w = torch.empty_like(u)
+            med, lo, hi = time_ax(sem, mesh, variant, prec, u, w, flush, reps=10, warmup=2, assemble=False)
+            med_a, _, _ = time_ax(sem, mesh, variant, prec, u, w, flush, reps=5, warmup=1, assemble=True)
+            byt = ax_bytes_per_point(vname, pname, NORD) * n
+            fl = flops_eq11(NORD) * n
+            peak_tf = PEAK_FP64_TFLOPS if pname == "f64" else PEAK_FP32_TFLOPS
+            t_roof = max(byt / (hbm_gbs * 1e9), fl / (peak_tf * 1e12))
+            err = ax_error_vs_oracle(sem, mesh, m, variant, prec) if rank == 0 else None
+            ax[f"{pname}_{vname}"] = {
+                "ms": med, "ms_min": lo, "ms_max": hi, "gdof_s": n / (med * 1e-3) / 1e9,
+                "gflop_s_eq11": fl / (med * 1e-3) / 1e9, "hbm_gbs": byt / (med * 1e-3) / 1e9,
+                "hbm_frac": byt / (med * 1e-3) / 1e9 / hbm_gbs,
+                "roofline_frac_eq11": t_roof / (med * 1e-3),
+                "assembled_ms": med_a, "assembled_gdof_s": n / (med_a * 1e-3) / 1e9,
+                "rel_err_vs_fp64_oracle": err}
+    del flush
+
+    # ---- end to end through the public API with pinned host buffers
+    bh = b.cpu().pin_memory()
+    xh = x0.cpu().pin_memory()
+    xo = torch.empty(n, dtype=torch.float64).pin_memory()
+    bd = torch.empty_like(b)
+    xd = torch.empty_like(b)
+    e2e_iters = args.steps
+    e_opts = sem.sem_cg_default_opts(rtol=0.0, max_iter=e2e_iters, check_every=e2e_iters, use_graph=1)
+    s = torch.cuda.current_stream()
+
+    def e2e_step():
+        bd.copy_(bh, non_blocking=True)
+        xd.copy_(xh, non_blocking=True)
+        res = sem.sem_cg_solve(mesh.handle, bd, xd, e_opts)
+        xo.copy_(xd, non_blocking=True)
+        return res
+
+    e2e_step()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2e_reps = 2
+    e0.record(s)
+    for _ in range(e2e_reps):
+        res = e2e_step()
+    e1.record(s)
+    e1.synchronize()
+    barrier()
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1) / e2e_reps)
+    if res["iters"] != e2e_iters:
+        raise RuntimeError(f"end-to-end solve ran {res['iters']} iterations, expected {e2e_iters}")
+    e2e = {"value": world * n * e2e_iters / (e2e_ms * 1e-3) / 1e9, "unit": "GDOF/s",
+           "h2d_bytes_per_step": 2 * n * 8, "d2h_bytes_per_step": n * 8,
+           "step": f"sem_cg_solve of {e2e_iters} Jacobi-PCG iterations from pinned host b and x0 to host x "
+                   "(work-vector allocation, r0 = b - A x0 and CUDA-graph capture included)",
+           "ms_per_step": e2e_ms}
+
+    if rank == 0:
+        cpu = run_cpu_baseline()
+        out = {
+            "metric": METRIC, "value": value, "unit": "GDOF/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "mesh": f"{NEL}^3 jittered box", "N": NORD, "n_local": n,
+                       "n_glob": info["n_glob"], "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "l2": "inputs larger than L2 (about 1.1 GB of algorithmic traffic per step)",
+                       "gflop_s_eq11": flops_eq11(NORD) * n / (ms_step * 1e-3) / 1e9},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clk.summary(), "ax": ax,
+        }
+        print(json.dumps(out))
+    mesh.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="sem", choices=["sem", "reference"])
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

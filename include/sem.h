@@ -211,6 +211,13 @@ sem_status sem_cg_create(sem_mesh mesh, const sem_cg_opts* opts, sem_cg* out);
 sem_status sem_cg_start(sem_cg cg, const double* b_dev, double* x_dev, void* stream);
 sem_status sem_cg_iterate(sem_cg cg, int k, void* stream);
 sem_status sem_cg_query(sem_cg cg, sem_cg_result* result_host, void* stream);
+/* Instrumented variant of sem_cg_iterate for measurement: runs k iterations eagerly
+ * (no graph) with CUDA events recorded on `stream` before the first kernel and after
+ * each of the three kernels of every iteration (local operator, gather-scatter, vector
+ * update); synchronises `stream` and returns the elapsed time of the k iterations in
+ * total_ms_host and the mean duration of each kernel in kernel_ms_host[3]. */
+sem_status sem_cg_iterate_timed(sem_cg cg, int k, double* total_ms_host, double* kernel_ms_host, void* stream);
+
 sem_status sem_cg_destroy(sem_cg cg);
 
 /* Number of kernel launches the library enqueued since load (all entry points). */

@@ -713,6 +713,62 @@ extern "C" sem_status sem_cg_iterate(sem_cg c, int k, void* stream) {
   return cg_iterate(c, k, static_cast<cudaStream_t>(stream));
 }
 
+extern "C" sem_status sem_cg_iterate_timed(sem_cg c, int k, double* total_ms, double* kernel_ms, void* stream) {
+  if (!c || !total_ms || !kernel_ms) return fail(SEM_ERR_ARG, "null argument");
+  if (!c->x) return fail(SEM_ERR_ARG, "sem_cg_start has not been called");
+  if (k < 1) return fail(SEM_ERR_ARG, "k must be >= 1");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  sem_mesh m = c->m;
+  std::vector<cudaEvent_t> ev(3 * static_cast<size_t>(k) + 1, nullptr);
+  auto destroy = [&] {
+    for (cudaEvent_t e : ev)
+      if (e) cudaEventDestroy(e);
+  };
+  for (auto& e : ev) {
+    cudaError_t r = cudaEventCreate(&e);
+    if (r != cudaSuccess) {
+      destroy();
+      return cuda_fail(r, "cudaEventCreate");
+    }
+  }
+  sem_status st = SEM_OK;
+  cudaEventRecord(ev[0], s);
+  for (int q = 0; q < k && st == SEM_OK; ++q) {
+    AxLaunch a{};
+    a.w = c->w;
+    a.z = c->z;
+    a.p = c->p;
+    a.st = c->st;
+    a.partials = c->ax_part;
+    a.grid_out = &c->ax_blocks;
+    st = launch_ax_any(m, c->prec, c->variant, true, a, s);
+    cudaEventRecord(ev[3 * q + 1], s);
+    if (st == SEM_OK)
+      st = launch_dssum_cg(c->prec, m->n_seg, m->seg_off, m->seg_idx, m->seg_mask, c->w, c->p, c->st, c->ax_part,
+                           c->ax_blocks, c->gs_part, s);
+    cudaEventRecord(ev[3 * q + 2], s);
+    if (st == SEM_OK)
+      st = launch_cg_update(c->prec, m->n, c->x, c->p, c->r, c->w, c->z, minv_of(c), m->mult, m->ctab, c->st,
+                            c->upd_part, s);
+    cudaEventRecord(ev[3 * q + 3], s);
+  }
+  cudaError_t r = cudaStreamSynchronize(s);
+  if (st == SEM_OK && r != cudaSuccess) st = cuda_fail(r, "cudaStreamSynchronize");
+  if (st == SEM_OK) {
+    float t = 0.f;
+    cudaEventElapsedTime(&t, ev[0], ev[3 * k]);
+    *total_ms = t;
+    for (int j = 0; j < 3; ++j) kernel_ms[j] = 0.0;
+    for (int q = 0; q < k; ++q)
+      for (int j = 0; j < 3; ++j) {
+        cudaEventElapsedTime(&t, ev[3 * q + j], ev[3 * q + j + 1]);
+        kernel_ms[j] += t / k;
+      }
+  }
+  destroy();
+  return st;
+}
+
 extern "C" sem_status sem_cg_query(sem_cg c, sem_cg_result* res, void* stream) {
   if (!c || !res) return fail(SEM_ERR_ARG, "null argument");
   res->time_ms = 0;

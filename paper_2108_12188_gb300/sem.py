@@ -27,7 +27,7 @@ EXPORTS = [
     "sem_mesh_create", "sem_mesh_numbering", "sem_mesh_destroy", "sem_mesh_get_info", "sem_mesh_get_glo_num", "sem_mesh_get_mask",
     "sem_mesh_get_segments", "sem_mesh_coords", "sem_mesh_geometry", "sem_scatter", "sem_ax", "sem_dssum",
     "sem_glsc3", "sem_jacobi", "sem_rhs_sine", "sem_cg_default_opts", "sem_cg_solve", "sem_cg_create",
-    "sem_cg_start", "sem_cg_iterate", "sem_cg_query", "sem_cg_destroy", "sem_launch_count", "sem_last_error",
+    "sem_cg_start", "sem_cg_iterate", "sem_cg_iterate_timed", "sem_cg_query", "sem_cg_destroy", "sem_launch_count", "sem_last_error",
     "sem_status_string",
 ]
 
@@ -93,6 +93,7 @@ def load_library(path: str | None = None):
         "sem_cg_start": [_VP, _VP, _VP, _VP],
         "sem_cg_iterate": [_VP, _I, _VP],
         "sem_cg_query": [_VP, C.POINTER(CgResult), _VP],
+        "sem_cg_iterate_timed": [_VP, _I, C.POINTER(_D), C.POINTER(_D), _VP],
         "sem_cg_destroy": [_VP],
     }
     for name, args in sig.items():
@@ -306,6 +307,14 @@ def sem_cg_start(cg, b, x, stream=None):
 
 def sem_cg_iterate(cg, k, stream=None):
     _check(load_library().sem_cg_iterate(cg, int(k), _stream(stream)))
+
+
+def sem_cg_iterate_timed(cg, k, stream=None):
+    """Runs k instrumented iterations; returns (total_ms, [ax_ms, gather_scatter_ms, update_ms])."""
+    total = C.c_double()
+    per = (C.c_double * 3)()
+    _check(load_library().sem_cg_iterate_timed(cg, int(k), C.byref(total), per, _stream(stream)))
+    return total.value, [per[0], per[1], per[2]]
 
 
 def sem_cg_query(cg, stream=None) -> dict:
