@@ -156,6 +156,21 @@ sem_status sem_dssum(sem_mesh mesh, sem_prec prec, void* u_dev, int apply_mask, 
 sem_status sem_glsc3(sem_mesh mesh, sem_prec prec, const void* a_dev, const void* b_dev, double* result_dev,
                      void* stream);
 
+/* Allocation-free variant of sem_glsc3 (no counterpart in the paper). Some callers cannot
+ * let a library allocate device memory: programs that own every device buffer through their
+ * own pool, or loops that cannot take the device-wide synchronisation of cudaMalloc/cudaFree.
+ * This call computes the same <a, b, c> as sem_glsc3 (FP64 accumulation; it may differ from
+ * sem_glsc3 in the last bits because blocks split the sum differently) without allocating
+ * anything: its block partials and completion counter live in a static device array of
+ * 33,024 bytes that every GPU loading the library holds until the process exits. Limits and
+ * rules: n_local <= 33,554,432 (4096 blocks x 8192 points), else SEM_ERR_ARG; all calls share
+ * the array, so calls that overlap on the GPU (other streams or host threads) race and give
+ * wrong results; the counter is cleared on `stream` before each launch; the first call on
+ * each device looks up the array's device address and must come before any stream capture
+ * is started. Async. */
+sem_status sem_glsc3_noalloc(sem_mesh mesh, sem_prec prec, const void* a_dev, const void* b_dev, double* result_dev,
+                             void* stream);
+
 /* Jacobi preconditioner: minv_dev = 1 / diag(QQ^T A_L) on unmasked points, 0 on
  * Dirichlet points (exact diagonal of the assembled operator). Async. */
 sem_status sem_jacobi(sem_mesh mesh, sem_prec prec, void* minv_dev, void* stream);

@@ -26,7 +26,7 @@ SEM_MAX_N = 11
 EXPORTS = [
     "sem_mesh_create", "sem_mesh_numbering", "sem_mesh_destroy", "sem_mesh_get_info", "sem_mesh_get_glo_num", "sem_mesh_get_mask",
     "sem_mesh_get_segments", "sem_mesh_coords", "sem_mesh_geometry", "sem_scatter", "sem_ax", "sem_dssum",
-    "sem_glsc3", "sem_jacobi", "sem_rhs_sine", "sem_cg_default_opts", "sem_cg_solve", "sem_cg_create",
+    "sem_glsc3", "sem_glsc3_noalloc", "sem_jacobi", "sem_rhs_sine", "sem_cg_default_opts", "sem_cg_solve", "sem_cg_create",
     "sem_cg_start", "sem_cg_iterate", "sem_cg_iterate_timed", "sem_cg_query", "sem_cg_destroy", "sem_launch_count", "sem_last_error",
     "sem_status_string",
 ]
@@ -85,6 +85,7 @@ def load_library(path: str | None = None):
         "sem_ax": [_VP, _I, _I, _VP, _VP, _I, _VP],
         "sem_dssum": [_VP, _I, _VP, _I, _VP],
         "sem_glsc3": [_VP, _I, _VP, _VP, _VP, _VP],
+        "sem_glsc3_noalloc": [_VP, _I, _VP, _VP, _VP, _VP],
         "sem_jacobi": [_VP, _I, _VP, _VP],
         "sem_rhs_sine": [_VP, _I, _I, _I, _I, _VP, _VP],
         "sem_cg_default_opts": [C.POINTER(CgOpts)],
@@ -252,6 +253,15 @@ def sem_glsc3(mesh, prec, a, b, result, stream=None):
     dt = _torch_dtype(prec)
     _check(load_library().sem_glsc3(mesh, prec, _dev(a, dt, n, "a"), _dev(b, dt, n, "b"),
                                     _dev(result, torch.float64, 1, "result"), _stream(stream)))
+
+
+def sem_glsc3_noalloc(mesh, prec, a, b, result, stream=None):
+    """<a, b, c> without any device allocation (static scratch; see include/sem.h)."""
+    import torch
+    n = sem_mesh_get_info(mesh)["n_local"]
+    dt = _torch_dtype(prec)
+    _check(load_library().sem_glsc3_noalloc(mesh, prec, _dev(a, dt, n, "a"), _dev(b, dt, n, "b"),
+                                            _dev(result, torch.float64, 1, "result"), _stream(stream)))
 
 
 def sem_jacobi(mesh, prec, minv, stream=None):
