@@ -96,46 +96,67 @@ def ncu_traffic(kernel_key: str):
 # ---------------------------------------------------------------------------
 
 class ClockSampler:
-    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+    """nvidia-smi samples (every 20 ms) taken while the timed region runs.
+
+    The sampler is started and its first line awaited before the region begins; samples
+    are kept if their host timestamp falls inside [start, stop] of the region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap")
+    REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
 
     def __init__(self, index: int):
         self.index = index
         self.proc = None
+        self.samples = []  # (host time, fields)
+        self.t0 = self.t1 = None
 
     def __enter__(self):
+        import threading
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "20"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True, bufsize=1)
         except OSError:
             self.proc = None
+            self.t0 = time.time()
+            return self
+        first = threading.Event()
+
+        def reader():
+            for ln in self.proc.stdout:
+                if ln.strip():
+                    self.samples.append((time.time(), [x.strip() for x in ln.split(",")]))
+                    first.set()
+
+        self.thread = threading.Thread(target=reader, daemon=True)
+        self.thread.start()
+        first.wait(timeout=10)
+        self.t0 = time.time()
         return self
 
     def __exit__(self, *exc):
-        self.lines = []
+        self.t1 = time.time()
         if self.proc is not None:
-            time.sleep(0.25)
+            time.sleep(0.05)
             self.proc.terminate()
             try:
-                out, _ = self.proc.communicate(timeout=5)
+                self.proc.wait(timeout=5)
             except subprocess.TimeoutExpired:
                 self.proc.kill()
-                out, _ = self.proc.communicate()
-            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+            self.thread.join(timeout=5)
 
     def summary(self):
         sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in getattr(self, "lines", []):
-            f = [x.strip() for x in ln.split(",")]
+        for t, f in self.samples:
+            if self.t0 is None or t < self.t0 or t > self.t1 + 0.03:
+                continue
             try:
                 sm.append(float(f[0]))
                 mx.append(float(f[1]))
             except (ValueError, IndexError):
                 continue
-            for name, val in zip(names, f[4:8]):
+            for name, val in zip(self.REASONS, f[3:7]):
                 if val.lower() == "active":
                     reasons.add(name)
         if not sm:
@@ -392,7 +413,7 @@ def run_gpu(args):
     xo = torch.empty(n, dtype=torch.float64).pin_memory()
     bd = torch.empty_like(b)
     xd = torch.empty_like(b)
-    e2e_iters = args.steps
+    e2e_iters = min(args.steps, 50)
     e_opts = sem.sem_cg_default_opts(rtol=0.0, max_iter=e2e_iters, check_every=e2e_iters, use_graph=1)
     s = torch.cuda.current_stream()
 
@@ -444,7 +465,7 @@ def run_gpu(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="sem", choices=["sem", "reference"])
     args = ap.parse_args()
