@@ -443,6 +443,28 @@ def run_gpu(args):
                    "(work-vector allocation, r0 = b - A x0 and CUDA-graph capture included)",
            "ms_per_step": e2e_ms}
 
+    # ---- config 1: 4^3 mesh (+-0.1h, seed 0), N = 7, sine RHS, Jacobi-CG from zero to 1e-10
+    m1 = BoxMesh(4, 4, 4, jitter=0.1, seed=0)
+    mesh1 = sem.Mesh(NORD, m1.vert_xyz, m1.elem_verts, flags=sem.SEM_MESH_F64_STORED)
+    b1 = torch.empty(mesh1.n, dtype=torch.float64, device="cuda")
+    sem.sem_rhs_sine(mesh1.handle, 1, 1, 1, sem.SEM_F64, b1)
+    x1 = torch.zeros_like(b1)
+    cg_c1 = {}
+    for name, o in (("fp64", sem.sem_cg_default_opts(rtol=1e-10)),
+                    ("mixed_otf", sem.sem_cg_default_opts(rtol=1e-10, mixed=1, inner_rtol=1e-5))):
+        times = []
+        for _ in range(3):  # first solve builds the Jacobi diagonal and the graphs
+            x1.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            r1 = sem.sem_cg_solve(mesh1.handle, b1, x1, o)
+            e1.record(s)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        cg_c1[name] = {"ms": min(times[1:]), "iterations": r1["iters"], "outer": r1["outer_iters"],
+                       "rel_res": r1["rel_res"], "status": sem.sem_status_string(r1["status"])}
+    mesh1.close()
+
     if rank == 0:
         cpu = run_cpu_baseline()
         out = {
@@ -454,12 +476,84 @@ def run_gpu(args):
                        "l2": "inputs larger than L2 (about 1.1 GB of algorithmic traffic per step)",
                        "gflop_s_eq11": flops_eq11(NORD) * n / (ms_step * 1e-3) / 1e9},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "clocks": clk.summary(), "ax": ax,
+            "clocks": clk.summary(), "ax": ax, "cg_config1": cg_c1,
         }
         print(json.dumps(out))
     mesh.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def solve_metrics(sem, mesh, b, x, xyz):
+    """True relative residual sqrt(<r,r,c>/<b,b,c>) with r = b - A x (FP64 operator) and the
+    max nodal error to sin(pi x) sin(pi y) sin(pi z)."""
+    import torch
+    w = torch.empty_like(x)
+    variant = sem.SEM_AX_STORED if mesh.info["flags"] & sem.SEM_MESH_F64_STORED else sem.SEM_AX_OTF
+    sem.sem_ax(mesh.handle, variant, sem.SEM_F64, x, w, assemble=True, n_local=mesh.n)
+    r = b - w
+    rr = torch.zeros(1, dtype=torch.float64, device="cuda")
+    bb = torch.zeros(1, dtype=torch.float64, device="cuda")
+    sem.sem_glsc3(mesh.handle, sem.SEM_F64, r, r, rr)
+    sem.sem_glsc3(mesh.handle, sem.SEM_F64, b, b, bb)
+    n = mesh.n
+    exact = torch.sin(math.pi * xyz[:n]) * torch.sin(math.pi * xyz[n:2 * n]) * torch.sin(math.pi * xyz[2 * n:])
+    return math.sqrt(rr.item() / bb.item()), float(torch.max(torch.abs(x - exact)))
+
+
+def run_solve(args):
+    """Full-solve configuration: 64^3 hexahedra (+-0.15h, seed 2), N = 7, 134,217,728 local
+    points, manufactured sine right-hand side; plain FP64 Jacobi-CG (stored factors) against
+    FP32 on-the-fly inner Jacobi-CG with FP64 iterative refinement, both to 1e-10."""
+    import torch
+    from paper_2108_12188_gb300 import build_lib, sem
+    from synthetic import BoxMesh
+    build_lib.build()
+    sem.load_library()
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    nel = args.nel
+    t0 = time.perf_counter()
+    m = BoxMesh(nel, nel, nel, jitter=JITTER, seed=2)
+    mesh = sem.Mesh(NORD, m.vert_xyz, m.elem_verts, flags=sem.SEM_MESH_F64_STORED)
+    setup_s = time.perf_counter() - t0
+    n = mesh.n
+    b = torch.empty(n, dtype=torch.float64, device="cuda")
+    sem.sem_rhs_sine(mesh.handle, 1, 1, 1, sem.SEM_F64, b)
+    xyz = torch.empty(3 * n, dtype=torch.float64, device="cuda")
+    sem.sem_mesh_coords(mesh.handle, xyz)
+    x = torch.zeros_like(b)
+    mj = torch.empty_like(b)
+    sem.sem_jacobi(mesh.handle, sem.SEM_F64, mj)  # builds the Jacobi diagonal once (set-up)
+    del mj
+    runs = {}
+    configs = {
+        "fp64_cg": sem.sem_cg_default_opts(rtol=1e-10, variant=sem.SEM_AX_STORED, check_every=50),
+        "mixed_otf": sem.sem_cg_default_opts(rtol=1e-10, mixed=1, variant=sem.SEM_AX_STORED,
+                                             inner_variant=sem.SEM_AX_OTF, inner_rtol=args.inner_rtol,
+                                             check_every=50),
+    }
+    for name, opts in configs.items():
+        x.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        res = sem.sem_cg_solve(mesh.handle, b, x, opts)
+        e1.record()
+        e1.synchronize()
+        rel, err = solve_metrics(sem, mesh, b, x, xyz)
+        runs[name] = {"seconds": e0.elapsed_time(e1) / 1e3, "host_seconds": res["time_ms"] / 1e3,
+                      "iterations": res["iters"], "outer_iterations": res["outer_iters"],
+                      "status": sem.sem_status_string(res["status"]), "solver_rel_res": res["rel_res"],
+                      "true_rel_res": rel, "max_err_vs_sine": err}
+    out = {"metric": "CG time to 1e-10 (s)", "value": runs["mixed_otf"]["seconds"], "unit": "s",
+           "higher_is_better": False, "n_gpus": 1, "dtype": "f64 (outer) / f32 (inner)", "data": "synthetic",
+           "config": {"workload": f"{nel}^3 hexahedra on [0,1]^3, jitter +-0.15h (seed 2), N={NORD}, "
+                                  f"{n} local points, sine right-hand side, rtol 1e-10",
+                      "inner_rtol": args.inner_rtol, "mesh_setup_s": setup_s},
+           "fp64_cg": runs["fp64_cg"], "mixed_otf": runs["mixed_otf"],
+           "speedup_mixed_vs_fp64": runs["fp64_cg"]["seconds"] / runs["mixed_otf"]["seconds"]}
+    print(json.dumps(out))
+    mesh.close()
 
 
 def main():
@@ -468,11 +562,17 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="sem", choices=["sem", "reference"])
+    ap.add_argument("--workload", default="ax", choices=["ax", "solve"],
+                    help="ax: the Ax-throughput line (default); solve: the 64^3 full-solve comparison")
+    ap.add_argument("--nel", type=int, default=64, help="elements per direction of the solve workload")
+    ap.add_argument("--inner-rtol", type=float, default=1e-5)
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "solve":
+        run_solve(args)
     else:
         run_gpu(args)
 

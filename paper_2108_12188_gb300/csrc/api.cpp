@@ -796,11 +796,33 @@ extern "C" sem_status sem_cg_solve(sem_mesh m, const double* b, double* x, const
   if (o->mixed) {
     st = solve_mixed(m, b, x, o, res, s);
   } else {
+    // Algorithm 1; when the recursively updated residual meets rtol, CG restarts from x:
+    // the restart recomputes r = b - A x, so the solve ends only when the true residual meets
+    // rtol (long runs let the recursive residual drift away from b - A x).
     sem_cg c = nullptr;
     SEM_TRY(cg_alloc(m, SEM_F64, static_cast<sem_ax_variant>(o->variant), o->precond, o->rtol, o->max_iter,
                      o->use_graph, &c));
     st = cg_start(c, b, x, false, s);
-    if (st == SEM_OK) st = cg_run(c, o->check_every, res, s);
+    int total = 0;
+    for (int restart = 0; st == SEM_OK; ++restart) {
+      sem_cg_result r{};
+      st = cg_query(c, &r, s);
+      if (st != SEM_OK) break;
+      if (r.status != SEM_ERR_BUSY) {  // decided at the (re)start: true residual small, or limit
+        res->status = r.status;
+        res->rel_res = r.rel_res;
+        break;
+      }
+      st = cg_run(c, o->check_every, &r, s);
+      if (st != SEM_OK) break;
+      total += r.iters;
+      res->status = r.status;
+      res->rel_res = r.rel_res;
+      if (r.status != SEM_OK || restart >= 20) break;
+      c->max_iter = o->max_iter - total;
+      st = cg_start(c, b, x, false, s);
+    }
+    res->iters = total;
     cudaStreamSynchronize(s);
     cg_free(c);
   }

@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(NP * NP * ax_epb<NP>())
   }
   const int slot = threadIdx.x / NP2, tid = threadIdx.x % NP2;
   const int i = tid % NP, j = tid / NP;
-  double dot = 0.0;
+  DotAcc<T> dot;
   __syncthreads();
 
   for (int64_t grp = blockIdx.x; grp * EPB < E; grp += gridDim.x) {
@@ -175,13 +175,13 @@ __global__ void __launch_bounds__(NP * NP * ax_epb<NP>())
       if (valid) w[base + k * NP2] = acc;
       if constexpr (CG) {
         const bool interior = i > 0 && i < NP - 1 && j > 0 && j < NP - 1 && k > 0 && k < NP - 1;
-        if (valid && interior) dot += static_cast<double>(rU[k]) * static_cast<double>(acc);
+        if (valid && interior) dot.add(rU[k], acc);
       }
     }
     __syncthreads();
   }
   if constexpr (CG) {
-    const double s = block_sum(dot, sRed);
+    const double s = block_sum(dot.value(), sRed);
     if (threadIdx.x == 0) partials[blockIdx.x] = s;
   }
 }

@@ -26,6 +26,14 @@ __device__ __forceinline__ double weight(const uint8_t* __restrict__ mult, const
   return m == 1u ? 1.0 : __ldg(ctab + m);
 }
 
+// c_i in the vector's type: the FP64 table for FP64 data, its FP32 rounding for FP32 data
+// (exact for multiplicities that are powers of two, as on box meshes).
+template <typename T>
+__device__ __forceinline__ T weight_t(const uint8_t* __restrict__ mult, const double* __restrict__ ctab, int64_t i) {
+  const unsigned m = mult[i];
+  return m == 1u ? T(1) : static_cast<T>(__ldg(ctab + m));
+}
+
 template <typename T>
 __global__ void k_glsc3(int64_t n, const T* __restrict__ a, const T* __restrict__ b, const uint8_t* __restrict__ mult,
                         const double* __restrict__ ctab, double* __restrict__ partials, unsigned int* ticket,
@@ -50,7 +58,7 @@ __global__ void k_cg_init(int64_t n, const T* __restrict__ b, const T* __restric
                           const uint8_t* __restrict__ mult, const double* __restrict__ ctab, CgScalars* st,
                           double* __restrict__ partials) {
   __shared__ double sRed[kThreads / 32];
-  double rz = 0.0, rr = 0.0, bb = 0.0;
+  DotAcc<T> rz, rr, bb;
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const T bi = b[i];
@@ -59,12 +67,12 @@ __global__ void k_cg_init(int64_t n, const T* __restrict__ b, const T* __restric
     r[i] = ri;
     z[i] = zi;
     p[i] = T(0);
-    const double c = weight(mult, ctab, i);
-    rz += c * static_cast<double>(ri) * static_cast<double>(zi);
-    rr += c * static_cast<double>(ri) * static_cast<double>(ri);
-    bb += c * static_cast<double>(bi) * static_cast<double>(bi);
+    const T c = weight_t<T>(mult, ctab, i);
+    rz.add(ri, c * zi);
+    rr.add(ri, c * ri);
+    bb.add(bi, c * bi);
   }
-  const double v[3] = {block_sum(rz, sRed), block_sum(rr, sRed), block_sum(bb, sRed)};
+  const double v[3] = {block_sum(rz.value(), sRed), block_sum(rr.value(), sRed), block_sum(bb.value(), sRed)};
   if (publish_partials<3>(v, partials, &st->ticket[2])) {
     const double srz = sum_partials(partials, gridDim.x, 3, 0, sRed);
     const double srr = sum_partials(partials, gridDim.x, 3, 1, sRed);
@@ -103,7 +111,7 @@ __global__ void k_cg_update(int64_t n, T* __restrict__ x, const T* __restrict__ 
   __shared__ double sRed[kThreads / 32];
   if (st->done) return;
   const T alpha = static_cast<T>(st->alpha);
-  double rz = 0.0, rr = 0.0;
+  DotAcc<T> rz, rr;
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     x[i] += alpha * p[i];
@@ -111,11 +119,11 @@ __global__ void k_cg_update(int64_t n, T* __restrict__ x, const T* __restrict__ 
     const T zi = minv ? minv[i] * ri : ri;
     r[i] = ri;
     z[i] = zi;
-    const double c = weight(mult, ctab, i);
-    rz += c * static_cast<double>(ri) * static_cast<double>(zi);
-    rr += c * static_cast<double>(ri) * static_cast<double>(ri);
+    const T c = weight_t<T>(mult, ctab, i);
+    rz.add(ri, c * zi);
+    rr.add(ri, c * ri);
   }
-  const double v[2] = {block_sum(rz, sRed), block_sum(rr, sRed)};
+  const double v[2] = {block_sum(rz.value(), sRed), block_sum(rr.value(), sRed)};
   if (publish_partials<2>(v, partials, &st->ticket[1])) {
     const double srz = sum_partials(partials, gridDim.x, 2, 0, sRed);
     const double srr = sum_partials(partials, gridDim.x, 2, 1, sRed);

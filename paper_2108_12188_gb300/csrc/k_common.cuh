@@ -72,3 +72,39 @@ __device__ __forceinline__ double sum_partials(const double* partials, int count
 __host__ __device__ constexpr int ceil_div(long long a, long long b) { return static_cast<int>((a + b - 1) / b); }
 
 }  // namespace sem
+
+namespace sem {
+
+// Per-thread accumulator of dot products.
+// FP64 data: plain FP64 fused multiply-adds.
+// FP32 data: each product is formed exactly as a pair of floats (p = x*y, e = fma(x, y, -p))
+// and added to a compensated pair (Knuth's two-sum on the high parts, errors gathered in the
+// low part), a 48-bit accumulation that keeps the FP64 pipe free; value() returns it in FP64
+// and the block and grid sums then continue in FP64.
+template <typename T>
+struct DotAcc;
+
+template <>
+struct DotAcc<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double x, double y) { s = fma(x, y, s); }
+  __device__ __forceinline__ double value() const { return s; }
+};
+
+template <>
+struct DotAcc<float> {
+  float hi = 0.f, lo = 0.f;
+  // round-to-nearest intrinsics: the compiler must not fuse or reorder these steps
+  __device__ __forceinline__ void add(float x, float y) {
+    const float p = __fmul_rn(x, y);
+    const float e = __fmaf_rn(x, y, -p);
+    const float s = __fadd_rn(hi, p);
+    const float bb = __fsub_rn(s, hi);
+    const float t = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(t, e));
+  }
+  __device__ __forceinline__ double value() const { return static_cast<double>(hi) + static_cast<double>(lo); }
+};
+
+}  // namespace sem

@@ -42,7 +42,7 @@ __global__ void k_dssum_cg(int64_t n_seg, const int32_t* __restrict__ off, const
                            double* __restrict__ partials) {
   __shared__ double sRed[kThreads / 32];
   if (st->done) return;
-  double dot = 0.0;
+  DotAcc<T> dot;
   for (int64_t g = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; g < n_seg;
        g += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const int o0 = off[g], o1 = off[g + 1];
@@ -51,9 +51,9 @@ __global__ void k_dssum_cg(int64_t n_seg, const int32_t* __restrict__ off, const
     for (int o = o0 + 1; o < o1; ++o) s += w[idx[o]];
     if (smask[g]) s = T(0);
     for (int o = o0; o < o1; ++o) w[idx[o]] = s;
-    dot += static_cast<double>(p[first]) * static_cast<double>(s);
+    dot.add(p[first], s);
   }
-  const double v[1] = {block_sum(dot, sRed)};
+  const double v[1] = {block_sum(dot.value(), sRed)};
   if (publish_partials<1>(v, partials, &st->ticket[0])) {
     const double a = sum_partials(ax_partials, ax_blocks, 1, 0, sRed);
     const double b = sum_partials(partials, gridDim.x, 1, 0, sRed);
