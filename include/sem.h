@@ -53,7 +53,13 @@ typedef enum {
   SEM_ERR_UNSUPPORTED = 9    /* e.g. polynomial order outside [1, SEM_MAX_N] */
 } sem_status;
 
-typedef enum { SEM_F64 = 0, SEM_F32 = 1 } sem_prec;
+/* SEM_F64: FP64 data and FP64 arithmetic. SEM_F32: FP32 data and arithmetic.
+ * SEM_F64X: FP64 data (double* vectors, FP64 stored factors); the local operator runs in
+ * double-float arithmetic (pairs of floats with error-free products and sums, about 47
+ * significant bits) on the FP32 pipes, which GB300 issues 61 times faster than FP64. Only
+ * sem_ax with SEM_AX_STORED (and the CG options' f64_arith) use it; every other call treats
+ * SEM_F64X like SEM_F64. Values below 2^-126 in magnitude are flushed to zero inside it. */
+typedef enum { SEM_F64 = 0, SEM_F32 = 1, SEM_F64X = 2 } sem_prec;
 
 /* Variants of the local operator A_L (Section 5.1):
  * STORED reads the six geometric factors per point from device memory;
@@ -193,6 +199,7 @@ typedef struct {
   int max_outer;      /* refinement steps limit (mixed) */
   int check_every;    /* iterations between host reads of the device convergence flag (>= 1) */
   int use_graph;      /* 1: replay check_every iterations as one captured CUDA graph */
+  int f64_arith;      /* FP64 operator arithmetic: 0 native FP64, 1 double-float (SEM_F64X; stored variant) */
 } sem_cg_opts;
 
 typedef struct {
@@ -204,13 +211,18 @@ typedef struct {
 } sem_cg_result;
 
 /* Fill opts with defaults: rtol 1e-10, max_iter 100000, Jacobi, STORED FP64,
- * not mixed, inner OTF with inner_rtol 1e-5, max_outer 50, check_every 50, graph on. */
+ * not mixed, inner OTF with inner_rtol 1e-5, max_outer 50, check_every 50, graph on,
+ * native FP64 operator arithmetic. */
 sem_status sem_cg_default_opts(sem_cg_opts* opts_host);
 
 /* Solve A x = b to rtol. b_dev, x_dev: FP64 [n_local]; x_dev holds x0 on entry
  * and the solution on return (also on NOT_CONVERGED / BREAKDOWN). b must be
- * assembled and masked (e.g. from sem_rhs_sine). Blocks the host until done;
- * allocates its work vectors for the duration of the call. */
+ * assembled and masked (e.g. from sem_rhs_sine). The solve ends when the true residual
+ * b - A x meets rtol: FP64 CG restarts from x once its recursively updated residual
+ * converges (so the reported iterations include any restart), and the refinement loop
+ * recomputes b - A x in FP64 every outer step. Blocks the host until done. Work vectors
+ * are allocated on the first call and kept with the mesh for later solves (freed by
+ * sem_mesh_destroy). */
 sem_status sem_cg_solve(sem_mesh mesh, const double* b_dev, double* x_dev, const sem_cg_opts* opts,
                         sem_cg_result* result_host, void* stream);
 

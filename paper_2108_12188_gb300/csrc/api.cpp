@@ -75,11 +75,23 @@ sem_status check_ptr(const void* p, const char* name) {
 }
 
 sem_status check_prec(int prec) {
-  if (prec != SEM_F64 && prec != SEM_F32) return fail(SEM_ERR_ARG, "precision must be SEM_F64 or SEM_F32");
+  if (prec != SEM_F64 && prec != SEM_F32 && prec != SEM_F64X)
+    return fail(SEM_ERR_ARG, "precision must be SEM_F64, SEM_F32 or SEM_F64X");
   return SEM_OK;
 }
 
+void cg_free(sem_cg c);
+
 void free_mesh(sem_mesh m) {
+  if (m->solve_cg64) cg_free(m->solve_cg64);
+  if (m->solve_cg32) cg_free(m->solve_cg32);
+  m->solve_cg64 = m->solve_cg32 = nullptr;
+  dfree(m->ir_w64);
+  dfree(m->ir_r64);
+  dfree(m->ir_r32);
+  dfree(m->ir_d32);
+  dfree(m->ir_st);
+  dfree(m->ir_part);
   dfree(m->coef64);
   dfree(m->coef32);
   dfree(m->G64);
@@ -93,14 +105,18 @@ void free_mesh(sem_mesh m) {
   dfree(m->ctab);
   dfree(m->partials);
   dfree(m->ticket);
+  dfree(m->dev_err);
 }
 
 sem_status launch_ax_any(sem_mesh m, sem_prec prec, sem_ax_variant v, bool cg, AxLaunch a, cudaStream_t s) {
   a.E = m->E;
-  a.coef = prec == SEM_F64 ? static_cast<const void*>(m->coef64) : static_cast<const void*>(m->coef32);
-  a.G = prec == SEM_F64 ? static_cast<const void*>(m->G64) : static_cast<const void*>(m->G32);
+  a.err = m->dev_err;
+  const bool fp64_data = prec != SEM_F32;
+  a.coef = fp64_data ? static_cast<const void*>(m->coef64) : static_cast<const void*>(m->coef32);
+  a.G = fp64_data ? static_cast<const void*>(m->G64) : static_cast<const void*>(m->G32);
   if (v == SEM_AX_STORED && !a.G)
     return fail(SEM_ERR_ARG, "stored factors of this precision were not requested at mesh creation");
+  if (prec == SEM_F64X) return launch_ax_f64x(m->N, v, cg, a, s);
   return prec == SEM_F64 ? launch_ax_f64(m->N, v, cg, a, s) : launch_ax_f32(m->N, v, cg, a, s);
 }
 
@@ -203,6 +219,8 @@ extern "C" sem_status sem_mesh_create(int N, int64_t nv, const double* vert_xyz,
   SEM_STEP(dmalloc(&m->ctab, 256, &acc));
   SEM_STEP(dmalloc(&m->partials, kRedMax, &acc));
   SEM_STEP(dmalloc(&m->ticket, 1, &acc));
+  SEM_STEP(dmalloc(&m->dev_err, 1, &acc));
+  SEM_CSTEP(cudaMemsetAsync(m->dev_err, 0, sizeof(int), s));
   SEM_CSTEP(cudaMemcpyAsync(Xd, X.data(), X.size() * sizeof(double), cudaMemcpyHostToDevice, s));
   SEM_CSTEP(cudaMemcpyAsync(m->seg_off, T.seg_off.data(), T.seg_off.size() * 4, cudaMemcpyHostToDevice, s));
   SEM_CSTEP(cudaMemcpyAsync(m->seg_idx, T.seg_idx.data(), T.seg_idx.size() * 4, cudaMemcpyHostToDevice, s));
@@ -300,9 +318,10 @@ extern "C" sem_status sem_mesh_geometry(sem_mesh m, sem_prec prec, void* G, void
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int* bad = nullptr;
   SEM_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&bad), sizeof(int), s));
-  sem_status st = launch_geometry(m->N, m->E, m->coef64, prec == SEM_F64 ? static_cast<double*>(G) : nullptr,
+  const bool f64 = prec != SEM_F32;
+  sem_status st = launch_geometry(m->N, m->E, m->coef64, f64 ? static_cast<double*>(G) : nullptr,
                                   prec == SEM_F32 ? static_cast<float*>(G) : nullptr,
-                                  prec == SEM_F64 ? static_cast<double*>(B) : nullptr,
+                                  f64 ? static_cast<double*>(B) : nullptr,
                                   prec == SEM_F32 ? static_cast<float*>(B) : nullptr, bad, s);
   cudaFreeAsync(bad, s);
   return st;
@@ -320,7 +339,7 @@ extern "C" sem_status sem_scatter(sem_mesh m, sem_prec prec, const void* ug, voi
   sem_status st = SEM_OK;
   cudaError_t e = cudaMemcpyAsync(gd, g32.data(), g32.size() * 4, cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) st = cuda_fail(e, "cudaMemcpyAsync (numbering)");
-  if (st == SEM_OK) st = launch_scatter(prec, m->n, gd, ug, ul, s);
+  if (st == SEM_OK) st = launch_scatter(data_prec(prec), m->n, gd, ug, ul, s);
   // the host copy must outlive the transfer
   e = cudaStreamSynchronize(s);
   if (st == SEM_OK && e != cudaSuccess) st = cuda_fail(e, "cudaStreamSynchronize");
@@ -341,7 +360,7 @@ extern "C" sem_status sem_ax(sem_mesh m, sem_ax_variant v, sem_prec prec, const 
   a.u = u;
   a.w = w;
   SEM_TRY(launch_ax_any(m, prec, v, false, a, s));
-  if (assemble) SEM_TRY(launch_dssum(prec, m->n_seg, m->seg_off, m->seg_idx, m->seg_mask, w, 1, s));
+  if (assemble) SEM_TRY(launch_dssum(data_prec(prec), m->n_seg, m->seg_off, m->seg_idx, m->seg_mask, w, 1, s));
   return SEM_OK;
 }
 
@@ -349,7 +368,7 @@ extern "C" sem_status sem_dssum(sem_mesh m, sem_prec prec, void* u, int apply_ma
   SEM_TRY(check_mesh(m));
   SEM_TRY(check_prec(prec));
   SEM_TRY(check_ptr(u, "u_dev"));
-  return launch_dssum(prec, m->n_seg, m->seg_off, m->seg_idx, m->seg_mask, u, apply_mask,
+  return launch_dssum(data_prec(prec), m->n_seg, m->seg_off, m->seg_idx, m->seg_mask, u, apply_mask,
                       static_cast<cudaStream_t>(stream));
 }
 
@@ -360,7 +379,7 @@ extern "C" sem_status sem_glsc3(sem_mesh m, sem_prec prec, const void* a, const 
   SEM_TRY(check_ptr(a, "a_dev"));
   SEM_TRY(check_ptr(b, "b_dev"));
   if (!result) return fail(SEM_ERR_ARG, "result_dev is null");
-  return launch_glsc3(prec, m->n, a, b, m->mult, m->ctab, m->partials, m->ticket, result,
+  return launch_glsc3(data_prec(prec), m->n, a, b, m->mult, m->ctab, m->partials, m->ticket, result,
                       static_cast<cudaStream_t>(stream));
 }
 
@@ -370,8 +389,9 @@ extern "C" sem_status sem_jacobi(sem_mesh m, sem_prec prec, void* minv, void* st
   SEM_TRY(check_ptr(minv, "minv_dev"));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   SEM_TRY(ensure_jacobi(m, s));
-  const size_t bytes = m->n * (prec == SEM_F64 ? sizeof(double) : sizeof(float));
-  SEM_CUDA_TRY(cudaMemcpyAsync(minv, prec == SEM_F64 ? static_cast<void*>(m->minv64) : static_cast<void*>(m->minv32),
+  const bool f32 = prec == SEM_F32;
+  const size_t bytes = m->n * (f32 ? sizeof(float) : sizeof(double));
+  SEM_CUDA_TRY(cudaMemcpyAsync(minv, f32 ? static_cast<void*>(m->minv32) : static_cast<void*>(m->minv64),
                                bytes, cudaMemcpyDeviceToDevice, s));
   return SEM_OK;
 }
@@ -420,7 +440,7 @@ namespace {
 
 const void* minv_of(sem_cg c) {
   if (!c->precond) return nullptr;
-  return c->prec == SEM_F64 ? static_cast<const void*>(c->m->minv64) : static_cast<const void*>(c->m->minv32);
+  return c->prec == SEM_F32 ? static_cast<const void*>(c->m->minv32) : static_cast<const void*>(c->m->minv64);
 }
 
 void cg_free(sem_cg c) {
@@ -436,8 +456,10 @@ void cg_free(sem_cg c) {
 sem_status cg_alloc(sem_mesh m, sem_prec prec, sem_ax_variant v, int precond, double rtol, int max_iter, int use_graph,
                     sem_cg* out) {
   *out = nullptr;
-  if (v == SEM_AX_STORED && !(prec == SEM_F64 ? m->G64 != nullptr : m->G32 != nullptr))
+  if (v == SEM_AX_STORED && !(prec == SEM_F32 ? m->G32 != nullptr : m->G64 != nullptr))
     return fail(SEM_ERR_ARG, "stored factors of this precision were not requested at mesh creation");
+  if (prec == SEM_F64X && v != SEM_AX_STORED)
+    return fail(SEM_ERR_UNSUPPORTED, "double-float FP64 arithmetic runs the stored-factor variant only");
   sem_cg c = new sem_cg_s();
   c->m = m;
   c->prec = prec;
@@ -446,7 +468,7 @@ sem_status cg_alloc(sem_mesh m, sem_prec prec, sem_ax_variant v, int precond, do
   c->rtol = rtol;
   c->max_iter = max_iter;
   c->use_graph = use_graph;
-  const size_t es = prec == SEM_F64 ? sizeof(double) : sizeof(float);
+  const size_t es = prec == SEM_F32 ? sizeof(float) : sizeof(double);
   sem_status st = SEM_OK;
   for (void** q : {&c->r, &c->z, &c->p, &c->w}) {
     cudaError_t e = cudaMalloc(q, m->n * es);
@@ -477,6 +499,22 @@ sem_status cg_alloc(sem_mesh m, sem_prec prec, sem_ax_variant v, int precond, do
   return SEM_OK;
 }
 
+// The solver handle kept on the mesh for sem_cg_solve: reused while the variant,
+// preconditioner and graph setting are unchanged (rtol and max_iter are per solve).
+sem_status cached_cg(sem_mesh m, sem_prec prec, sem_ax_variant v, int precond, int use_graph, double rtol,
+                     int max_iter, sem_cg* out) {
+  sem_cg& slot = prec == SEM_F32 ? m->solve_cg32 : m->solve_cg64;
+  if (slot && (slot->prec != prec || slot->variant != v || slot->precond != precond || slot->use_graph != use_graph)) {
+    cg_free(slot);
+    slot = nullptr;
+  }
+  if (!slot) SEM_TRY(cg_alloc(m, prec, v, precond, rtol, max_iter, use_graph, &slot));
+  slot->rtol = rtol;
+  slot->max_iter = max_iter;
+  *out = slot;
+  return SEM_OK;
+}
+
 // Host-side state reset + r0 = b - A x0, z0, rho0 (device).
 sem_status cg_start(sem_cg c, const void* b, void* x, bool x0_is_zero, cudaStream_t s) {
   sem_mesh m = c->m;
@@ -494,10 +532,10 @@ sem_status cg_start(sem_cg c, const void* b, void* x, bool x0_is_zero, cudaStrea
     a.u = x;
     a.w = c->w;
     SEM_TRY(launch_ax_any(m, c->prec, c->variant, false, a, s));
-    SEM_TRY(launch_dssum(c->prec, m->n_seg, m->seg_off, m->seg_idx, m->seg_mask, c->w, 1, s));
+    SEM_TRY(launch_dssum(data_prec(c->prec), m->n_seg, m->seg_off, m->seg_idx, m->seg_mask, c->w, 1, s));
     ax0 = c->w;
   }
-  SEM_TRY(launch_cg_init(c->prec, m->n, b, ax0, c->r, c->z, c->p, minv_of(c), m->mult, m->ctab, c->st, c->init_part,
+  SEM_TRY(launch_cg_init(data_prec(c->prec), m->n, b, ax0, c->r, c->z, c->p, minv_of(c), m->mult, m->ctab, c->st, c->init_part,
                          s));
   // the host struct is reused by query: make sure the copy above has been consumed
   SEM_CUDA_TRY(cudaStreamSynchronize(s));
@@ -516,9 +554,9 @@ sem_status cg_enqueue_iteration(sem_cg c, cudaStream_t s) {
   a.partials = c->ax_part;
   a.grid_out = &c->ax_blocks;
   SEM_TRY(launch_ax_any(m, c->prec, c->variant, true, a, s));
-  SEM_TRY(launch_dssum_cg(c->prec, m->n_seg, m->seg_off, m->seg_idx, m->seg_mask, c->w, c->p, c->st, c->ax_part,
+  SEM_TRY(launch_dssum_cg(data_prec(c->prec), m->n_seg, m->seg_off, m->seg_idx, m->seg_mask, c->w, c->p, c->st, c->ax_part,
                           c->ax_blocks, c->gs_part, s));
-  SEM_TRY(launch_cg_update(c->prec, m->n, c->x, c->p, c->r, c->w, c->z, minv_of(c), m->mult, m->ctab, c->st,
+  SEM_TRY(launch_cg_update(data_prec(c->prec), m->n, c->x, c->p, c->r, c->w, c->z, minv_of(c), m->mult, m->ctab, c->st,
                            c->upd_part, s));
   return SEM_OK;
 }
@@ -577,7 +615,7 @@ sem_status check_opts(const sem_cg_opts* o) {
   if (!o) return fail(SEM_ERR_ARG, "opts is null");
   if (!(o->rtol >= 0) || o->max_iter < 0 || o->check_every < 1 || (o->precond != 0 && o->precond != 1) ||
       (o->variant != SEM_AX_STORED && o->variant != SEM_AX_OTF) ||
-      (o->inner_variant != SEM_AX_STORED && o->inner_variant != SEM_AX_OTF))
+      (o->inner_variant != SEM_AX_STORED && o->inner_variant != SEM_AX_OTF) || (o->f64_arith != 0 && o->f64_arith != 1))
     return fail(SEM_ERR_ARG, "invalid CG options");
   if (o->mixed && (!(o->inner_rtol > 0 && o->inner_rtol < 1) || o->max_outer < 1))
     return fail(SEM_ERR_ARG, "mixed precision needs 0 < inner_rtol < 1 and max_outer >= 1");
@@ -603,27 +641,29 @@ sem_status cg_run(sem_cg c, int check_every, sem_cg_result* r, cudaStream_t s) {
 sem_status solve_mixed(sem_mesh m, const double* b, double* x, const sem_cg_opts* o, sem_cg_result* res,
                        cudaStream_t s) {
   sem_cg inner = nullptr;
-  SEM_TRY(cg_alloc(m, SEM_F32, static_cast<sem_ax_variant>(o->inner_variant), o->precond, o->inner_rtol,
-                   o->max_iter, o->use_graph, &inner));
-  std::unique_ptr<sem_cg_s, void (*)(sem_cg)> inner_guard(inner, cg_free);
-  double* w64 = nullptr;
-  double* r64 = nullptr;
-  float* r32 = nullptr;
-  float* d32 = nullptr;
-  CgScalars* ost = nullptr;
-  double* opart = nullptr;
-  auto release = [&] {
-    for (void* q : {static_cast<void*>(w64), static_cast<void*>(r64), static_cast<void*>(r32),
-                    static_cast<void*>(d32), static_cast<void*>(ost), static_cast<void*>(opart)})
-      if (q) cudaFree(q);
-  };
-  sem_status st = SEM_OK;
-  if ((st = dmalloc(&w64, m->n, nullptr)) != SEM_OK || (st = dmalloc(&r64, m->n, nullptr)) != SEM_OK ||
-      (st = dmalloc(&r32, m->n, nullptr)) != SEM_OK || (st = dmalloc(&d32, m->n, nullptr)) != SEM_OK ||
-      (st = dmalloc(&ost, 1, nullptr)) != SEM_OK || (st = dmalloc(&opart, 2 * kRedMax, nullptr)) != SEM_OK) {
-    release();
-    return st;
+  SEM_TRY(cached_cg(m, SEM_F32, static_cast<sem_ax_variant>(o->inner_variant), o->precond, o->use_graph,
+                    o->inner_rtol, o->max_iter, &inner));
+  if (!m->ir_part) {
+    sem_status a = SEM_OK;
+    if ((a = dmalloc(&m->ir_w64, m->n, nullptr)) != SEM_OK || (a = dmalloc(&m->ir_r64, m->n, nullptr)) != SEM_OK ||
+        (a = dmalloc(&m->ir_r32, m->n, nullptr)) != SEM_OK || (a = dmalloc(&m->ir_d32, m->n, nullptr)) != SEM_OK ||
+        (a = dmalloc(&m->ir_st, 1, nullptr)) != SEM_OK || (a = dmalloc(&m->ir_part, 2 * kRedMax, nullptr)) != SEM_OK) {
+      dfree(m->ir_w64);
+      dfree(m->ir_r64);
+      dfree(m->ir_r32);
+      dfree(m->ir_d32);
+      dfree(m->ir_st);
+      dfree(m->ir_part);
+      return a;
+    }
   }
+  double* w64 = m->ir_w64;
+  double* r64 = m->ir_r64;
+  float* r32 = m->ir_r32;
+  float* d32 = m->ir_d32;
+  CgScalars* ost = m->ir_st;
+  double* opart = m->ir_part;
+  sem_status st = SEM_OK;
   CgScalars oinit{};
   oinit.rtol2 = o->rtol * o->rtol;
   int total_inner = 0, outer = 0;
@@ -633,7 +673,9 @@ sem_status solve_mixed(sem_mesh m, const double* b, double* x, const sem_cg_opts
     AxLaunch a{};
     a.u = x;
     a.w = w64;
-    if ((st = launch_ax_any(m, SEM_F64, static_cast<sem_ax_variant>(o->variant), false, a, s)) != SEM_OK) break;
+    if ((st = launch_ax_any(m, o->f64_arith ? SEM_F64X : SEM_F64, static_cast<sem_ax_variant>(o->variant), false, a,
+                            s)) != SEM_OK)
+      break;
     if ((st = launch_dssum(SEM_F64, m->n_seg, m->seg_off, m->seg_idx, m->seg_mask, w64, 1, s)) != SEM_OK) break;
     cudaError_t e = cudaMemcpyAsync(ost, &oinit, sizeof(CgScalars), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) { st = cuda_fail(e, "cudaMemcpyAsync"); break; }
@@ -667,7 +709,6 @@ sem_status solve_mixed(sem_mesh m, const double* b, double* x, const sem_cg_opts
   }
   res->iters = total_inner;
   res->outer_iters = outer;
-  release();
   return st;
 }
 
@@ -686,6 +727,7 @@ extern "C" sem_status sem_cg_default_opts(sem_cg_opts* o) {
   o->max_outer = 50;
   o->check_every = 50;
   o->use_graph = 1;
+  o->f64_arith = 0;
   return SEM_OK;
 }
 
@@ -695,8 +737,8 @@ extern "C" sem_status sem_cg_create(sem_mesh m, const sem_cg_opts* o, sem_cg* ou
   SEM_TRY(check_mesh(m));
   SEM_TRY(check_opts(o));
   if (o->mixed) return fail(SEM_ERR_ARG, "the stateful CG handle runs FP64 CG only (mixed=0)");
-  return cg_alloc(m, SEM_F64, static_cast<sem_ax_variant>(o->variant), o->precond, o->rtol, o->max_iter, o->use_graph,
-                  out);
+  return cg_alloc(m, o->f64_arith ? SEM_F64X : SEM_F64, static_cast<sem_ax_variant>(o->variant), o->precond, o->rtol,
+                  o->max_iter, o->use_graph, out);
 }
 
 extern "C" sem_status sem_cg_start(sem_cg c, const double* b, double* x, void* stream) {
@@ -744,11 +786,11 @@ extern "C" sem_status sem_cg_iterate_timed(sem_cg c, int k, double* total_ms, do
     st = launch_ax_any(m, c->prec, c->variant, true, a, s);
     cudaEventRecord(ev[3 * q + 1], s);
     if (st == SEM_OK)
-      st = launch_dssum_cg(c->prec, m->n_seg, m->seg_off, m->seg_idx, m->seg_mask, c->w, c->p, c->st, c->ax_part,
+      st = launch_dssum_cg(data_prec(c->prec), m->n_seg, m->seg_off, m->seg_idx, m->seg_mask, c->w, c->p, c->st, c->ax_part,
                            c->ax_blocks, c->gs_part, s);
     cudaEventRecord(ev[3 * q + 2], s);
     if (st == SEM_OK)
-      st = launch_cg_update(c->prec, m->n, c->x, c->p, c->r, c->w, c->z, minv_of(c), m->mult, m->ctab, c->st,
+      st = launch_cg_update(data_prec(c->prec), m->n, c->x, c->p, c->r, c->w, c->z, minv_of(c), m->mult, m->ctab, c->st,
                             c->upd_part, s);
     cudaEventRecord(ev[3 * q + 3], s);
   }
@@ -800,8 +842,8 @@ extern "C" sem_status sem_cg_solve(sem_mesh m, const double* b, double* x, const
     // the restart recomputes r = b - A x, so the solve ends only when the true residual meets
     // rtol (long runs let the recursive residual drift away from b - A x).
     sem_cg c = nullptr;
-    SEM_TRY(cg_alloc(m, SEM_F64, static_cast<sem_ax_variant>(o->variant), o->precond, o->rtol, o->max_iter,
-                     o->use_graph, &c));
+    SEM_TRY(cached_cg(m, o->f64_arith ? SEM_F64X : SEM_F64, static_cast<sem_ax_variant>(o->variant), o->precond,
+                      o->use_graph, o->rtol, o->max_iter, &c));
     st = cg_start(c, b, x, false, s);
     int total = 0;
     for (int restart = 0; st == SEM_OK; ++restart) {
@@ -824,7 +866,6 @@ extern "C" sem_status sem_cg_solve(sem_mesh m, const double* b, double* x, const
     }
     res->iters = total;
     cudaStreamSynchronize(s);
-    cg_free(c);
   }
   res->time_ms = now_ms() - t0;
   if (st != SEM_OK) {

@@ -53,7 +53,7 @@ template <int NP, typename T, bool OTF, bool CG>
 __global__ void __launch_bounds__(NP * NP * ax_epb<NP>())
     k_ax(const __grid_constant__ GllParam<NP, T> tab, int64_t E, const T* __restrict__ u, T* __restrict__ w,
          const T* __restrict__ G, const T* __restrict__ coef, const T* __restrict__ z, T* __restrict__ p,
-         const CgScalars* __restrict__ st, double* __restrict__ partials) {
+         CgScalars* __restrict__ st, double* __restrict__ partials) {
   constexpr int NP2 = NP * NP, P = NP2 * NP, EPB = ax_epb<NP>();
   __shared__ T sD[NP2];
   __shared__ T sXi[NP], sW[NP];

@@ -77,7 +77,17 @@ struct sem_mesh_s {
   double* ctab = nullptr;     // [256] exact reciprocals 1/m (weights c = 1/multiplicity)
   double* partials = nullptr; // reduction scratch [kRedMax] for sem_glsc3
   unsigned int* ticket = nullptr;
+  int* dev_err = nullptr;     // device error word written by kernels whose bounded waits ran out
   size_t device_bytes = 0;
+  // work space of sem_cg_solve, kept between solves (freed with the mesh)
+  sem_cg solve_cg64 = nullptr;      // FP64 CG handle
+  sem_cg solve_cg32 = nullptr;      // FP32 inner CG handle (mixed precision)
+  double* ir_w64 = nullptr;         // refinement: A x, residual (FP64), residual and correction (FP32)
+  double* ir_r64 = nullptr;
+  float* ir_r32 = nullptr;
+  float* ir_d32 = nullptr;
+  sem::CgScalars* ir_st = nullptr;
+  double* ir_part = nullptr;
 };
 
 namespace sem {
@@ -95,9 +105,13 @@ struct AxLaunch {
   CgScalars* st;
   double* partials;   // [gridDim.x] interior partial dots
   int* grid_out;      // receives gridDim.x used
+  int* err;           // device error word (bounded waits that ran out write SEM_ERR_TIMEOUT)
 };
 sem_status launch_ax_f64(int N, sem_ax_variant v, bool cg_mode, const AxLaunch& a, cudaStream_t s);
 sem_status launch_ax_f32(int N, sem_ax_variant v, bool cg_mode, const AxLaunch& a, cudaStream_t s);
+sem_status launch_ax_f64x(int N, sem_ax_variant v, bool cg_mode, const AxLaunch& a, cudaStream_t s);
+// element type of a precision's data: FP64 for SEM_F64 and SEM_F64X
+inline sem_prec data_prec(sem_prec p) { return p == SEM_F32 ? SEM_F32 : SEM_F64; }
 
 // element geometry (k_mesh.cu)
 sem_status launch_coefficients(int64_t E, const double* X, double* coef64, float* coef32, cudaStream_t s);

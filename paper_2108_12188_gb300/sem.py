@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_PKG, "libsem.so")
 
 SEM_OK, SEM_ERR_ARG, SEM_ERR_MESH, SEM_ERR_OOM, SEM_ERR_CUDA = 0, 1, 2, 3, 4
 SEM_ERR_NOT_CONVERGED, SEM_ERR_BREAKDOWN, SEM_ERR_TIMEOUT, SEM_ERR_BUSY, SEM_ERR_UNSUPPORTED = 5, 6, 7, 8, 9
-SEM_F64, SEM_F32 = 0, 1
+SEM_F64, SEM_F32, SEM_F64X = 0, 1, 2
 SEM_AX_STORED, SEM_AX_OTF = 0, 1
 SEM_MESH_F64_STORED, SEM_MESH_F32_STORED = 1, 2
 SEM_MAX_N = 11
@@ -47,7 +47,7 @@ class MeshInfo(C.Structure):
 class CgOpts(C.Structure):
     _fields_ = [("rtol", C.c_double), ("max_iter", C.c_int), ("precond", C.c_int), ("variant", C.c_int),
                 ("mixed", C.c_int), ("inner_variant", C.c_int), ("inner_rtol", C.c_double),
-                ("max_outer", C.c_int), ("check_every", C.c_int), ("use_graph", C.c_int)]
+                ("max_outer", C.c_int), ("check_every", C.c_int), ("use_graph", C.c_int), ("f64_arith", C.c_int)]
 
 
 class CgResult(C.Structure):
@@ -145,7 +145,7 @@ def _dev(t, dtype=None, numel=None, name="tensor"):
 
 def _torch_dtype(prec):
     import torch
-    return torch.float64 if prec == SEM_F64 else torch.float32
+    return torch.float32 if prec == SEM_F32 else torch.float64
 
 
 # ---------------------------------------------------------------------------

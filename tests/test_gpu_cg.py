@@ -51,11 +51,13 @@ def _solve(sem, mesh, prob, opts):
     return res, x.cpu().numpy()
 
 
-@pytest.mark.parametrize("variant,use_graph,check_every", [(0, 1, 50), (1, 1, 17), (0, 0, 1)],
-                         ids=["stored-graph", "otf-graph", "stored-eager"])
-def test_cg_fp64_matches_oracle(sem, c1, variant, use_graph, check_every):
+@pytest.mark.parametrize("variant,use_graph,check_every,f64_arith", [(0, 1, 50, 0), (1, 1, 17, 0), (0, 0, 1, 0),
+                                                                     (0, 1, 50, 1)],
+                         ids=["stored-graph", "otf-graph", "stored-eager", "stored-doublefloat"])
+def test_cg_fp64_matches_oracle(sem, c1, variant, use_graph, check_every, f64_arith):
     m, prob, b, ref, mesh = c1
-    opts = sem.sem_cg_default_opts(rtol=1e-10, variant=variant, use_graph=use_graph, check_every=check_every)
+    opts = sem.sem_cg_default_opts(rtol=1e-10, variant=variant, use_graph=use_graph, check_every=check_every,
+                                   f64_arith=f64_arith)
     res, x = _solve(sem, mesh, prob, opts)
     assert res["status"] == sem.SEM_OK, res
     assert abs(res["iters"] - ref.iterations) <= max(1, 0.02 * ref.iterations), (res["iters"], ref.iterations)
@@ -65,10 +67,12 @@ def test_cg_fp64_matches_oracle(sem, c1, variant, use_graph, check_every):
     assert abs(e_gpu - e_ref) <= 5e-4 * e_ref, (e_gpu, e_ref)
 
 
-@pytest.mark.parametrize("inner_variant", [1, 0], ids=["inner-otf", "inner-stored"])
-def test_cg_mixed_precision(sem, c1, inner_variant):
+@pytest.mark.parametrize("inner_variant,f64_arith", [(1, 0), (0, 0), (1, 1)],
+                         ids=["inner-otf", "inner-stored", "inner-otf-outer-doublefloat"])
+def test_cg_mixed_precision(sem, c1, inner_variant, f64_arith):
     m, prob, b, ref, mesh = c1
-    opts = sem.sem_cg_default_opts(rtol=1e-10, mixed=1, inner_variant=inner_variant, inner_rtol=1e-4)
+    opts = sem.sem_cg_default_opts(rtol=1e-10, mixed=1, inner_variant=inner_variant, inner_rtol=1e-4,
+                                   f64_arith=f64_arith)
     res, x = _solve(sem, mesh, prob, opts)
     assert res["status"] == sem.SEM_OK, res
     assert res["outer_iters"] >= 2
