@@ -576,14 +576,88 @@ def run_solve(args):
     mesh.close()
 
 
+def run_serve(args):
+    """Serving configuration: a stream of Poisson-solve requests with Poisson arrivals; each is a
+    box mesh n^3 with n ~ U{8..40}, N ~ U{5,7,9}, interior jitter +-0.1h, right-hand side
+    sin(a pi x) sin(b pi y) sin(c pi z) with a, b, c ~ U{1,2,3}, tolerance 1e-8, FP32 inner CG
+    with FP64 refinement; admission by a 100 GB device-memory budget. Reports p50/p99 latency
+    (submit -> solution in host memory) and solves/s per arrival rate."""
+    import numpy as np
+    import torch
+    from paper_2108_12188_gb300 import build_lib, sem
+    from synthetic import BoxMesh, splitmix64
+    build_lib.build()
+    sem.load_library()
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    opts = sem.sem_cg_default_opts(rtol=1e-8, mixed=1, variant=sem.SEM_AX_OTF, inner_variant=sem.SEM_AX_OTF,
+                                   inner_rtol=1e-5, check_every=25)
+    budget = 100 * 10 ** 9
+    rates = [float(r) for r in args.rates.split(",")]
+    out_rates = []
+    total_points = 0
+    for ri, lam in enumerate(rates):
+        R = args.requests
+        draws = splitmix64(1000 + ri, 0, 6 * R)
+        srv = sem.sem_server_create(budget, args.slots)
+        rng_t = np.random.default_rng(2000 + ri)
+        arrivals = np.cumsum(rng_t.exponential(1.0 / lam, size=R))
+        tickets, done, pending = [], {}, set()
+        t0 = time.perf_counter()
+        q = 0
+        while len(done) < R:
+            now = time.perf_counter() - t0
+            while q < R and arrivals[q] <= now:
+                d = draws[6 * q: 6 * q + 6]
+                nel = 8 + int(d[0] % 33)
+                N = (5, 7, 9)[int(d[1] % 3)]
+                sine = tuple(1 + int(v % 3) for v in d[2:5])
+                mesh = BoxMesh(nel, nel, nel, jitter=0.1, seed=int(d[5] % (1 << 31)))
+                t = sem.sem_server_submit(srv, N, mesh.vert_xyz, mesh.elem_verts, sine, opts)
+                tickets.append((t, nel, N))
+                pending.add(t)
+                q += 1
+            for t in list(pending):
+                r = sem.sem_server_poll(srv, t, want_x=False)
+                if r is not None:
+                    sem.sem_server_poll(srv, t, want_x=True)  # take the solution, release the ticket
+                    done[t] = r[0]
+                    pending.discard(t)
+            time.sleep(0.002)
+        wall = time.perf_counter() - t0
+        sem.sem_server_destroy(srv)
+        lat = np.array([done[t]["latency_ms"] for t, _, _ in tickets])
+        ok = sum(1 for t, _, _ in tickets if done[t]["status"] == sem.SEM_OK)
+        pts = sum(done[t]["n_local"] for t, _, _ in tickets)
+        total_points += pts
+        out_rates.append({"arrival_rate_per_s": lam, "requests": R, "ok": ok,
+                          "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                          "mean_ms": float(lat.mean()), "solves_per_s": R / wall, "wall_s": wall,
+                          "mean_queue_ms": float(np.mean([done[t]["queue_ms"] for t, _, _ in tickets])),
+                          "mean_setup_ms": float(np.mean([done[t]["setup_ms"] for t, _, _ in tickets])),
+                          "mean_solve_ms": float(np.mean([done[t]["solve_ms"] for t, _, _ in tickets])),
+                          "local_points": int(pts)})
+    main = out_rates[-1]
+    print(json.dumps({
+        "metric": "served p50/p99 latency (ms)", "value": main["p50_ms"], "unit": "ms", "higher_is_better": False,
+        "n_gpus": 1, "dtype": "f64 (outer) / f32 (inner)", "data": "synthetic",
+        "config": {"workload": "solve requests: n^3 box, n~U{8..40}, N~U{5,7,9}, jitter 0.1h, sine RHS a,b,c~U{1,2,3}, "
+                               "rtol 1e-8 mixed precision, Poisson arrivals, 100 GB admission budget",
+                   "requests_per_rate": args.requests, "slots": args.slots},
+        "p99_ms": main["p99_ms"], "rates": out_rates}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="sem", choices=["sem", "reference"])
-    ap.add_argument("--workload", default="ax", choices=["ax", "solve"],
-                    help="ax: the Ax-throughput line (default); solve: the 64^3 full-solve comparison")
+    ap.add_argument("--workload", default="ax", choices=["ax", "solve", "serve"],
+                    help="ax: the Ax-throughput line (default); solve: the 64^3 full-solve comparison; "
+                         "serve: the request-stream latency measurement")
+    ap.add_argument("--requests", type=int, default=1000, help="requests per arrival rate (serve)")
+    ap.add_argument("--rates", default="1,2,4", help="arrival rates in requests/s (serve)")
+    ap.add_argument("--slots", type=int, default=16, help="concurrent solves (serve)")
     ap.add_argument("--nel", type=int, default=64, help="elements per direction of the solve workload")
     ap.add_argument("--inner-rtol", type=float, default=1e-5)
     args = ap.parse_args()
@@ -593,6 +667,8 @@ def main():
         run_reference(args)
     elif args.workload == "solve":
         run_solve(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_gpu(args)
 

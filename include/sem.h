@@ -108,7 +108,9 @@ typedef struct {
 sem_status sem_mesh_create(int N, int64_t num_vertices, const double* vert_xyz_host, int64_t E,
                            const int64_t* elem_verts_host, const uint8_t* dirichlet_vertex_flags_host,
                            unsigned flags, void* stream, sem_mesh* out);
-sem_status sem_mesh_destroy(sem_mesh mesh); /* NULL is a no-op; synchronises the device */
+/* Releases the mesh. Waits for the streams the mesh was used on (not the whole device),
+ * then frees its memory stream-ordered; those streams must still exist. NULL is a no-op. */
+sem_status sem_mesh_destroy(sem_mesh mesh);
 /* Host-only: the numbering and mask sem_mesh_create would build (Section 3.1's Q), without
  * touching a GPU. glo_num_host [E*(N+1)^3] int64, mask_host [E*(N+1)^3] uint8 (either may be
  * NULL), n_glob_host receives the number of global nodes. Same validation as sem_mesh_create
@@ -245,7 +247,54 @@ sem_status sem_cg_query(sem_cg cg, sem_cg_result* result_host, void* stream);
  * total_ms_host and the mean duration of each kernel in kernel_ms_host[3]. */
 sem_status sem_cg_iterate_timed(sem_cg cg, int k, double* total_ms_host, double* kernel_ms_host, void* stream);
 
-sem_status sem_cg_destroy(sem_cg cg);
+sem_status sem_cg_destroy(sem_cg cg); /* waits for the streams the handle was used on */
+
+/* ---- Solve server (continuous batching of Poisson solves) ----
+ * Requests are queued on submit and admitted first in, first out when a worker slot is free
+ * and the device memory the request needs (estimated from E, N and its options) fits in the
+ * budget; each admitted request runs on its own CUDA stream (mesh set-up, right-hand side,
+ * sem_cg_solve, copy of x to host memory, release), so admitted solves overlap on the GPU and
+ * new requests enter as earlier ones finish. A request's result does not depend on the other
+ * requests (same launches and fixed-order reductions as alone). A failing request (invalid
+ * mesh, non-convergence) reports its status alone. The server uses the device current at
+ * sem_server_create. The paper has no server; this serves its solver (Algorithm 1). */
+typedef struct sem_server_s* sem_server;
+
+typedef struct {
+  int N;                                      /* polynomial order */
+  int64_t num_vertices;
+  const double* vert_xyz_host;                /* [num_vertices][3], copied at submit */
+  int64_t E;
+  const int64_t* elem_verts_host;             /* [E][8], as in sem_mesh_create, copied at submit */
+  const uint8_t* dirichlet_vertex_flags_host; /* NULL or [num_vertices], copied at submit */
+  int sine[3];                                /* right-hand side of sem_rhs_sine with wave numbers (a, b, c) */
+  sem_cg_opts opts;                           /* solver options (mixed precision, tolerance, ...) */
+} sem_request;
+
+typedef struct {
+  int status;         /* sem_status of the request; SEM_ERR_BUSY while queued or running */
+  int64_t n_local;    /* length of the solution vector */
+  sem_cg_result cg;   /* solver result */
+  double queue_ms;    /* submit -> admitted */
+  double setup_ms;    /* mesh, right-hand side */
+  double solve_ms;    /* CG and copy of x to host memory */
+  double latency_ms;  /* submit -> solution available in host memory */
+} sem_server_result;
+
+/* hbm_budget_bytes: device memory the admitted requests may hold together; max_slots: solves
+ * running at once (worker threads). */
+sem_status sem_server_create(size_t hbm_budget_bytes, int max_slots, sem_server* out);
+/* Copies the request and queues it; never waits for the GPU. SEM_ERR_ARG if the request alone
+ * needs more than the budget. */
+sem_status sem_server_submit(sem_server server, const sem_request* request, uint64_t* ticket);
+/* SEM_ERR_BUSY (res->status too) while the request is queued or running. When done: SEM_OK and
+ * res filled; if x_host is not NULL and x_capacity >= res->n_local, x is copied into it and the
+ * ticket is released (later polls of it return SEM_ERR_ARG). */
+sem_status sem_server_poll(sem_server server, uint64_t ticket, double* x_host, int64_t x_capacity,
+                           sem_server_result* res);
+sem_status sem_server_stats(sem_server server, int* queued, int* active, size_t* bytes_in_use);
+/* Drops queued requests, waits for the running ones, frees the server. */
+sem_status sem_server_destroy(sem_server server);
 
 /* Number of kernel launches the library enqueued since load (all entry points). */
 uint64_t sem_launch_count(void);

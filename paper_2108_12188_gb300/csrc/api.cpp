@@ -33,25 +33,34 @@ void count_launch(int k) {
 
 namespace {
 
+// Stream-ordered allocation on `s` (the memory is usable on `s` at once and on other streams
+// once `s` has been synchronised).
 template <typename T>
-sem_status dmalloc(T** p, size_t count, size_t* acc) {
+sem_status dmalloc(T** p, size_t count, size_t* acc, cudaStream_t s) {
   *p = nullptr;
   if (count == 0) count = 1;
   const size_t bytes = count * sizeof(T);
-  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), bytes);
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(p), bytes, s);
   if (e != cudaSuccess) {
     cudaGetLastError();
+    *p = nullptr;
     return fail(e == cudaErrorMemoryAllocation ? SEM_ERR_OOM : SEM_ERR_CUDA,
-                "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e));
+                "cudaMallocAsync of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e));
   }
   if (acc) *acc += bytes;
   return SEM_OK;
 }
 
 template <typename T>
-void dfree(T*& p) {
-  if (p) cudaFree(p);
+void dfree(T*& p, cudaStream_t s) {
+  if (p) cudaFreeAsync(p, s);
   p = nullptr;
+}
+
+void note_stream(sem_mesh m, cudaStream_t s) {
+  for (cudaStream_t u : m->used)
+    if (u == s) return;
+  m->used.push_back(s);
 }
 
 #define SEM_TRY(expr)                 \
@@ -82,30 +91,39 @@ sem_status check_prec(int prec) {
 
 void cg_free(sem_cg c);
 
+// Waits for the streams the mesh was used on, then returns its memory on the private stream.
 void free_mesh(sem_mesh m) {
+  for (cudaStream_t u : m->used) cudaStreamSynchronize(u);
   if (m->solve_cg64) cg_free(m->solve_cg64);
   if (m->solve_cg32) cg_free(m->solve_cg32);
   m->solve_cg64 = m->solve_cg32 = nullptr;
-  dfree(m->ir_w64);
-  dfree(m->ir_r64);
-  dfree(m->ir_r32);
-  dfree(m->ir_d32);
-  dfree(m->ir_st);
-  dfree(m->ir_part);
-  dfree(m->coef64);
-  dfree(m->coef32);
-  dfree(m->G64);
-  dfree(m->G32);
-  dfree(m->seg_off);
-  dfree(m->seg_idx);
-  dfree(m->seg_mask);
-  dfree(m->mult);
-  dfree(m->minv64);
-  dfree(m->minv32);
-  dfree(m->ctab);
-  dfree(m->partials);
-  dfree(m->ticket);
-  dfree(m->dev_err);
+  cudaStream_t h = m->home;
+  dfree(m->ir_w64, h);
+  dfree(m->ir_r64, h);
+  dfree(m->ir_r32, h);
+  dfree(m->ir_d32, h);
+  dfree(m->ir_st, h);
+  dfree(m->ir_part, h);
+  dfree(m->coef64, h);
+  dfree(m->coef32, h);
+  dfree(m->G64, h);
+  dfree(m->G32, h);
+  dfree(m->seg_off, h);
+  dfree(m->seg_idx, h);
+  dfree(m->seg_mask, h);
+  dfree(m->mult, h);
+  dfree(m->minv64, h);
+  dfree(m->minv32, h);
+  dfree(m->ctab, h);
+  dfree(m->partials, h);
+  dfree(m->ticket, h);
+  dfree(m->dev_err, h);
+  if (h) {
+    cudaStreamSynchronize(h);
+    cudaStreamDestroy(h);
+  }
+  m->home = nullptr;
+  m->used.clear();
 }
 
 sem_status launch_ax_any(sem_mesh m, sem_prec prec, sem_ax_variant v, bool cg, AxLaunch a, cudaStream_t s) {
@@ -123,11 +141,12 @@ sem_status launch_ax_any(sem_mesh m, sem_prec prec, sem_ax_variant v, bool cg, A
 // Jacobi inverse diagonal, built once per mesh in FP64 (and rounded to FP32).
 sem_status ensure_jacobi(sem_mesh m, cudaStream_t s) {
   if (m->minv64) return SEM_OK;
+  note_stream(m, s);
   double* d = nullptr;
-  SEM_TRY(dmalloc(&d, m->n, nullptr));
+  SEM_TRY(dmalloc(&d, m->n, nullptr, s));
   sem_status st = SEM_OK;
   size_t bytes = 0;
-  if ((st = dmalloc(&m->minv64, m->n, &bytes)) == SEM_OK && (st = dmalloc(&m->minv32, m->n, &bytes)) == SEM_OK &&
+  if ((st = dmalloc(&m->minv64, m->n, &bytes, s)) == SEM_OK && (st = dmalloc(&m->minv32, m->n, &bytes, s)) == SEM_OK &&
       (st = launch_local_diag(m->N, m->E, m->coef64, d, s)) == SEM_OK &&
       (st = launch_invert(m->n, d, m->minv64, m->minv32, s)) == SEM_OK &&
       (st = launch_dssum_invert(m->n_seg, m->seg_off, m->seg_idx, m->seg_mask, d, m->minv64, m->minv32, s)) ==
@@ -135,10 +154,11 @@ sem_status ensure_jacobi(sem_mesh m, cudaStream_t s) {
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) st = cuda_fail(e, "cudaStreamSynchronize (Jacobi set-up)");
   }
-  cudaFree(d);
+  dfree(d, s);
   if (st != SEM_OK) {
-    dfree(m->minv64);
-    dfree(m->minv32);
+    dfree(m->minv64, s);
+    dfree(m->minv32, s);
+    cudaStreamSynchronize(s);
     return st;
   }
   m->device_bytes += bytes;
@@ -188,9 +208,11 @@ extern "C" sem_status sem_mesh_create(int N, int64_t nv, const double* vert_xyz,
 
   double* Xd = nullptr;
   int* bad = nullptr;
+  SEM_CUDA_TRY(cudaStreamCreateWithFlags(&m->home, cudaStreamNonBlocking));
+  m->used.push_back(s);
   auto cleanup = [&](sem_status st) {
-    if (Xd) cudaFree(Xd);
-    if (bad) cudaFree(bad);
+    dfree(Xd, s);
+    dfree(bad, s);
     if (st != SEM_OK) free_mesh(m.get());
     return st;
   };
@@ -206,20 +228,20 @@ extern "C" sem_status sem_mesh_create(int N, int64_t nv, const double* vert_xyz,
     cudaError_t _e = (expr);                             \
     if (_e != cudaSuccess) return cleanup(cuda_fail(_e, #expr)); \
   } while (0)
-  SEM_STEP(dmalloc(&Xd, X.size(), nullptr));
-  SEM_STEP(dmalloc(&bad, 1, nullptr));
-  SEM_STEP(dmalloc(&m->coef64, static_cast<size_t>(E) * 24, &acc));
-  SEM_STEP(dmalloc(&m->coef32, static_cast<size_t>(E) * 24, &acc));
-  if (flags & SEM_MESH_F64_STORED) SEM_STEP(dmalloc(&m->G64, static_cast<size_t>(E * 6 * P), &acc));
-  if (flags & SEM_MESH_F32_STORED) SEM_STEP(dmalloc(&m->G32, static_cast<size_t>(E * 6 * P), &acc));
-  SEM_STEP(dmalloc(&m->seg_off, T.seg_off.size(), &acc));
-  SEM_STEP(dmalloc(&m->seg_idx, T.seg_idx.size(), &acc));
-  SEM_STEP(dmalloc(&m->seg_mask, T.seg_mask.size(), &acc));
-  SEM_STEP(dmalloc(&m->mult, T.mult.size(), &acc));
-  SEM_STEP(dmalloc(&m->ctab, 256, &acc));
-  SEM_STEP(dmalloc(&m->partials, kRedMax, &acc));
-  SEM_STEP(dmalloc(&m->ticket, 1, &acc));
-  SEM_STEP(dmalloc(&m->dev_err, 1, &acc));
+  SEM_STEP(dmalloc(&Xd, X.size(), nullptr, s));
+  SEM_STEP(dmalloc(&bad, 1, nullptr, s));
+  SEM_STEP(dmalloc(&m->coef64, static_cast<size_t>(E) * 24, &acc, s));
+  SEM_STEP(dmalloc(&m->coef32, static_cast<size_t>(E) * 24, &acc, s));
+  if (flags & SEM_MESH_F64_STORED) SEM_STEP(dmalloc(&m->G64, static_cast<size_t>(E * 6 * P), &acc, s));
+  if (flags & SEM_MESH_F32_STORED) SEM_STEP(dmalloc(&m->G32, static_cast<size_t>(E * 6 * P), &acc, s));
+  SEM_STEP(dmalloc(&m->seg_off, T.seg_off.size(), &acc, s));
+  SEM_STEP(dmalloc(&m->seg_idx, T.seg_idx.size(), &acc, s));
+  SEM_STEP(dmalloc(&m->seg_mask, T.seg_mask.size(), &acc, s));
+  SEM_STEP(dmalloc(&m->mult, T.mult.size(), &acc, s));
+  SEM_STEP(dmalloc(&m->ctab, 256, &acc, s));
+  SEM_STEP(dmalloc(&m->partials, kRedMax, &acc, s));
+  SEM_STEP(dmalloc(&m->ticket, 1, &acc, s));
+  SEM_STEP(dmalloc(&m->dev_err, 1, &acc, s));
   SEM_CSTEP(cudaMemsetAsync(m->dev_err, 0, sizeof(int), s));
   SEM_CSTEP(cudaMemcpyAsync(Xd, X.data(), X.size() * sizeof(double), cudaMemcpyHostToDevice, s));
   SEM_CSTEP(cudaMemcpyAsync(m->seg_off, T.seg_off.data(), T.seg_off.size() * 4, cudaMemcpyHostToDevice, s));
@@ -261,7 +283,6 @@ extern "C" sem_status sem_mesh_destroy(sem_mesh m) {
   int cur = 0;
   cudaGetDevice(&cur);
   if (cur != m->device) cudaSetDevice(m->device);
-  cudaDeviceSynchronize();
   free_mesh(m);
   if (cur != m->device) cudaSetDevice(cur);
   delete m;
@@ -306,6 +327,7 @@ extern "C" sem_status sem_mesh_get_segments(sem_mesh m, int32_t* off, int32_t* i
 extern "C" sem_status sem_mesh_coords(sem_mesh m, double* xyz, void* stream) {
   SEM_TRY(check_mesh(m));
   SEM_TRY(check_ptr(xyz, "xyz_dev"));
+  note_stream(m, static_cast<cudaStream_t>(stream));
   return launch_coords(m->N, m->E, m->coef64, xyz, m->n, static_cast<cudaStream_t>(stream));
 }
 
@@ -316,6 +338,7 @@ extern "C" sem_status sem_mesh_geometry(sem_mesh m, sem_prec prec, void* G, void
   if (B) SEM_TRY(check_ptr(B, "B_dev"));
   if (!G && !B) return SEM_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  note_stream(m, s);
   int* bad = nullptr;
   SEM_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&bad), sizeof(int), s));
   const bool f64 = prec != SEM_F32;
@@ -333,6 +356,7 @@ extern "C" sem_status sem_scatter(sem_mesh m, sem_prec prec, const void* ug, voi
   SEM_TRY(check_ptr(ug, "u_glob_dev"));
   SEM_TRY(check_ptr(ul, "u_local_dev"));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  note_stream(m, s);
   std::vector<int32_t> g32(m->glo.begin(), m->glo.end());
   int32_t* gd = nullptr;
   SEM_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&gd), g32.size() * 4, s));
@@ -356,6 +380,7 @@ extern "C" sem_status sem_ax(sem_mesh m, sem_ax_variant v, sem_prec prec, const 
   SEM_TRY(check_ptr(w, "w_dev"));
   if (u == w) return fail(SEM_ERR_ARG, "u and w must not overlap");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  note_stream(m, s);
   AxLaunch a{};
   a.u = u;
   a.w = w;
@@ -368,6 +393,7 @@ extern "C" sem_status sem_dssum(sem_mesh m, sem_prec prec, void* u, int apply_ma
   SEM_TRY(check_mesh(m));
   SEM_TRY(check_prec(prec));
   SEM_TRY(check_ptr(u, "u_dev"));
+  note_stream(m, static_cast<cudaStream_t>(stream));
   return launch_dssum(data_prec(prec), m->n_seg, m->seg_off, m->seg_idx, m->seg_mask, u, apply_mask,
                       static_cast<cudaStream_t>(stream));
 }
@@ -379,6 +405,7 @@ extern "C" sem_status sem_glsc3(sem_mesh m, sem_prec prec, const void* a, const 
   SEM_TRY(check_ptr(a, "a_dev"));
   SEM_TRY(check_ptr(b, "b_dev"));
   if (!result) return fail(SEM_ERR_ARG, "result_dev is null");
+  note_stream(m, static_cast<cudaStream_t>(stream));
   return launch_glsc3(data_prec(prec), m->n, a, b, m->mult, m->ctab, m->partials, m->ticket, result,
                       static_cast<cudaStream_t>(stream));
 }
@@ -388,6 +415,7 @@ extern "C" sem_status sem_jacobi(sem_mesh m, sem_prec prec, void* minv, void* st
   SEM_TRY(check_prec(prec));
   SEM_TRY(check_ptr(minv, "minv_dev"));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  note_stream(m, s);
   SEM_TRY(ensure_jacobi(m, s));
   const bool f32 = prec == SEM_F32;
   const size_t bytes = m->n * (f32 ? sizeof(float) : sizeof(double));
@@ -401,6 +429,7 @@ extern "C" sem_status sem_rhs_sine(sem_mesh m, int a, int b, int c, sem_prec pre
   SEM_TRY(check_prec(prec));
   SEM_TRY(check_ptr(rhs, "rhs_dev"));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  note_stream(m, s);
   double* tmp = static_cast<double*>(rhs);
   if (prec == SEM_F32) SEM_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&tmp), m->n * sizeof(double), s));
   sem_status st = launch_rhs_local(m->N, m->E, m->coef64, a, b, c, tmp, s);
@@ -426,10 +455,11 @@ struct sem_cg_s {
   void* x = nullptr;
   const void* b = nullptr;
   CgScalars* st = nullptr;
-  CgScalars* st_host = nullptr;  // pinned
+  CgScalars st_host{};  // host mirror of the device scalars (pageable: no device-wide synchronisation)
   double *ax_part = nullptr, *gs_part = nullptr, *upd_part = nullptr, *init_part = nullptr;
   int ax_blocks = 0;
-  cudaStream_t cap = nullptr;
+  cudaStream_t cap = nullptr;     // private stream: allocation, graph capture, release
+  std::vector<cudaStream_t> used; // streams the solver's work was enqueued on
   cudaGraphExec_t exec = nullptr;
   int exec_k = 0;
   void* exec_x = nullptr;
@@ -443,13 +473,28 @@ const void* minv_of(sem_cg c) {
   return c->prec == SEM_F32 ? static_cast<const void*>(c->m->minv32) : static_cast<const void*>(c->m->minv64);
 }
 
+void cg_note(sem_cg c, cudaStream_t s) {
+  for (cudaStream_t u : c->used)
+    if (u == s) return;
+  c->used.push_back(s);
+}
+
+// Waits for the streams the solver was used on, then releases its memory on its own stream.
 void cg_free(sem_cg c) {
+  for (cudaStream_t u : c->used) cudaStreamSynchronize(u);
   if (c->exec) cudaGraphExecDestroy(c->exec);
-  if (c->cap) cudaStreamDestroy(c->cap);
-  for (void* q : {c->r, c->z, c->p, c->w}) if (q) cudaFree(q);
-  for (double* q : {c->ax_part, c->gs_part, c->upd_part, c->init_part}) if (q) cudaFree(q);
-  if (c->st) cudaFree(c->st);
-  if (c->st_host) cudaFreeHost(c->st_host);
+  cudaStream_t h = c->cap;
+  for (void* q : {c->r, c->z, c->p, c->w})
+    if (q) cudaFreeAsync(q, h);
+  dfree(c->ax_part, h);
+  dfree(c->gs_part, h);
+  dfree(c->upd_part, h);
+  dfree(c->init_part, h);
+  dfree(c->st, h);
+  if (h) {
+    cudaStreamSynchronize(h);
+    cudaStreamDestroy(h);
+  }
   delete c;
 }
 
@@ -470,27 +515,26 @@ sem_status cg_alloc(sem_mesh m, sem_prec prec, sem_ax_variant v, int precond, do
   c->use_graph = use_graph;
   const size_t es = prec == SEM_F32 ? sizeof(float) : sizeof(double);
   sem_status st = SEM_OK;
+  cudaError_t e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    delete c;
+    return cuda_fail(e, "cudaStreamCreate");
+  }
   for (void** q : {&c->r, &c->z, &c->p, &c->w}) {
-    cudaError_t e = cudaMalloc(q, m->n * es);
+    e = cudaMallocAsync(q, m->n * es, c->cap);
     if (e != cudaSuccess) {
       cudaGetLastError();
-      st = fail(SEM_ERR_OOM, "cudaMalloc of CG work vectors failed");
+      *q = nullptr;
+      st = fail(SEM_ERR_OOM, "cudaMallocAsync of CG work vectors failed");
       break;
     }
   }
-  if (st == SEM_OK) st = dmalloc(&c->ax_part, kRedMax, nullptr);
-  if (st == SEM_OK) st = dmalloc(&c->gs_part, kRedMax, nullptr);
-  if (st == SEM_OK) st = dmalloc(&c->upd_part, 2 * kRedMax, nullptr);
-  if (st == SEM_OK) st = dmalloc(&c->init_part, 3 * kRedMax, nullptr);
-  if (st == SEM_OK) st = dmalloc(&c->st, 1, nullptr);
-  if (st == SEM_OK) {
-    cudaError_t e = cudaMallocHost(reinterpret_cast<void**>(&c->st_host), sizeof(CgScalars));
-    if (e != cudaSuccess) st = cuda_fail(e, "cudaMallocHost");
-  }
-  if (st == SEM_OK) {
-    cudaError_t e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking);
-    if (e != cudaSuccess) st = cuda_fail(e, "cudaStreamCreate");
-  }
+  if (st == SEM_OK) st = dmalloc(&c->ax_part, kRedMax, nullptr, c->cap);
+  if (st == SEM_OK) st = dmalloc(&c->gs_part, kRedMax, nullptr, c->cap);
+  if (st == SEM_OK) st = dmalloc(&c->upd_part, 2 * kRedMax, nullptr, c->cap);
+  if (st == SEM_OK) st = dmalloc(&c->init_part, 3 * kRedMax, nullptr, c->cap);
+  if (st == SEM_OK) st = dmalloc(&c->st, 1, nullptr, c->cap);
+  if (st == SEM_OK && (e = cudaStreamSynchronize(c->cap)) != cudaSuccess) st = cuda_fail(e, "cudaStreamSynchronize");
   if (st != SEM_OK) {
     cg_free(c);
     return st;
@@ -522,8 +566,10 @@ sem_status cg_start(sem_cg c, const void* b, void* x, bool x0_is_zero, cudaStrea
   CgScalars init{};
   init.rtol2 = c->rtol * c->rtol;
   init.max_iter = c->max_iter;
-  *c->st_host = init;
-  SEM_CUDA_TRY(cudaMemcpyAsync(c->st, c->st_host, sizeof(CgScalars), cudaMemcpyHostToDevice, s));
+  cg_note(c, s);
+  note_stream(m, s);
+  c->st_host = init;
+  SEM_CUDA_TRY(cudaMemcpyAsync(c->st, &c->st_host, sizeof(CgScalars), cudaMemcpyHostToDevice, s));
   c->b = b;
   c->x = x;
   const void* ax0 = nullptr;
@@ -563,6 +609,8 @@ sem_status cg_enqueue_iteration(sem_cg c, cudaStream_t s) {
 
 sem_status cg_iterate(sem_cg c, int k, cudaStream_t s) {
   if (k <= 0) return SEM_OK;
+  cg_note(c, s);
+  note_stream(c->m, s);
   if (!c->use_graph) {
     for (int q = 0; q < k; ++q) SEM_TRY(cg_enqueue_iteration(c, s));
     return SEM_OK;
@@ -599,9 +647,10 @@ sem_status cg_iterate(sem_cg c, int k, cudaStream_t s) {
 }
 
 sem_status cg_query(sem_cg c, sem_cg_result* res, cudaStream_t s) {
-  SEM_CUDA_TRY(cudaMemcpyAsync(c->st_host, c->st, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
+  cg_note(c, s);
+  SEM_CUDA_TRY(cudaMemcpyAsync(&c->st_host, c->st, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
   SEM_CUDA_TRY(cudaStreamSynchronize(s));
-  const CgScalars& h = *c->st_host;
+  const CgScalars& h = c->st_host;
   if (res) {
     res->iters = h.iter;
     res->outer_iters = 0;
@@ -645,15 +694,17 @@ sem_status solve_mixed(sem_mesh m, const double* b, double* x, const sem_cg_opts
                     o->inner_rtol, o->max_iter, &inner));
   if (!m->ir_part) {
     sem_status a = SEM_OK;
-    if ((a = dmalloc(&m->ir_w64, m->n, nullptr)) != SEM_OK || (a = dmalloc(&m->ir_r64, m->n, nullptr)) != SEM_OK ||
-        (a = dmalloc(&m->ir_r32, m->n, nullptr)) != SEM_OK || (a = dmalloc(&m->ir_d32, m->n, nullptr)) != SEM_OK ||
-        (a = dmalloc(&m->ir_st, 1, nullptr)) != SEM_OK || (a = dmalloc(&m->ir_part, 2 * kRedMax, nullptr)) != SEM_OK) {
-      dfree(m->ir_w64);
-      dfree(m->ir_r64);
-      dfree(m->ir_r32);
-      dfree(m->ir_d32);
-      dfree(m->ir_st);
-      dfree(m->ir_part);
+    note_stream(m, s);
+    if ((a = dmalloc(&m->ir_w64, m->n, nullptr, s)) != SEM_OK || (a = dmalloc(&m->ir_r64, m->n, nullptr, s)) != SEM_OK ||
+        (a = dmalloc(&m->ir_r32, m->n, nullptr, s)) != SEM_OK || (a = dmalloc(&m->ir_d32, m->n, nullptr, s)) != SEM_OK ||
+        (a = dmalloc(&m->ir_st, 1, nullptr, s)) != SEM_OK ||
+        (a = dmalloc(&m->ir_part, 2 * kRedMax, nullptr, s)) != SEM_OK) {
+      dfree(m->ir_w64, s);
+      dfree(m->ir_r64, s);
+      dfree(m->ir_r32, s);
+      dfree(m->ir_d32, s);
+      dfree(m->ir_st, s);
+      dfree(m->ir_part, s);
       return a;
     }
   }
@@ -761,6 +812,8 @@ extern "C" sem_status sem_cg_iterate_timed(sem_cg c, int k, double* total_ms, do
   if (k < 1) return fail(SEM_ERR_ARG, "k must be >= 1");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   sem_mesh m = c->m;
+  cg_note(c, s);
+  note_stream(m, s);
   std::vector<cudaEvent_t> ev(3 * static_cast<size_t>(k) + 1, nullptr);
   auto destroy = [&] {
     for (cudaEvent_t e : ev)
@@ -819,8 +872,7 @@ extern "C" sem_status sem_cg_query(sem_cg c, sem_cg_result* res, void* stream) {
 
 extern "C" sem_status sem_cg_destroy(sem_cg c) {
   if (!c) return SEM_OK;
-  cudaDeviceSynchronize();
-  cg_free(c);
+  cg_free(c);  // waits only for the streams this solver was used on
   return SEM_OK;
 }
 

@@ -188,14 +188,14 @@ __global__ void __launch_bounds__(NP * NP * ax_epb<NP>())
 
 template <int NP, typename T, bool OTF, bool CG>
 int ax_max_blocks() {
-  static int cached = 0;
-  if (cached == 0) {
+  // resident blocks per SM x SMs; computed once (thread-safe static initialisation)
+  static const int cached = [] {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ax<NP, T, OTF, CG>, NP * NP * ax_epb<NP>(), 0);
-    cached = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
-  }
+    return (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+  }();
   return cached;
 }
 

@@ -198,16 +198,15 @@ template <int NP, bool CG>
 sem_status launch_df_t(int N, const AxLaunch& a, cudaStream_t s) {
   constexpr int EPB = ax_epb<NP>();
   constexpr size_t smem = df_smem_bytes<NP>();
-  static int max_blocks = 0;
-  if (max_blocks == 0) {
-    SEM_CUDA_TRY(cudaFuncSetAttribute(k_ax_df<NP, CG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      static_cast<int>(smem)));
+  // resident blocks per SM x SMs, with the dynamic shared-memory limit raised first; once
+  static const int max_blocks = [] {
+    cudaFuncSetAttribute(k_ax_df<NP, CG>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ax_df<NP, CG>, NP * NP * EPB, smem);
-    max_blocks = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
-  }
+    return (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+  }();
   const int64_t groups = (a.E + EPB - 1) / EPB;
   int grid = max_blocks < kRedMax ? max_blocks : kRedMax;
   if (groups < grid) grid = static_cast<int>(groups);

@@ -240,11 +240,9 @@ sem_status launch_coords(int N, int64_t E, const double* coef64, double* xyz, in
 sem_status launch_local_diag(int N, int64_t E, const double* coef64, double* d, cudaStream_t s) {
   const int Np = N + 1, P = Np * Np * Np;
   const size_t smem = 6 * static_cast<size_t>(P) * sizeof(double);
-  static bool attr_set = false;
-  if (!attr_set) {
-    SEM_CUDA_TRY(cudaFuncSetAttribute(k_local_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, 6 * 1728 * 8));
-    attr_set = true;
-  }
+  static const cudaError_t attr = cudaFuncSetAttribute(k_local_diag, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                       6 * kMaxNp * kMaxNp * kMaxNp * static_cast<int>(sizeof(double)));
+  SEM_CUDA_TRY(attr);
   // E blocks: at most 2^31 / 8 elements (the local-size limit), within the grid x limit
   k_local_diag<<<static_cast<unsigned>(E), P < 512 ? P : 512, smem, s>>>(gll_table(N), Np, E, coef64, d);
   count_launch();

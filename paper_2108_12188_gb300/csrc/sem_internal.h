@@ -79,6 +79,11 @@ struct sem_mesh_s {
   unsigned int* ticket = nullptr;
   int* dev_err = nullptr;     // device error word written by kernels whose bounded waits ran out
   size_t device_bytes = 0;
+  // Stream-ordered memory: everything is allocated with cudaMallocAsync and released with
+  // cudaFreeAsync on `home` (a private non-blocking stream) after the streams the mesh was used
+  // on have drained, so destroying a mesh never waits for unrelated work on the device.
+  cudaStream_t home = nullptr;
+  std::vector<cudaStream_t> used;
   // work space of sem_cg_solve, kept between solves (freed with the mesh)
   sem_cg solve_cg64 = nullptr;      // FP64 CG handle
   sem_cg solve_cg32 = nullptr;      // FP32 inner CG handle (mixed precision)

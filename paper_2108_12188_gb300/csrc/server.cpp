@@ -1,0 +1,259 @@
+// Solve server: admits Poisson solve requests of different sizes and orders by a device
+// memory budget and runs the admitted ones concurrently, each on its own non-blocking CUDA
+// stream, so their kernels overlap on the GPU; requests that arrive while others run are
+// admitted as slots and memory free up (continuous batching at the level of solves).
+//
+// A request carries its mesh (vertices, connectivity, order), the wave numbers of the
+// manufactured right-hand side and CG options; the worker that takes it builds the mesh,
+// the right-hand side, solves, copies x to host memory and releases everything. Every
+// device allocation is stream-ordered, so one request's set-up or teardown never waits for
+// the others' kernels. A request that fails (bad mesh, non-convergence) fails alone.
+//
+// Results do not depend on what else runs: each solve's launches and reductions are the
+// same as when it runs alone (fixed grids, fixed-order sums, no atomics on values).
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+
+#include "sem_internal.h"
+
+namespace {
+
+double now_ms() {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+struct Request {
+  uint64_t ticket = 0;
+  int N = 0;
+  std::vector<double> vxyz;
+  std::vector<int64_t> ev;
+  std::vector<uint8_t> dflags;
+  int sine[3] = {1, 1, 1};
+  sem_cg_opts opts{};
+  size_t est_bytes = 0;
+  int64_t n_local = 0;
+  // results
+  bool done = false;
+  sem_server_result res{};
+  std::vector<double> x;
+  double t_submit = 0, t_start = 0;
+};
+
+}  // namespace
+
+struct sem_server_s {
+  int device = 0;
+  size_t budget = 0, in_use = 0;
+  int max_slots = 1, active = 0;
+  bool stop = false;
+  uint64_t next_ticket = 1;
+  std::deque<Request*> queue;
+  std::unordered_map<uint64_t, std::unique_ptr<Request>> all;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::vector<std::thread> workers;
+};
+
+namespace {
+
+// Device bytes of one request: mesh (coefficients, segments, multiplicities), stored factors
+// if the options need them, Jacobi inverse (FP64 + FP32), right-hand side and solution,
+// FP64 CG or refinement work vectors plus the FP32 inner CG.
+size_t estimate_bytes(int64_t E, int N, const sem_cg_opts& o) {
+  const size_t Np = static_cast<size_t>(N) + 1;
+  const size_t n = static_cast<size_t>(E) * Np * Np * Np;
+  size_t b = static_cast<size_t>(E) * 24 * 12 + 5 * n + 12 * n + 16 * n;
+  const bool f64_stored = o.variant == SEM_AX_STORED;
+  const bool f32_stored = o.mixed && o.inner_variant == SEM_AX_STORED;
+  if (f64_stored) b += 48 * n;
+  if (f32_stored) b += 24 * n;
+  b += o.mixed ? (16 * n + 8 * n + 16 * n) : 32 * n;
+  return b + (8u << 20);
+}
+
+void run_request(sem_server srv, Request* r) {
+  cudaSetDevice(srv->device);
+  sem_server_result& res = r->res;
+  cudaStream_t s = nullptr;
+  sem_mesh mesh = nullptr;
+  double* b = nullptr;
+  double* x = nullptr;
+  sem_status st = SEM_OK;
+  const double t0 = now_ms();
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) st = SEM_ERR_CUDA;
+  unsigned flags = 0;
+  if (r->opts.variant == SEM_AX_STORED) flags |= SEM_MESH_F64_STORED;
+  if (r->opts.mixed && r->opts.inner_variant == SEM_AX_STORED) flags |= SEM_MESH_F32_STORED;
+  if (st == SEM_OK)
+    st = sem_mesh_create(r->N, static_cast<int64_t>(r->vxyz.size() / 3), r->vxyz.data(),
+                         static_cast<int64_t>(r->ev.size() / 8), r->ev.data(),
+                         r->dflags.empty() ? nullptr : r->dflags.data(), flags, s, &mesh);
+  sem_mesh_info_t info{};
+  if (st == SEM_OK) st = sem_mesh_get_info(mesh, &info);
+  if (st == SEM_OK && cudaMallocAsync(reinterpret_cast<void**>(&b), info.n_local * sizeof(double), s) != cudaSuccess)
+    st = SEM_ERR_OOM;
+  if (st == SEM_OK && cudaMallocAsync(reinterpret_cast<void**>(&x), info.n_local * sizeof(double), s) != cudaSuccess)
+    st = SEM_ERR_OOM;
+  if (st == SEM_OK) st = sem_rhs_sine(mesh, r->sine[0], r->sine[1], r->sine[2], SEM_F64, b, s);
+  if (st == SEM_OK && cudaMemsetAsync(x, 0, info.n_local * sizeof(double), s) != cudaSuccess) st = SEM_ERR_CUDA;
+  const double t1 = now_ms();
+  sem_cg_result cg{};
+  if (st == SEM_OK) {
+    sem_status solve = sem_cg_solve(mesh, b, x, &r->opts, &cg, s);
+    if (solve == SEM_ERR_ARG || solve == SEM_ERR_OOM || solve == SEM_ERR_CUDA || solve == SEM_ERR_UNSUPPORTED)
+      st = solve;
+  }
+  std::vector<double> xh;
+  if (st == SEM_OK) {
+    xh.resize(static_cast<size_t>(info.n_local));
+    if (cudaMemcpyAsync(xh.data(), x, xh.size() * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      st = SEM_ERR_CUDA;
+  }
+  const double t2 = now_ms();
+  if (b) cudaFreeAsync(b, s);
+  if (x) cudaFreeAsync(x, s);
+  if (mesh) sem_mesh_destroy(mesh);
+  if (s) {
+    cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+  }
+  std::lock_guard<std::mutex> lock(srv->mu);
+  res.status = st == SEM_OK ? cg.status : st;
+  res.n_local = info.n_local;
+  res.cg = cg;
+  res.queue_ms = r->t_start - r->t_submit;
+  res.setup_ms = t1 - t0;
+  res.solve_ms = t2 - t1;
+  res.latency_ms = t2 - r->t_submit;
+  r->x = std::move(xh);
+  r->done = true;
+  srv->in_use -= r->est_bytes;
+  --srv->active;
+  srv->cv.notify_all();
+}
+
+void worker_loop(sem_server srv) {
+  for (;;) {
+    Request* r = nullptr;
+    {
+      std::unique_lock<std::mutex> lock(srv->mu);
+      srv->cv.wait(lock, [&] {
+        if (srv->stop) return true;
+        if (srv->queue.empty()) return false;
+        const Request* h = srv->queue.front();
+        // first in, first admitted: the head waits until its memory fits (or the device is idle)
+        return srv->active == 0 || srv->in_use + h->est_bytes <= srv->budget;
+      });
+      if (srv->stop) return;
+      r = srv->queue.front();
+      srv->queue.pop_front();
+      srv->in_use += r->est_bytes;
+      ++srv->active;
+      r->t_start = now_ms();
+    }
+    run_request(srv, r);
+  }
+}
+
+}  // namespace
+
+using sem::fail;
+
+extern "C" sem_status sem_server_create(size_t hbm_budget_bytes, int max_slots, sem_server* out) {
+  if (!out) return fail(SEM_ERR_ARG, "out is null");
+  *out = nullptr;
+  if (max_slots < 1 || max_slots > 256 || hbm_budget_bytes == 0)
+    return fail(SEM_ERR_ARG, "need 1 <= max_slots <= 256 and a non-zero budget");
+  auto srv = std::make_unique<sem_server_s>();
+  SEM_CUDA_TRY(cudaGetDevice(&srv->device));
+  // keep freed stream-ordered memory in the pool between requests (this process only)
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, srv->device) == cudaSuccess) {
+    uint64_t keep = hbm_budget_bytes;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  srv->budget = hbm_budget_bytes;
+  srv->max_slots = max_slots;
+  for (int q = 0; q < max_slots; ++q) srv->workers.emplace_back(worker_loop, srv.get());
+  *out = srv.release();
+  return SEM_OK;
+}
+
+extern "C" sem_status sem_server_submit(sem_server srv, const sem_request* req, uint64_t* ticket) {
+  if (!srv || !req || !ticket) return fail(SEM_ERR_ARG, "null argument");
+  if (req->N < 1 || req->N > SEM_MAX_N) return fail(SEM_ERR_UNSUPPORTED, "polynomial order out of range");
+  if (req->E < 1 || req->num_vertices < 8 || !req->vert_xyz_host || !req->elem_verts_host)
+    return fail(SEM_ERR_ARG, "request needs vertices and elements");
+  auto r = std::make_unique<Request>();
+  r->N = req->N;
+  r->vxyz.assign(req->vert_xyz_host, req->vert_xyz_host + 3 * req->num_vertices);
+  r->ev.assign(req->elem_verts_host, req->elem_verts_host + 8 * req->E);
+  if (req->dirichlet_vertex_flags_host)
+    r->dflags.assign(req->dirichlet_vertex_flags_host, req->dirichlet_vertex_flags_host + req->num_vertices);
+  std::memcpy(r->sine, req->sine, sizeof(r->sine));
+  r->opts = req->opts;
+  const size_t Np = static_cast<size_t>(req->N) + 1;
+  r->n_local = static_cast<int64_t>(static_cast<size_t>(req->E) * Np * Np * Np);
+  r->est_bytes = estimate_bytes(req->E, req->N, req->opts);
+  std::lock_guard<std::mutex> lock(srv->mu);
+  if (r->est_bytes > srv->budget) return fail(SEM_ERR_ARG, "request needs more device memory than the budget");
+  r->t_submit = now_ms();
+  r->ticket = srv->next_ticket++;
+  r->res.status = SEM_ERR_BUSY;
+  *ticket = r->ticket;
+  srv->queue.push_back(r.get());
+  srv->all.emplace(r->ticket, std::move(r));
+  srv->cv.notify_all();
+  return SEM_OK;
+}
+
+extern "C" sem_status sem_server_poll(sem_server srv, uint64_t ticket, double* x_host, int64_t x_capacity,
+                                      sem_server_result* res) {
+  if (!srv || !res) return fail(SEM_ERR_ARG, "null argument");
+  std::lock_guard<std::mutex> lock(srv->mu);
+  auto it = srv->all.find(ticket);
+  if (it == srv->all.end()) return fail(SEM_ERR_ARG, "unknown or released ticket");
+  Request* r = it->second.get();
+  if (!r->done) {
+    *res = sem_server_result{};
+    res->status = SEM_ERR_BUSY;
+    res->n_local = r->n_local;
+    return SEM_ERR_BUSY;
+  }
+  *res = r->res;
+  if (x_host) {
+    if (x_capacity < static_cast<int64_t>(r->x.size())) return fail(SEM_ERR_ARG, "x_host is too small");
+    std::memcpy(x_host, r->x.data(), r->x.size() * sizeof(double));
+    srv->all.erase(it);  // released once its solution has been taken
+  }
+  return SEM_OK;
+}
+
+extern "C" sem_status sem_server_stats(sem_server srv, int* queued, int* active, size_t* bytes_in_use) {
+  if (!srv) return fail(SEM_ERR_ARG, "null server");
+  std::lock_guard<std::mutex> lock(srv->mu);
+  if (queued) *queued = static_cast<int>(srv->queue.size());
+  if (active) *active = srv->active;
+  if (bytes_in_use) *bytes_in_use = srv->in_use;
+  return SEM_OK;
+}
+
+extern "C" sem_status sem_server_destroy(sem_server srv) {
+  if (!srv) return SEM_OK;
+  {
+    std::lock_guard<std::mutex> lock(srv->mu);
+    srv->stop = true;
+    srv->queue.clear();  // queued requests are dropped; running ones finish
+  }
+  srv->cv.notify_all();
+  for (auto& t : srv->workers) t.join();
+  delete srv;
+  return SEM_OK;
+}

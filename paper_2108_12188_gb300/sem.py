@@ -28,7 +28,8 @@ EXPORTS = [
     "sem_mesh_get_segments", "sem_mesh_coords", "sem_mesh_geometry", "sem_scatter", "sem_ax", "sem_dssum",
     "sem_glsc3", "sem_glsc3_noalloc", "sem_jacobi", "sem_rhs_sine", "sem_cg_default_opts", "sem_cg_solve", "sem_cg_create",
     "sem_cg_start", "sem_cg_iterate", "sem_cg_iterate_timed", "sem_cg_query", "sem_cg_destroy", "sem_launch_count", "sem_last_error",
-    "sem_status_string",
+    "sem_status_string", "sem_server_create", "sem_server_submit", "sem_server_poll", "sem_server_stats",
+    "sem_server_destroy",
 ]
 
 
@@ -56,6 +57,22 @@ class CgResult(C.Structure):
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class Request(C.Structure):
+    _fields_ = [("N", C.c_int), ("num_vertices", C.c_int64), ("vert_xyz_host", C.c_void_p), ("E", C.c_int64),
+                ("elem_verts_host", C.c_void_p), ("dirichlet_vertex_flags_host", C.c_void_p),
+                ("sine", C.c_int * 3), ("opts", CgOpts)]
+
+
+class ServerResult(C.Structure):
+    _fields_ = [("status", C.c_int), ("n_local", C.c_int64), ("cg", CgResult), ("queue_ms", C.c_double),
+                ("setup_ms", C.c_double), ("solve_ms", C.c_double), ("latency_ms", C.c_double)]
+
+    def as_dict(self):
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f != "cg"}
+        d["cg"] = self.cg.as_dict()
+        return d
 
 
 _lib = None
@@ -96,6 +113,11 @@ def load_library(path: str | None = None):
         "sem_cg_query": [_VP, C.POINTER(CgResult), _VP],
         "sem_cg_iterate_timed": [_VP, _I, C.POINTER(_D), C.POINTER(_D), _VP],
         "sem_cg_destroy": [_VP],
+        "sem_server_create": [C.c_size_t, _I, C.POINTER(_VP)],
+        "sem_server_submit": [_VP, C.POINTER(Request), C.POINTER(C.c_uint64)],
+        "sem_server_poll": [_VP, C.c_uint64, _VP, _I64, C.POINTER(ServerResult)],
+        "sem_server_stats": [_VP, C.POINTER(_I), C.POINTER(_I), C.POINTER(C.c_size_t)],
+        "sem_server_destroy": [_VP],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -335,6 +357,52 @@ def sem_cg_query(cg, stream=None) -> dict:
 
 def sem_cg_destroy(cg):
     _check(load_library().sem_cg_destroy(cg))
+
+
+# ---------------------------------------------------------------------------
+# solve server
+# ---------------------------------------------------------------------------
+
+def sem_server_create(hbm_budget_bytes: int, max_slots: int):
+    out = _VP()
+    _check(load_library().sem_server_create(int(hbm_budget_bytes), int(max_slots), C.byref(out)))
+    return out
+
+
+def sem_server_submit(server, N, vert_xyz, elem_verts, sine=(1, 1, 1), opts=None, dirichlet_vertex_flags=None):
+    vx = np.ascontiguousarray(vert_xyz, dtype=np.float64)
+    ev = np.ascontiguousarray(elem_verts, dtype=np.int64)
+    df = None if dirichlet_vertex_flags is None else np.ascontiguousarray(dirichlet_vertex_flags, dtype=np.uint8)
+    req = Request(int(N), vx.shape[0], vx.ctypes.data, ev.shape[0], ev.ctypes.data,
+                  None if df is None else df.ctypes.data, (C.c_int * 3)(*sine), opts or sem_cg_default_opts())
+    ticket = C.c_uint64()
+    _check(load_library().sem_server_submit(server, C.byref(req), C.byref(ticket)))  # copies the arrays
+    return int(ticket.value)
+
+
+def sem_server_poll(server, ticket, want_x=True):
+    """None while busy; else (result dict, x as numpy array or None)."""
+    lib = load_library()
+    res = ServerResult()
+    st = lib.sem_server_poll(server, C.c_uint64(ticket), None, 0, C.byref(res))
+    if st == SEM_ERR_BUSY:
+        return None
+    _check(st)
+    x = None
+    if want_x:
+        x = np.empty(res.n_local, dtype=np.float64)
+        _check(lib.sem_server_poll(server, C.c_uint64(ticket), x.ctypes.data, x.size, C.byref(res)))
+    return res.as_dict(), x
+
+
+def sem_server_stats(server):
+    q, a, b = _I(), _I(), C.c_size_t()
+    _check(load_library().sem_server_stats(server, C.byref(q), C.byref(a), C.byref(b)))
+    return {"queued": q.value, "active": a.value, "bytes_in_use": b.value}
+
+
+def sem_server_destroy(server):
+    _check(load_library().sem_server_destroy(server))
 
 
 def sem_launch_count() -> int:
