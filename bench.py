@@ -646,13 +646,70 @@ def run_serve(args):
         "p99_ms": main["p99_ms"], "rates": out_rates}))
 
 
+def run_sweep(args):
+    """Polynomial-order sweep: N in {3,5,7,9,11}, E = n^3 with n = round(cbrt(16.8M / (N+1)^3)),
+    interior jitter +-0.1h; per N the autotuner picks block shape and stored versus on-the-fly
+    factors for FP64 and FP32, then A_L (tuned) and the CG solve to 1e-10 are timed: FP64
+    Jacobi-CG and FP32 inner / FP64 refinement, CG iterations replayed as CUDA graphs."""
+    import torch
+    from paper_2108_12188_gb300 import build_lib, sem
+    from synthetic import BoxMesh, n_for_points
+    build_lib.build()
+    sem.load_library()
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    flush = torch.zeros(96 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    rows = []
+    for N in (3, 5, 7, 9, 11):
+        nel = n_for_points(N + 1)
+        m = BoxMesh(nel, nel, nel, jitter=0.1, seed=100 + N)
+        mesh = sem.Mesh(N, m.vert_xyz, m.elem_verts, flags=sem.SEM_MESH_F64_STORED | sem.SEM_MESH_F32_STORED)
+        n = mesh.n
+        row = {"N": N, "elements": nel ** 3, "n_local": n, "flops_per_point_eq11": flops_eq11(N)}
+        for pname, prec in (("f64", sem.SEM_F64), ("f32", sem.SEM_F32)):
+            rep = sem.sem_autotune(mesh.handle, prec, reps=10)
+            best = rep["candidates"][rep["best"]]
+            dt = torch.float64 if prec == sem.SEM_F64 else torch.float32
+            u = torch.rand(n, dtype=dt, device="cuda")
+            w = torch.empty_like(u)
+            med, _, _ = time_ax(sem, mesh, sem.SEM_AX_AUTO, prec, u, w, flush, reps=10, warmup=2, assemble=False)
+            row[pname] = {"tuner": rep["candidates"], "chosen": best, "ax_ms": med, "ax_gdof_s": n / (med * 1e-3) / 1e9,
+                          "ax_gflop_s_eq11": flops_eq11(N) * n / (med * 1e-3) / 1e9}
+        b = torch.empty(n, dtype=torch.float64, device="cuda")
+        sem.sem_rhs_sine(mesh.handle, 1, 1, 1, sem.SEM_F64, b)
+        x = torch.zeros_like(b)
+        for name, o in (("cg_fp64", sem.sem_cg_default_opts(rtol=1e-10, variant=sem.SEM_AX_AUTO)),
+                        ("cg_mixed", sem.sem_cg_default_opts(rtol=1e-10, mixed=1, variant=sem.SEM_AX_AUTO,
+                                                             inner_variant=sem.SEM_AX_AUTO))):
+            x.zero_()
+            sem.sem_cg_solve(mesh.handle, b, x, sem.sem_cg_default_opts(rtol=1e-2))  # warm-up: graphs, Jacobi
+            x.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            res = sem.sem_cg_solve(mesh.handle, b, x, o)
+            e1.record()
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            row[name] = {"ms": ms, "iterations": res["iters"], "outer": res["outer_iters"],
+                         "ms_per_iteration": ms / max(res["iters"], 1), "rel_res": res["rel_res"],
+                         "status": sem.sem_status_string(res["status"])}
+        rows.append(row)
+        mesh.close()
+        print(json.dumps({"N": N, "done": True}), file=sys.stderr)
+    print(json.dumps({"metric": "Ax GDOF/s per polynomial order (tuned)", "value": rows[2]["f32"]["ax_gdof_s"],
+                      "unit": "GDOF/s", "higher_is_better": True, "n_gpus": 1, "dtype": "f64/f32", "data": "synthetic",
+                      "config": {"workload": "N in {3,5,7,9,11}, n^3 elements with n = round(cbrt(16.8M/(N+1)^3)), "
+                                             "jitter 0.1h, autotuned, CG as CUDA graphs"},
+                      "rows": rows}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="sem", choices=["sem", "reference"])
-    ap.add_argument("--workload", default="ax", choices=["ax", "solve", "serve"],
+    ap.add_argument("--workload", default="ax", choices=["ax", "solve", "serve", "sweep"],
                     help="ax: the Ax-throughput line (default); solve: the 64^3 full-solve comparison; "
                          "serve: the request-stream latency measurement")
     ap.add_argument("--requests", type=int, default=1000, help="requests per arrival rate (serve)")
@@ -669,6 +726,8 @@ def main():
         run_solve(args)
     elif args.workload == "serve":
         run_serve(args)
+    elif args.workload == "sweep":
+        run_sweep(args)
     else:
         run_gpu(args)
 

@@ -63,8 +63,10 @@ typedef enum { SEM_F64 = 0, SEM_F32 = 1, SEM_F64X = 2 } sem_prec;
 
 /* Variants of the local operator A_L (Section 5.1):
  * STORED reads the six geometric factors per point from device memory;
- * OTF recomputes them per point from 21 per-element trilinear-map coefficients. */
-typedef enum { SEM_AX_STORED = 0, SEM_AX_OTF = 1 } sem_ax_variant;
+ * OTF recomputes them per point from 21 per-element trilinear-map coefficients;
+ * AUTO uses the variant and block shape sem_autotune found fastest for this order and
+ * precision (before tuning: STORED if the mesh holds the factors, else OTF). */
+typedef enum { SEM_AX_STORED = 0, SEM_AX_OTF = 1, SEM_AX_AUTO = 2 } sem_ax_variant;
 
 #define SEM_MAX_N 11 /* polynomial orders 1..11 are compiled in */
 
@@ -188,15 +190,42 @@ sem_status sem_jacobi(sem_mesh mesh, sem_prec prec, void* minv_dev, void* stream
  * at the mapped GLL points (Eq. 2's right side by GLL quadrature). Async. */
 sem_status sem_rhs_sine(sem_mesh mesh, int a, int b, int c, sem_prec prec, void* rhs_dev, void* stream);
 
+/* ---- Autotuning of the local operator ----
+ * sem_autotune times every candidate implementation of A_L on this mesh (stored or
+ * on-the-fly factors where available, times two block shapes: elements per thread block)
+ * with CUDA events over `reps` launches each, and records the fastest for the mesh's order
+ * and the precision, process-wide; SEM_AX_AUTO then uses it, and explicit variants use the
+ * faster block shape. Synchronises `stream`. sem_autotune_save / sem_autotune_load write and
+ * read the table as text, keyed by the GPU name (a table from another GPU model is refused
+ * with SEM_ERR_ARG). The paper has no tuner (its kernels are fixed FPGA pipelines). */
+typedef struct {
+  int variant;            /* sem_ax_variant */
+  int shape;              /* block shape choice 0 / 1 */
+  int elements_per_block;
+  double ms;              /* mean time of one A_L application */
+} sem_tune_entry;
+
+typedef struct {
+  int N;
+  int prec;
+  int n_candidates;
+  sem_tune_entry candidates[4];
+  int best;               /* index into candidates */
+} sem_tune_report;
+
+sem_status sem_autotune(sem_mesh mesh, sem_prec prec, int reps, sem_tune_report* report_host, void* stream);
+sem_status sem_autotune_save(const char* path);
+sem_status sem_autotune_load(const char* path);
+
 /* ---- Conjugate gradient (Algorithm 1 + Jacobi z = M^-1 r) ---- */
 
 typedef struct {
   double rtol;        /* stop when sqrt(<r,r,c> / <b,b,c>) <= rtol (checked after the r update) */
   int max_iter;       /* FP64 CG: iteration limit; mixed: limit on inner iterations in total */
   int precond;        /* 0: none, 1: Jacobi */
-  int variant;        /* sem_ax_variant of the FP64 operator */
+  int variant;        /* sem_ax_variant of the FP64 operator (SEM_AX_AUTO allowed) */
   int mixed;          /* 0: FP64 CG; 1: FP32 inner CG + FP64 iterative refinement */
-  int inner_variant;  /* sem_ax_variant of the FP32 inner operator (mixed) */
+  int inner_variant;  /* sem_ax_variant of the FP32 inner operator (mixed; SEM_AX_AUTO allowed) */
   double inner_rtol;  /* relative tolerance of each inner solve (mixed) */
   int max_outer;      /* refinement steps limit (mixed) */
   int check_every;    /* iterations between host reads of the device convergence flag (>= 1) */

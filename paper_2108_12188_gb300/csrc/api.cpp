@@ -4,7 +4,11 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <cstdio>
+#include <fstream>
 #include <memory>
+#include <mutex>
+#include <sstream>
 
 #include "sem_internal.h"
 
@@ -126,7 +130,35 @@ void free_mesh(sem_mesh m) {
   m->used.clear();
 }
 
+// Process-wide tuning results per precision (F64, F32, F64X) and order: the best variant and,
+// for each variant, its faster block shape.
+struct TuneSlot {
+  bool valid = false;
+  sem_ax_variant best = SEM_AX_STORED;
+  int shape[2] = {0, 0};
+  double ms[2] = {0, 0};
+};
+std::mutex g_tune_mu;
+TuneSlot g_tune[3][SEM_MAX_N + 1];
+
+bool has_factors(sem_mesh m, sem_prec prec) { return prec == SEM_F32 ? m->G32 != nullptr : m->G64 != nullptr; }
+
+// Resolves SEM_AX_AUTO and picks the tuned block shape.
+void resolve_variant(sem_mesh m, sem_prec prec, sem_ax_variant v, sem_ax_variant* out_v, int* out_shape) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  const TuneSlot& t = g_tune[prec][m->N];
+  sem_ax_variant r = v;
+  if (v == SEM_AX_AUTO) {
+    if (t.valid && (t.best == SEM_AX_OTF || has_factors(m, prec))) r = t.best;
+    else r = has_factors(m, prec) ? SEM_AX_STORED : SEM_AX_OTF;
+    if (prec == SEM_F64X) r = SEM_AX_STORED;
+  }
+  *out_v = r;
+  *out_shape = t.valid ? t.shape[r] : 0;
+}
+
 sem_status launch_ax_any(sem_mesh m, sem_prec prec, sem_ax_variant v, bool cg, AxLaunch a, cudaStream_t s) {
+  resolve_variant(m, prec, v, &v, &a.shape);
   a.E = m->E;
   a.err = m->dev_err;
   const bool fp64_data = prec != SEM_F32;
@@ -375,7 +407,7 @@ extern "C" sem_status sem_ax(sem_mesh m, sem_ax_variant v, sem_prec prec, const 
                              void* stream) {
   SEM_TRY(check_mesh(m));
   SEM_TRY(check_prec(prec));
-  if (v != SEM_AX_STORED && v != SEM_AX_OTF) return fail(SEM_ERR_ARG, "unknown Ax variant");
+  if (v != SEM_AX_STORED && v != SEM_AX_OTF && v != SEM_AX_AUTO) return fail(SEM_ERR_ARG, "unknown Ax variant");
   SEM_TRY(check_ptr(u, "u_dev"));
   SEM_TRY(check_ptr(w, "w_dev"));
   if (u == w) return fail(SEM_ERR_ARG, "u and w must not overlap");
@@ -503,7 +535,7 @@ sem_status cg_alloc(sem_mesh m, sem_prec prec, sem_ax_variant v, int precond, do
   *out = nullptr;
   if (v == SEM_AX_STORED && !(prec == SEM_F32 ? m->G32 != nullptr : m->G64 != nullptr))
     return fail(SEM_ERR_ARG, "stored factors of this precision were not requested at mesh creation");
-  if (prec == SEM_F64X && v != SEM_AX_STORED)
+  if (prec == SEM_F64X && v == SEM_AX_OTF)
     return fail(SEM_ERR_UNSUPPORTED, "double-float FP64 arithmetic runs the stored-factor variant only");
   sem_cg c = new sem_cg_s();
   c->m = m;
@@ -663,8 +695,8 @@ sem_status cg_query(sem_cg c, sem_cg_result* res, cudaStream_t s) {
 sem_status check_opts(const sem_cg_opts* o) {
   if (!o) return fail(SEM_ERR_ARG, "opts is null");
   if (!(o->rtol >= 0) || o->max_iter < 0 || o->check_every < 1 || (o->precond != 0 && o->precond != 1) ||
-      (o->variant != SEM_AX_STORED && o->variant != SEM_AX_OTF) ||
-      (o->inner_variant != SEM_AX_STORED && o->inner_variant != SEM_AX_OTF) || (o->f64_arith != 0 && o->f64_arith != 1))
+      (o->variant < SEM_AX_STORED || o->variant > SEM_AX_AUTO) ||
+      (o->inner_variant < SEM_AX_STORED || o->inner_variant > SEM_AX_AUTO) || (o->f64_arith != 0 && o->f64_arith != 1))
     return fail(SEM_ERR_ARG, "invalid CG options");
   if (o->mixed && (!(o->inner_rtol > 0 && o->inner_rtol < 1) || o->max_outer < 1))
     return fail(SEM_ERR_ARG, "mixed precision needs 0 < inner_rtol < 1 and max_outer >= 1");
@@ -947,4 +979,148 @@ extern "C" const char* sem_status_string(sem_status s) {
     case SEM_ERR_UNSUPPORTED: return "SEM_ERR_UNSUPPORTED";
   }
   return "unknown";
+}
+
+// ---------------------------------------------------------------------------
+// autotuning
+// ---------------------------------------------------------------------------
+
+namespace {
+std::string device_name() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceProp p{};
+  cudaGetDeviceProperties(&p, dev);
+  std::string n = p.name;
+  for (char& ch : n)
+    if (ch == ' ') ch = '_';
+  return n;
+}
+}  // namespace
+
+extern "C" sem_status sem_autotune(sem_mesh m, sem_prec prec, int reps, sem_tune_report* rep, void* stream) {
+  SEM_TRY(check_mesh(m));
+  SEM_TRY(check_prec(prec));
+  if (!rep || reps < 1) return fail(SEM_ERR_ARG, "need a report and reps >= 1");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  note_stream(m, s);
+  const size_t es = prec == SEM_F32 ? sizeof(float) : sizeof(double);
+  void *u = nullptr, *w = nullptr;
+  SEM_CUDA_TRY(cudaMallocAsync(&u, m->n * es, s));
+  cudaError_t e = cudaMallocAsync(&w, m->n * es, s);
+  if (e != cudaSuccess) {
+    cudaFreeAsync(u, s);
+    return cuda_fail(e, "cudaMallocAsync");
+  }
+  cudaMemsetAsync(u, 0, m->n * es, s);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  *rep = sem_tune_report{};
+  rep->N = m->N;
+  rep->prec = prec;
+  sem_status st = SEM_OK;
+  for (int vi = 0; vi < 2 && st == SEM_OK; ++vi) {
+    const sem_ax_variant v = static_cast<sem_ax_variant>(vi);
+    if (v == SEM_AX_STORED && !has_factors(m, prec)) continue;
+    if (v == SEM_AX_OTF && prec == SEM_F64X) continue;
+    for (int shape = 0; shape < 2 && st == SEM_OK; ++shape) {
+      if (shape == 1 && (prec == SEM_F64X || ax_elements_per_block(m->N, 1) == ax_elements_per_block(m->N, 0)))
+        continue;
+      AxLaunch a{};
+      a.u = u;
+      a.w = w;
+      a.E = m->E;
+      a.err = m->dev_err;
+      a.shape = shape;
+      a.coef = prec == SEM_F32 ? static_cast<const void*>(m->coef32) : static_cast<const void*>(m->coef64);
+      a.G = prec == SEM_F32 ? static_cast<const void*>(m->G32) : static_cast<const void*>(m->G64);
+      auto launch = [&] {
+        if (prec == SEM_F64X) return launch_ax_f64x(m->N, v, false, a, s);
+        return prec == SEM_F64 ? launch_ax_f64(m->N, v, false, a, s) : launch_ax_f32(m->N, v, false, a, s);
+      };
+      for (int q = 0; q < 2 && st == SEM_OK; ++q) st = launch();
+      cudaEventRecord(e0, s);
+      for (int q = 0; q < reps && st == SEM_OK; ++q) st = launch();
+      cudaEventRecord(e1, s);
+      if (st != SEM_OK) break;
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      sem_tune_entry& c = rep->candidates[rep->n_candidates++];
+      c.variant = v;
+      c.shape = shape;
+      c.elements_per_block = prec == SEM_F64X ? 0 : ax_elements_per_block(m->N, shape);
+      c.ms = ms / reps;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFreeAsync(u, s);
+  cudaFreeAsync(w, s);
+  cudaStreamSynchronize(s);
+  if (st != SEM_OK) return st;
+  if (rep->n_candidates == 0) return fail(SEM_ERR_ARG, "no candidate implementation for this precision");
+  TuneSlot t;
+  t.valid = true;
+  double best = 1e300;
+  double best_v[2] = {1e300, 1e300};
+  for (int q = 0; q < rep->n_candidates; ++q) {
+    const sem_tune_entry& c = rep->candidates[q];
+    if (c.ms < best_v[c.variant]) {
+      best_v[c.variant] = c.ms;
+      t.shape[c.variant] = c.shape;
+      t.ms[c.variant] = c.ms;
+    }
+    if (c.ms < best) {
+      best = c.ms;
+      rep->best = q;
+      t.best = static_cast<sem_ax_variant>(c.variant);
+    }
+  }
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune[prec][m->N] = t;
+  return SEM_OK;
+}
+
+extern "C" sem_status sem_autotune_save(const char* path) {
+  if (!path) return fail(SEM_ERR_ARG, "null path");
+  std::ofstream f(path);
+  if (!f) return fail(SEM_ERR_ARG, std::string("cannot write ") + path);
+  f << "sem-autotune 1 " << device_name() << "\n";
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  for (int p = 0; p < 3; ++p)
+    for (int N = 1; N <= SEM_MAX_N; ++N) {
+      const TuneSlot& t = g_tune[p][N];
+      if (t.valid)
+        f << p << " " << N << " " << t.best << " " << t.shape[0] << " " << t.shape[1] << " " << t.ms[0] << " "
+          << t.ms[1] << "\n";
+    }
+  return f ? SEM_OK : fail(SEM_ERR_ARG, "write failed");
+}
+
+extern "C" sem_status sem_autotune_load(const char* path) {
+  if (!path) return fail(SEM_ERR_ARG, "null path");
+  std::ifstream f(path);
+  if (!f) return fail(SEM_ERR_ARG, std::string("cannot read ") + path);
+  std::string magic, gpu;
+  int version = 0;
+  f >> magic >> version >> gpu;
+  if (magic != "sem-autotune" || version != 1) return fail(SEM_ERR_ARG, "not a tuning table");
+  if (gpu != device_name()) return fail(SEM_ERR_ARG, "tuning table was made on " + gpu);
+  int p, N, best, s0, s1;
+  double m0, m1;
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  while (f >> p >> N >> best >> s0 >> s1 >> m0 >> m1) {
+    if (p < 0 || p > 2 || N < 1 || N > SEM_MAX_N || best < 0 || best > 1 || s0 < 0 || s0 > 1 || s1 < 0 || s1 > 1)
+      return fail(SEM_ERR_ARG, "corrupt tuning table");
+    TuneSlot& t = g_tune[p][N];
+    t.valid = true;
+    t.best = static_cast<sem_ax_variant>(best);
+    t.shape[0] = s0;
+    t.shape[1] = s1;
+    t.ms[0] = m0;
+    t.ms[1] = m1;
+  }
+  return SEM_OK;
 }

@@ -23,9 +23,19 @@
 
 namespace sem {
 
+// Elements per block: the default shape and the alternative the tuner also tries (block shape
+// choice 0 / 1). Both keep the two staging buffers of a block within 48 KB of shared memory.
 template <int NP>
 __host__ __device__ constexpr int ax_epb() {
   return NP <= 2 ? 32 : NP == 3 ? 16 : NP == 4 ? 8 : NP == 5 ? 5 : NP <= 7 ? (NP == 6 ? 4 : 3) : NP <= 9 ? 2 : 1;
+}
+template <int NP>
+__host__ __device__ constexpr int ax_epb_alt() {
+  return NP == 2 ? 16 : NP == 3 ? 8 : NP == 4 ? 4 : NP <= 6 ? 2 : NP <= 9 ? 1 : NP <= 11 ? 2 : 1;
+}
+template <int NP>
+__host__ __device__ constexpr int ax_epb_of(int choice) {
+  return choice == 0 ? ax_epb<NP>() : ax_epb_alt<NP>();
 }
 
 template <typename T>
@@ -49,12 +59,12 @@ __device__ __forceinline__ float div_fast<float>(float a, float b) {
   return __fdividef(a, b);
 }
 
-template <int NP, typename T, bool OTF, bool CG>
-__global__ void __launch_bounds__(NP * NP * ax_epb<NP>())
+template <int NP, typename T, bool OTF, bool CG, int EPB>
+__global__ void __launch_bounds__(NP * NP * EPB)
     k_ax(const __grid_constant__ GllParam<NP, T> tab, int64_t E, const T* __restrict__ u, T* __restrict__ w,
          const T* __restrict__ G, const T* __restrict__ coef, const T* __restrict__ z, T* __restrict__ p,
          CgScalars* __restrict__ st, double* __restrict__ partials) {
-  constexpr int NP2 = NP * NP, P = NP2 * NP, EPB = ax_epb<NP>();
+  constexpr int NP2 = NP * NP, P = NP2 * NP;
   __shared__ T sD[NP2];
   __shared__ T sXi[NP], sW[NP];
   __shared__ T sA[EPB][P];
@@ -186,29 +196,28 @@ __global__ void __launch_bounds__(NP * NP * ax_epb<NP>())
   }
 }
 
-template <int NP, typename T, bool OTF, bool CG>
+template <int NP, typename T, bool OTF, bool CG, int EPB>
 int ax_max_blocks() {
   // resident blocks per SM x SMs; computed once (thread-safe static initialisation)
   static const int cached = [] {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ax<NP, T, OTF, CG>, NP * NP * ax_epb<NP>(), 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ax<NP, T, OTF, CG, EPB>, NP * NP * EPB, 0);
     return (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
   }();
   return cached;
 }
 
-template <int NP, typename T, bool OTF, bool CG>
+template <int NP, typename T, bool OTF, bool CG, int EPB>
 sem_status launch_ax_t(int N, const AxLaunch& a, cudaStream_t s) {
-  constexpr int EPB = ax_epb<NP>();
   const int64_t groups = (a.E + EPB - 1) / EPB;
-  int grid = ax_max_blocks<NP, T, OTF, CG>();
+  int grid = ax_max_blocks<NP, T, OTF, CG, EPB>();
   if (grid > kRedMax) grid = kRedMax;
   if (groups < grid) grid = static_cast<int>(groups);
   if (a.grid_out) *a.grid_out = grid;
   const GllParam<NP, T> tab = make_gll_param<NP, T>(N);
-  k_ax<NP, T, OTF, CG><<<grid, NP * NP * EPB, 0, s>>>(
+  k_ax<NP, T, OTF, CG, EPB><<<grid, NP * NP * EPB, 0, s>>>(
       tab, a.E, static_cast<const T*>(a.u), static_cast<T*>(a.w), static_cast<const T*>(a.G),
       static_cast<const T*>(a.coef), static_cast<const T*>(a.z), static_cast<T*>(a.p), a.st, a.partials);
   count_launch();
@@ -216,29 +225,28 @@ sem_status launch_ax_t(int N, const AxLaunch& a, cudaStream_t s) {
   return SEM_OK;
 }
 
-// Dispatch over the variant and the mode for one order and precision.
-template <int NP, typename T>
-sem_status launch_ax_np(int N, sem_ax_variant v, bool cg, const AxLaunch& a, cudaStream_t s) {
+template <int NP, typename T, int EPB>
+sem_status launch_ax_shape(int N, sem_ax_variant v, bool cg, const AxLaunch& a, cudaStream_t s) {
   if (v == SEM_AX_OTF)
-    return cg ? launch_ax_t<NP, T, true, true>(N, a, s) : launch_ax_t<NP, T, true, false>(N, a, s);
-  return cg ? launch_ax_t<NP, T, false, true>(N, a, s) : launch_ax_t<NP, T, false, false>(N, a, s);
+    return cg ? launch_ax_t<NP, T, true, true, EPB>(N, a, s) : launch_ax_t<NP, T, true, false, EPB>(N, a, s);
+  return cg ? launch_ax_t<NP, T, false, true, EPB>(N, a, s) : launch_ax_t<NP, T, false, false, EPB>(N, a, s);
 }
 
-template <typename T>
-sem_status launch_ax_prec(int N, sem_ax_variant v, bool cg, const AxLaunch& a, cudaStream_t s) {
-  switch (N + 1) {
-    case 2: return launch_ax_np<2, T>(N, v, cg, a, s);
-    case 3: return launch_ax_np<3, T>(N, v, cg, a, s);
-    case 4: return launch_ax_np<4, T>(N, v, cg, a, s);
-    case 5: return launch_ax_np<5, T>(N, v, cg, a, s);
-    case 6: return launch_ax_np<6, T>(N, v, cg, a, s);
-    case 7: return launch_ax_np<7, T>(N, v, cg, a, s);
-    case 8: return launch_ax_np<8, T>(N, v, cg, a, s);
-    case 9: return launch_ax_np<9, T>(N, v, cg, a, s);
-    case 10: return launch_ax_np<10, T>(N, v, cg, a, s);
-    case 11: return launch_ax_np<11, T>(N, v, cg, a, s);
-    case 12: return launch_ax_np<12, T>(N, v, cg, a, s);
-    default: return fail(SEM_ERR_UNSUPPORTED, "polynomial order not compiled in");
+// Dispatch over the block shape, the variant and the mode for one order and precision.
+template <int NP, typename T>
+sem_status launch_ax_np(int N, sem_ax_variant v, bool cg, const AxLaunch& a, cudaStream_t s) {
+  if (a.shape == 1 && ax_epb_alt<NP>() != ax_epb<NP>()) return launch_ax_shape<NP, T, ax_epb_alt<NP>()>(N, v, cg, a, s);
+  return launch_ax_shape<NP, T, ax_epb<NP>()>(N, v, cg, a, s);
+}
+
+// Orders LO..HI (points per direction) of one precision; each translation unit compiles a range.
+template <typename T, int LO, int HI>
+sem_status launch_ax_range(int N, sem_ax_variant v, bool cg, const AxLaunch& a, cudaStream_t s) {
+  if constexpr (LO > HI) {
+    return fail(SEM_ERR_UNSUPPORTED, "polynomial order not compiled in");
+  } else {
+    if (N + 1 == LO) return launch_ax_np<LO, T>(N, v, cg, a, s);
+    return launch_ax_range<T, LO + 1, HI>(N, v, cg, a, s);
   }
 }
 

@@ -111,9 +111,20 @@ struct AxLaunch {
   double* partials;   // [gridDim.x] interior partial dots
   int* grid_out;      // receives gridDim.x used
   int* err;           // device error word (bounded waits that ran out write SEM_ERR_TIMEOUT)
+  int shape;          // block shape choice: 0 default elements per block, 1 the alternative
 };
-sem_status launch_ax_f64(int N, sem_ax_variant v, bool cg_mode, const AxLaunch& a, cudaStream_t s);
-sem_status launch_ax_f32(int N, sem_ax_variant v, bool cg_mode, const AxLaunch& a, cudaStream_t s);
+sem_status launch_ax_f64_lo(int N, sem_ax_variant v, bool cg_mode, const AxLaunch& a, cudaStream_t s);  // N+1 <= 7
+sem_status launch_ax_f64_hi(int N, sem_ax_variant v, bool cg_mode, const AxLaunch& a, cudaStream_t s);  // N+1 >= 8
+sem_status launch_ax_f32_lo(int N, sem_ax_variant v, bool cg_mode, const AxLaunch& a, cudaStream_t s);
+sem_status launch_ax_f32_hi(int N, sem_ax_variant v, bool cg_mode, const AxLaunch& a, cudaStream_t s);
+inline sem_status launch_ax_f64(int N, sem_ax_variant v, bool cg, const AxLaunch& a, cudaStream_t s) {
+  return N + 1 <= 7 ? launch_ax_f64_lo(N, v, cg, a, s) : launch_ax_f64_hi(N, v, cg, a, s);
+}
+inline sem_status launch_ax_f32(int N, sem_ax_variant v, bool cg, const AxLaunch& a, cudaStream_t s) {
+  return N + 1 <= 7 ? launch_ax_f32_lo(N, v, cg, a, s) : launch_ax_f32_hi(N, v, cg, a, s);
+}
+// elements per block of shape choice 0 / 1 for N + 1 points per direction (host side)
+int ax_elements_per_block(int N, int shape);
 sem_status launch_ax_f64x(int N, sem_ax_variant v, bool cg_mode, const AxLaunch& a, cudaStream_t s);
 // element type of a precision's data: FP64 for SEM_F64 and SEM_F64X
 inline sem_prec data_prec(sem_prec p) { return p == SEM_F32 ? SEM_F32 : SEM_F64; }

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_PKG, "libsem.so")
 SEM_OK, SEM_ERR_ARG, SEM_ERR_MESH, SEM_ERR_OOM, SEM_ERR_CUDA = 0, 1, 2, 3, 4
 SEM_ERR_NOT_CONVERGED, SEM_ERR_BREAKDOWN, SEM_ERR_TIMEOUT, SEM_ERR_BUSY, SEM_ERR_UNSUPPORTED = 5, 6, 7, 8, 9
 SEM_F64, SEM_F32, SEM_F64X = 0, 1, 2
-SEM_AX_STORED, SEM_AX_OTF = 0, 1
+SEM_AX_STORED, SEM_AX_OTF, SEM_AX_AUTO = 0, 1, 2
 SEM_MESH_F64_STORED, SEM_MESH_F32_STORED = 1, 2
 SEM_MAX_N = 11
 
@@ -29,7 +29,7 @@ EXPORTS = [
     "sem_glsc3", "sem_glsc3_noalloc", "sem_jacobi", "sem_rhs_sine", "sem_cg_default_opts", "sem_cg_solve", "sem_cg_create",
     "sem_cg_start", "sem_cg_iterate", "sem_cg_iterate_timed", "sem_cg_query", "sem_cg_destroy", "sem_launch_count", "sem_last_error",
     "sem_status_string", "sem_server_create", "sem_server_submit", "sem_server_poll", "sem_server_stats",
-    "sem_server_destroy",
+    "sem_server_destroy", "sem_autotune", "sem_autotune_save", "sem_autotune_load",
 ]
 
 
@@ -57,6 +57,19 @@ class CgResult(C.Structure):
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class TuneEntry(C.Structure):
+    _fields_ = [("variant", C.c_int), ("shape", C.c_int), ("elements_per_block", C.c_int), ("ms", C.c_double)]
+
+
+class TuneReport(C.Structure):
+    _fields_ = [("N", C.c_int), ("prec", C.c_int), ("n_candidates", C.c_int), ("candidates", TuneEntry * 4),
+                ("best", C.c_int)]
+
+    def as_dict(self):
+        cands = [{f: getattr(self.candidates[q], f) for f, _ in TuneEntry._fields_} for q in range(self.n_candidates)]
+        return {"N": self.N, "prec": self.prec, "candidates": cands, "best": self.best}
 
 
 class Request(C.Structure):
@@ -118,6 +131,9 @@ def load_library(path: str | None = None):
         "sem_server_poll": [_VP, C.c_uint64, _VP, _I64, C.POINTER(ServerResult)],
         "sem_server_stats": [_VP, C.POINTER(_I), C.POINTER(_I), C.POINTER(C.c_size_t)],
         "sem_server_destroy": [_VP],
+        "sem_autotune": [_VP, _I, _I, C.POINTER(TuneReport), _VP],
+        "sem_autotune_save": [C.c_char_p],
+        "sem_autotune_load": [C.c_char_p],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -403,6 +419,20 @@ def sem_server_stats(server):
 
 def sem_server_destroy(server):
     _check(load_library().sem_server_destroy(server))
+
+
+def sem_autotune(mesh, prec, reps=10, stream=None) -> dict:
+    rep = TuneReport()
+    _check(load_library().sem_autotune(mesh, int(prec), int(reps), C.byref(rep), _stream(stream)))
+    return rep.as_dict()
+
+
+def sem_autotune_save(path):
+    _check(load_library().sem_autotune_save(str(path).encode()))
+
+
+def sem_autotune_load(path):
+    _check(load_library().sem_autotune_load(str(path).encode()))
 
 
 def sem_launch_count() -> int:
