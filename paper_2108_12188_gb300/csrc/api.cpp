@@ -265,7 +265,8 @@ extern "C" sem_status sem_mesh_create(int N, int64_t nv, const double* vert_xyz,
   SEM_STEP(dmalloc(&m->coef64, static_cast<size_t>(E) * 24, &acc, s));
   SEM_STEP(dmalloc(&m->coef32, static_cast<size_t>(E) * 24, &acc, s));
   if (flags & SEM_MESH_F64_STORED) SEM_STEP(dmalloc(&m->G64, static_cast<size_t>(E * 6 * P), &acc, s));
-  if (flags & SEM_MESH_F32_STORED) SEM_STEP(dmalloc(&m->G32, static_cast<size_t>(E * 6 * P), &acc, s));
+  if (flags & SEM_MESH_F32_STORED)
+    SEM_STEP(dmalloc(&m->G32, static_cast<size_t>(E * factor_stride(m->Np, true)), &acc, s));
   SEM_STEP(dmalloc(&m->seg_off, T.seg_off.size(), &acc, s));
   SEM_STEP(dmalloc(&m->seg_idx, T.seg_idx.size(), &acc, s));
   SEM_STEP(dmalloc(&m->seg_mask, T.seg_mask.size(), &acc, s));
@@ -285,7 +286,8 @@ extern "C" sem_status sem_mesh_create(int N, int64_t nv, const double* vert_xyz,
   SEM_CSTEP(cudaMemsetAsync(bad, 0, sizeof(int), s));
   SEM_STEP(launch_coefficients(E, Xd, m->coef64, m->coef32, s));
   // geometric factors (and the det J > 0 check at every GLL point)
-  SEM_STEP(launch_geometry(N, E, m->coef64, m->G64, m->G32, nullptr, nullptr, bad, s));
+  SEM_STEP(launch_geometry(N, E, m->coef64, m->G64, m->G32, nullptr, nullptr, bad, factor_stride(m->Np, false),
+                           factor_stride(m->Np, true), s));
   int bad_h = 0;
   SEM_CSTEP(cudaMemcpyAsync(&bad_h, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
   SEM_CSTEP(cudaStreamSynchronize(s));
@@ -377,7 +379,8 @@ extern "C" sem_status sem_mesh_geometry(sem_mesh m, sem_prec prec, void* G, void
   sem_status st = launch_geometry(m->N, m->E, m->coef64, f64 ? static_cast<double*>(G) : nullptr,
                                   prec == SEM_F32 ? static_cast<float*>(G) : nullptr,
                                   f64 ? static_cast<double*>(B) : nullptr,
-                                  prec == SEM_F32 ? static_cast<float*>(B) : nullptr, bad, s);
+                                  prec == SEM_F32 ? static_cast<float*>(B) : nullptr, bad, 6LL * m->Np * m->Np * m->Np,
+                                  6LL * m->Np * m->Np * m->Np, s);
   cudaFreeAsync(bad, s);
   return st;
 }

@@ -8,6 +8,9 @@
 //              the element's trilinear coefficients (OTF, Section 5.1's rematerialisation)
 //   transpose: w = sum_l D_li vr(l,j,k) + sum_l D_lj vs(i,l,k) + sum_l D_lk vt(i,j,l)
 // The k-direction contractions stay in registers; D for it comes from the constant bank.
+// STORED: the six factor arrays of an element are one contiguous block; a bulk TMA copy
+// brings the next element group's blocks into shared memory while the current group runs
+// its transposed contractions (bounded mbarrier waits; a timeout sets SEM_ERR_TIMEOUT).
 //
 // OTF geometry without forming G: with g_b = dx/dxi_b (columns of J) and the cofactor
 // rows c_0 = g_1 x g_2, c_1 = g_2 x g_0, c_2 = g_0 x g_1 (c_b = det J * row b of J^-1),
@@ -20,6 +23,7 @@
 #pragma once
 
 #include "k_common.cuh"
+#include "k_tma.cuh"
 
 namespace sem {
 
@@ -59,16 +63,37 @@ __device__ __forceinline__ float div_fast<float>(float a, float b) {
   return __fdividef(a, b);
 }
 
+// Element stride of the stored factors (the mesh pads each element's [6][P] block to 16 bytes).
+template <int NP, typename T>
+__host__ __device__ constexpr int ax_gstride() {
+  return sizeof(T) == 8 ? 6 * NP * NP * NP : (6 * NP * NP * NP + 3) / 4 * 4;
+}
+
+// Dynamic shared memory of k_ax: [factors of the element group (STORED only, TMA target)]
+// [staging buffers A, B] [D] [xi, w] [mbarrier].
+template <int NP, typename T, bool OTF, int EPB>
+__host__ __device__ constexpr size_t ax_smem_bytes() {
+  constexpr size_t P = static_cast<size_t>(NP) * NP * NP;
+  return (OTF ? 0 : static_cast<size_t>(EPB) * ax_gstride<NP, T>() * sizeof(T)) + 2 * EPB * P * sizeof(T) +
+         (NP * NP + 2 * NP) * sizeof(T) + 16;
+}
+
 template <int NP, typename T, bool OTF, bool CG, int EPB>
 __global__ void __launch_bounds__(NP * NP * EPB)
     k_ax(const __grid_constant__ GllParam<NP, T> tab, int64_t E, const T* __restrict__ u, T* __restrict__ w,
          const T* __restrict__ G, const T* __restrict__ coef, const T* __restrict__ z, T* __restrict__ p,
-         CgScalars* __restrict__ st, double* __restrict__ partials) {
-  constexpr int NP2 = NP * NP, P = NP2 * NP;
-  __shared__ T sD[NP2];
-  __shared__ T sXi[NP], sW[NP];
-  __shared__ T sA[EPB][P];
-  __shared__ T sB[EPB][P];
+         CgScalars* __restrict__ st, double* __restrict__ partials, int* __restrict__ err) {
+  constexpr int NP2 = NP * NP, P = NP2 * NP, GS = ax_gstride<NP, T>();
+  constexpr size_t kG = OTF ? 0 : static_cast<size_t>(EPB) * GS;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  T* sG = reinterpret_cast<T*>(smem_raw);
+  T* sA = sG + kG;
+  T* sB = sA + EPB * P;
+  T* sD = sB + EPB * P;
+  T* sXi = sD + NP2;
+  T* sW = sXi + NP;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(
+      smem_raw + ((reinterpret_cast<uintptr_t>(sW + NP) - reinterpret_cast<uintptr_t>(smem_raw) + 7) & ~uintptr_t(7)));
   __shared__ double sRed[32];
 
   T beta = T(0);
@@ -81,12 +106,26 @@ __global__ void __launch_bounds__(NP * NP * EPB)
     sXi[q] = tab.xi[q];
     sW[q] = tab.w[q];
   }
+  const int64_t n_groups = (E + EPB - 1) / EPB;
+  constexpr unsigned kElemBytes = static_cast<unsigned>(GS * sizeof(T));
+  static_assert(OTF || kElemBytes % 16 == 0, "factor blocks must be whole 16-byte units");
+  if constexpr (!OTF) {
+    if (threadIdx.x == 0) {  // factors of the first group
+      mbar_init(bar, 1);
+      const int64_t e0 = static_cast<int64_t>(blockIdx.x) * EPB;
+      const int cnt = static_cast<int>(E - e0 < EPB ? E - e0 : EPB);
+      fence_proxy_async();
+      mbar_expect_tx(bar, kElemBytes * cnt);
+      for (int q = 0; q < cnt; ++q) tma_load_1d(sG + q * GS, G + (e0 + q) * GS, kElemBytes, bar);
+    }
+  }
   const int slot = threadIdx.x / NP2, tid = threadIdx.x % NP2;
   const int i = tid % NP, j = tid / NP;
   DotAcc<T> dot;
+  unsigned parity = 0;
   __syncthreads();
 
-  for (int64_t grp = blockIdx.x; grp * EPB < E; grp += gridDim.x) {
+  for (int64_t grp = blockIdx.x; grp < n_groups; grp += gridDim.x) {
     const int64_t e = grp * EPB + slot;
     const bool valid = e < E;
     const int64_t base = e * P + tid;
@@ -103,7 +142,7 @@ __global__ void __launch_bounds__(NP * NP * EPB)
         }
       }
       rU[k] = val;
-      sA[slot][k * NP2 + tid] = val;
+      sA[slot * P + k * NP2 + tid] = val;
     }
 
     // OTF: per-thread parts of the Jacobian columns that do not depend on k
@@ -125,6 +164,20 @@ __global__ void __launch_bounds__(NP * NP * EPB)
         Q1 = {a6.x + a7.x * xi, a6.y + a7.y * xi, a6.z + a7.z * xi};
         wij = sW[i] * sW[j];
       }
+    } else {
+      const bool ok = mbar_wait_bounded(bar, parity);
+      parity ^= 1u;
+      if (__syncthreads_or(!ok)) {  // the factor copy did not arrive: report and leave together
+        if (threadIdx.x == 0) {
+          mbar_wait_bounded(bar, parity ^ 1u);
+          atomicExch(err, static_cast<int>(SEM_ERR_TIMEOUT));
+          if constexpr (CG) {
+            st->status = SEM_ERR_TIMEOUT;
+            st->done = 1;
+          }
+        }
+        return;
+      }
     }
     __syncthreads();
 
@@ -134,8 +187,8 @@ __global__ void __launch_bounds__(NP * NP * EPB)
       T ur = T(0), us = T(0), ut = T(0);
 #pragma unroll
       for (int l = 0; l < NP; ++l) {
-        ur += sD[i * NP + l] * sA[slot][k * NP2 + j * NP + l];
-        us += sD[j * NP + l] * sA[slot][k * NP2 + l * NP + i];
+        ur += sD[i * NP + l] * sA[slot * P + k * NP2 + j * NP + l];
+        us += sD[j * NP + l] * sA[slot * P + k * NP2 + l * NP + i];
         ut += tab.D[k * NP + l] * rU[l];
       }
       if constexpr (OTF) {
@@ -151,26 +204,28 @@ __global__ void __launch_bounds__(NP * NP * EPB)
         rS[k] = s * dot3(c1, q);
         rT[k] = s * dot3(c2, q);
       } else {
-        T g11 = T(0), g12 = T(0), g13 = T(0), g22 = T(0), g23 = T(0), g33 = T(0);
-        if (valid) {
-          const T* gp = G + e * 6 * P + k * NP2 + tid;
-          g11 = gp[0 * P];
-          g12 = gp[1 * P];
-          g13 = gp[2 * P];
-          g22 = gp[3 * P];
-          g23 = gp[4 * P];
-          g33 = gp[5 * P];
-        }
+        const T* gp = sG + slot * GS + k * NP2 + tid;
+        const T g11 = gp[0 * P], g12 = gp[1 * P], g13 = gp[2 * P], g22 = gp[3 * P], g23 = gp[4 * P],
+                g33 = gp[5 * P];
         rR[k] = g11 * ur + g12 * us + g13 * ut;
         rS[k] = g12 * ur + g22 * us + g23 * ut;
         rT[k] = g13 * ur + g23 * us + g33 * ut;
       }
     }
-    __syncthreads();
+    __syncthreads();  // staging buffer A (the field) and the factors are consumed
+    if constexpr (!OTF) {
+      if (threadIdx.x == 0 && grp + gridDim.x < n_groups) {  // next group's factors, during the rest
+        const int64_t e0 = (grp + gridDim.x) * EPB;
+        const int cnt = static_cast<int>(E - e0 < EPB ? E - e0 : EPB);
+        fence_proxy_async();
+        mbar_expect_tx(bar, kElemBytes * cnt);
+        for (int q = 0; q < cnt; ++q) tma_load_1d(sG + q * GS, G + (e0 + q) * GS, kElemBytes, bar);
+      }
+    }
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
-      sA[slot][k * NP2 + tid] = rR[k];
-      sB[slot][k * NP2 + tid] = rS[k];
+      sA[slot * P + k * NP2 + tid] = rR[k];
+      sB[slot * P + k * NP2 + tid] = rS[k];
     }
     __syncthreads();
 #pragma unroll
@@ -178,8 +233,8 @@ __global__ void __launch_bounds__(NP * NP * EPB)
       T acc = T(0);
 #pragma unroll
       for (int l = 0; l < NP; ++l) {
-        acc += sD[l * NP + i] * sA[slot][k * NP2 + j * NP + l];
-        acc += sD[l * NP + j] * sB[slot][k * NP2 + l * NP + i];
+        acc += sD[l * NP + i] * sA[slot * P + k * NP2 + j * NP + l];
+        acc += sD[l * NP + j] * sB[slot * P + k * NP2 + l * NP + i];
         acc += tab.D[l * NP + k] * rT[l];
       }
       if (valid) w[base + k * NP2] = acc;
@@ -200,10 +255,13 @@ template <int NP, typename T, bool OTF, bool CG, int EPB>
 int ax_max_blocks() {
   // resident blocks per SM x SMs; computed once (thread-safe static initialisation)
   static const int cached = [] {
+    constexpr size_t smem = ax_smem_bytes<NP, T, OTF, EPB>();
+    cudaFuncSetAttribute(k_ax<NP, T, OTF, CG, EPB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         static_cast<int>(smem));
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ax<NP, T, OTF, CG, EPB>, NP * NP * EPB, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ax<NP, T, OTF, CG, EPB>, NP * NP * EPB, smem);
     return (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
   }();
   return cached;
@@ -217,9 +275,9 @@ sem_status launch_ax_t(int N, const AxLaunch& a, cudaStream_t s) {
   if (groups < grid) grid = static_cast<int>(groups);
   if (a.grid_out) *a.grid_out = grid;
   const GllParam<NP, T> tab = make_gll_param<NP, T>(N);
-  k_ax<NP, T, OTF, CG, EPB><<<grid, NP * NP * EPB, 0, s>>>(
+  k_ax<NP, T, OTF, CG, EPB><<<grid, NP * NP * EPB, ax_smem_bytes<NP, T, OTF, EPB>(), s>>>(
       tab, a.E, static_cast<const T*>(a.u), static_cast<T*>(a.w), static_cast<const T*>(a.G),
-      static_cast<const T*>(a.coef), static_cast<const T*>(a.z), static_cast<T*>(a.p), a.st, a.partials);
+      static_cast<const T*>(a.coef), static_cast<const T*>(a.z), static_cast<T*>(a.p), a.st, a.partials, a.err);
   count_launch();
   SEM_CUDA_TRY(cudaGetLastError());
   return SEM_OK;

@@ -51,6 +51,14 @@ struct CgScalars {
   unsigned int ticket[4];            // last-block-done counters (reset by the last block)
 };
 
+// Element stride (in elements of the factor type) of the mesh's stored-factor arrays: the six
+// P-point arrays of an element, padded so that every element block starts and ends on a
+// 16-byte boundary (bulk TMA copies need both). FP64 blocks (48 P bytes) need no padding.
+inline int64_t factor_stride(int Np, bool fp32) {
+  const int64_t s = 6LL * Np * Np * Np;
+  return fp32 ? (s + 3) / 4 * 4 : s;
+}
+
 // ---- reduction scratch ----
 constexpr int kRedMax = 8192;  // upper bound of blocks of any reducing launch
 
@@ -67,7 +75,7 @@ struct sem_mesh_s {
   double* coef64 = nullptr;   // [E][24] trilinear coefficients a0..a7 (x, y, z)
   float* coef32 = nullptr;    // [E][24] rounded to FP32
   double* G64 = nullptr;      // [E][6][P] or null
-  float* G32 = nullptr;       // [E][6][P] or null
+  float* G32 = nullptr;       // [E][factor_stride] (the [6][P] block, padded to 16 bytes) or null
   int32_t* seg_off = nullptr;
   int32_t* seg_idx = nullptr;
   uint8_t* seg_mask = nullptr;
@@ -131,8 +139,9 @@ inline sem_prec data_prec(sem_prec p) { return p == SEM_F32 ? SEM_F32 : SEM_F64;
 
 // element geometry (k_mesh.cu)
 sem_status launch_coefficients(int64_t E, const double* X, double* coef64, float* coef32, cudaStream_t s);
+// G64 / G32 (either may be null) are written with element strides gs64 / gs32.
 sem_status launch_geometry(int N, int64_t E, const double* coef64, double* G64, float* G32, double* B64,
-                           float* B32, int* bad_flag, cudaStream_t s);
+                           float* B32, int* bad_flag, int64_t gs64, int64_t gs32, cudaStream_t s);
 sem_status launch_coords(int N, int64_t E, const double* coef64, double* xyz, int64_t n, cudaStream_t s);
 sem_status launch_local_diag(int N, int64_t E, const double* coef64, double* d, cudaStream_t s);
 sem_status launch_rhs_local(int N, int64_t E, const double* coef64, int a, int b, int c, double* out,
