@@ -53,6 +53,8 @@ def ax_bytes_per_point(variant: str, prec: str, N: int) -> float:
     P = (N + 1) ** 3
     if variant == "stored":
         return word * (1 + 1 + 6)
+    if variant == "otfscale":  # u, w and the per-point scale w/det J, plus the coefficients
+        return word * (1 + 1 + 1) + word * 21 / P
     return word * (1 + 1) + word * 21 / P  # 21 trilinear coefficients per element
 
 
@@ -338,7 +340,8 @@ def run_gpu(args):
     hbm_gbs, peak_src = measured_peaks()
 
     m = BoxMesh(NEL, NEL, NEL, jitter=JITTER, seed=SEED)
-    mesh = sem.Mesh(NORD, m.vert_xyz, m.elem_verts, flags=sem.SEM_MESH_F64_STORED | sem.SEM_MESH_F32_STORED)
+    mesh = sem.Mesh(NORD, m.vert_xyz, m.elem_verts,
+                    flags=sem.SEM_MESH_F64_STORED | sem.SEM_MESH_F32_STORED | sem.SEM_MESH_OTF_SCALE)
     n = mesh.n
     info = mesh.info
     u_glob = torch.tensor(global_field(info["n_glob"], SEED, start=m.draws_used), dtype=torch.float64, device="cuda")
@@ -404,7 +407,9 @@ def run_gpu(args):
                                         ("stored", sem.SEM_AX_STORED, "f64x", sem.SEM_F64X),
                                         ("stored", sem.SEM_AX_STORED, "f32", sem.SEM_F32),
                                         ("otf", sem.SEM_AX_OTF, "f64", sem.SEM_F64),
-                                        ("otf", sem.SEM_AX_OTF, "f32", sem.SEM_F32)):
+                                        ("otf", sem.SEM_AX_OTF, "f32", sem.SEM_F32),
+                                        ("otfscale", sem.SEM_AX_OTF_SCALE, "f64", sem.SEM_F64),
+                                        ("otfscale", sem.SEM_AX_OTF_SCALE, "f32", sem.SEM_F32)):
         dt = torch.float32 if prec == sem.SEM_F32 else torch.float64
         u = x0.to(dt)
         w = torch.empty_like(u)

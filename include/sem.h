@@ -64,9 +64,12 @@ typedef enum { SEM_F64 = 0, SEM_F32 = 1, SEM_F64X = 2 } sem_prec;
 /* Variants of the local operator A_L (Section 5.1):
  * STORED reads the six geometric factors per point from device memory;
  * OTF recomputes them per point from 21 per-element trilinear-map coefficients;
+ * OTF_SCALE recomputes them too but reads one word per point, w_i w_j w_k / det J, so the
+ *   per-point division is not repeated (the rematerialisation of Section 5.1 with an I/O
+ *   cost of one word per point); needs SEM_MESH_OTF_SCALE;
  * AUTO uses the variant and block shape sem_autotune found fastest for this order and
  * precision (before tuning: STORED if the mesh holds the factors, else OTF). */
-typedef enum { SEM_AX_STORED = 0, SEM_AX_OTF = 1, SEM_AX_AUTO = 2 } sem_ax_variant;
+typedef enum { SEM_AX_STORED = 0, SEM_AX_OTF = 1, SEM_AX_AUTO = 2, SEM_AX_OTF_SCALE = 3 } sem_ax_variant;
 
 #define SEM_MAX_N 11 /* polynomial orders 1..11 are compiled in */
 
@@ -74,6 +77,7 @@ typedef enum { SEM_AX_STORED = 0, SEM_AX_OTF = 1, SEM_AX_AUTO = 2 } sem_ax_varia
  * The per-element coefficients for the OTF variant are always kept (FP64 and FP32). */
 #define SEM_MESH_F64_STORED 1u /* G in FP64: 48 bytes per local point */
 #define SEM_MESH_F32_STORED 2u /* G in FP32: 24 bytes per local point */
+#define SEM_MESH_OTF_SCALE 4u  /* w_i w_j w_k / det J per point, FP64 and FP32: 12 bytes per local point */
 
 typedef struct sem_mesh_s* sem_mesh;
 typedef struct sem_cg_s* sem_cg;
@@ -191,8 +195,9 @@ sem_status sem_jacobi(sem_mesh mesh, sem_prec prec, void* minv_dev, void* stream
 sem_status sem_rhs_sine(sem_mesh mesh, int a, int b, int c, sem_prec prec, void* rhs_dev, void* stream);
 
 /* ---- Autotuning of the local operator ----
- * sem_autotune times every candidate implementation of A_L on this mesh (stored or
- * on-the-fly factors where available, times two block shapes: elements per thread block)
+ * sem_autotune times every candidate implementation of A_L on this mesh (stored, on-the-fly
+ * or on-the-fly with per-point scale where available, times two block shapes: elements per
+ * thread block; the per-point-scale variant has one shape)
  * with CUDA events over `reps` launches each, and records the fastest for the mesh's order
  * and the precision, process-wide; SEM_AX_AUTO then uses it, and explicit variants use the
  * faster block shape. Synchronises `stream`. sem_autotune_save / sem_autotune_load write and
@@ -209,7 +214,7 @@ typedef struct {
   int N;
   int prec;
   int n_candidates;
-  sem_tune_entry candidates[4];
+  sem_tune_entry candidates[6];
   int best;               /* index into candidates */
 } sem_tune_report;
 

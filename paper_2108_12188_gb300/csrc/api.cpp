@@ -112,6 +112,8 @@ void free_mesh(sem_mesh m) {
   dfree(m->coef32, h);
   dfree(m->G64, h);
   dfree(m->G32, h);
+  dfree(m->scale64, h);
+  dfree(m->scale32, h);
   dfree(m->seg_off, h);
   dfree(m->seg_idx, h);
   dfree(m->seg_mask, h);
@@ -135,13 +137,15 @@ void free_mesh(sem_mesh m) {
 struct TuneSlot {
   bool valid = false;
   sem_ax_variant best = SEM_AX_STORED;
-  int shape[2] = {0, 0};
-  double ms[2] = {0, 0};
+  int shape[3] = {0, 0, 0};  // per variant slot: STORED, OTF, OTF_SCALE
+  double ms[3] = {0, 0, 0};
 };
+inline int vslot(sem_ax_variant v) { return v == SEM_AX_OTF_SCALE ? 2 : static_cast<int>(v); }
 std::mutex g_tune_mu;
 TuneSlot g_tune[3][SEM_MAX_N + 1];
 
 bool has_factors(sem_mesh m, sem_prec prec) { return prec == SEM_F32 ? m->G32 != nullptr : m->G64 != nullptr; }
+bool has_scales(sem_mesh m) { return m->scale64 != nullptr; }
 
 // Resolves SEM_AX_AUTO and picks the tuned block shape.
 void resolve_variant(sem_mesh m, sem_prec prec, sem_ax_variant v, sem_ax_variant* out_v, int* out_shape) {
@@ -149,12 +153,15 @@ void resolve_variant(sem_mesh m, sem_prec prec, sem_ax_variant v, sem_ax_variant
   const TuneSlot& t = g_tune[prec][m->N];
   sem_ax_variant r = v;
   if (v == SEM_AX_AUTO) {
-    if (t.valid && (t.best == SEM_AX_OTF || has_factors(m, prec))) r = t.best;
-    else r = has_factors(m, prec) ? SEM_AX_STORED : SEM_AX_OTF;
+    if (t.valid && (t.best == SEM_AX_OTF || (t.best == SEM_AX_STORED && has_factors(m, prec)) ||
+                    (t.best == SEM_AX_OTF_SCALE && has_scales(m))))
+      r = t.best;
+    else
+      r = has_factors(m, prec) ? SEM_AX_STORED : SEM_AX_OTF;
     if (prec == SEM_F64X) r = SEM_AX_STORED;
   }
   *out_v = r;
-  *out_shape = t.valid ? t.shape[r] : 0;
+  *out_shape = t.valid ? t.shape[vslot(r)] : 0;
 }
 
 sem_status launch_ax_any(sem_mesh m, sem_prec prec, sem_ax_variant v, bool cg, AxLaunch a, cudaStream_t s) {
@@ -164,8 +171,11 @@ sem_status launch_ax_any(sem_mesh m, sem_prec prec, sem_ax_variant v, bool cg, A
   const bool fp64_data = prec != SEM_F32;
   a.coef = fp64_data ? static_cast<const void*>(m->coef64) : static_cast<const void*>(m->coef32);
   a.G = fp64_data ? static_cast<const void*>(m->G64) : static_cast<const void*>(m->G32);
+  a.scale = fp64_data ? static_cast<const void*>(m->scale64) : static_cast<const void*>(m->scale32);
   if (v == SEM_AX_STORED && !a.G)
     return fail(SEM_ERR_ARG, "stored factors of this precision were not requested at mesh creation");
+  if (v == SEM_AX_OTF_SCALE && !a.scale)
+    return fail(SEM_ERR_ARG, "per-point scales were not requested at mesh creation (SEM_MESH_OTF_SCALE)");
   if (prec == SEM_F64X) return launch_ax_f64x(m->N, v, cg, a, s);
   return prec == SEM_F64 ? launch_ax_f64(m->N, v, cg, a, s) : launch_ax_f32(m->N, v, cg, a, s);
 }
@@ -211,7 +221,8 @@ extern "C" sem_status sem_mesh_create(int N, int64_t nv, const double* vert_xyz,
   if (!out) return fail(SEM_ERR_ARG, "out is null");
   *out = nullptr;
   if (!vert_xyz || !elem_verts) return fail(SEM_ERR_ARG, "vert_xyz and elem_verts must be given");
-  if (flags & ~(SEM_MESH_F64_STORED | SEM_MESH_F32_STORED)) return fail(SEM_ERR_ARG, "unknown mesh flags");
+  if (flags & ~(SEM_MESH_F64_STORED | SEM_MESH_F32_STORED | SEM_MESH_OTF_SCALE))
+    return fail(SEM_ERR_ARG, "unknown mesh flags");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   Topology T;
   SEM_TRY(build_topology(N, nv, E, elem_verts, dflags, T));
@@ -267,6 +278,10 @@ extern "C" sem_status sem_mesh_create(int N, int64_t nv, const double* vert_xyz,
   if (flags & SEM_MESH_F64_STORED) SEM_STEP(dmalloc(&m->G64, static_cast<size_t>(E * 6 * P), &acc, s));
   if (flags & SEM_MESH_F32_STORED)
     SEM_STEP(dmalloc(&m->G32, static_cast<size_t>(E * factor_stride(m->Np, true)), &acc, s));
+  if (flags & SEM_MESH_OTF_SCALE) {
+    SEM_STEP(dmalloc(&m->scale64, static_cast<size_t>(E * P), &acc, s));
+    SEM_STEP(dmalloc(&m->scale32, static_cast<size_t>(E * P), &acc, s));
+  }
   SEM_STEP(dmalloc(&m->seg_off, T.seg_off.size(), &acc, s));
   SEM_STEP(dmalloc(&m->seg_idx, T.seg_idx.size(), &acc, s));
   SEM_STEP(dmalloc(&m->seg_mask, T.seg_mask.size(), &acc, s));
@@ -287,7 +302,7 @@ extern "C" sem_status sem_mesh_create(int N, int64_t nv, const double* vert_xyz,
   SEM_STEP(launch_coefficients(E, Xd, m->coef64, m->coef32, s));
   // geometric factors (and the det J > 0 check at every GLL point)
   SEM_STEP(launch_geometry(N, E, m->coef64, m->G64, m->G32, nullptr, nullptr, bad, factor_stride(m->Np, false),
-                           factor_stride(m->Np, true), s));
+                           factor_stride(m->Np, true), s, m->scale64, m->scale32));
   int bad_h = 0;
   SEM_CSTEP(cudaMemcpyAsync(&bad_h, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
   SEM_CSTEP(cudaStreamSynchronize(s));
@@ -410,7 +425,7 @@ extern "C" sem_status sem_ax(sem_mesh m, sem_ax_variant v, sem_prec prec, const 
                              void* stream) {
   SEM_TRY(check_mesh(m));
   SEM_TRY(check_prec(prec));
-  if (v != SEM_AX_STORED && v != SEM_AX_OTF && v != SEM_AX_AUTO) return fail(SEM_ERR_ARG, "unknown Ax variant");
+  if (v < SEM_AX_STORED || v > SEM_AX_OTF_SCALE) return fail(SEM_ERR_ARG, "unknown Ax variant");
   SEM_TRY(check_ptr(u, "u_dev"));
   SEM_TRY(check_ptr(w, "w_dev"));
   if (u == w) return fail(SEM_ERR_ARG, "u and w must not overlap");
@@ -538,8 +553,10 @@ sem_status cg_alloc(sem_mesh m, sem_prec prec, sem_ax_variant v, int precond, do
   *out = nullptr;
   if (v == SEM_AX_STORED && !(prec == SEM_F32 ? m->G32 != nullptr : m->G64 != nullptr))
     return fail(SEM_ERR_ARG, "stored factors of this precision were not requested at mesh creation");
-  if (prec == SEM_F64X && v == SEM_AX_OTF)
+  if (prec == SEM_F64X && (v == SEM_AX_OTF || v == SEM_AX_OTF_SCALE))
     return fail(SEM_ERR_UNSUPPORTED, "double-float FP64 arithmetic runs the stored-factor variant only");
+  if (v == SEM_AX_OTF_SCALE && !has_scales(m))
+    return fail(SEM_ERR_ARG, "per-point scales were not requested at mesh creation (SEM_MESH_OTF_SCALE)");
   sem_cg c = new sem_cg_s();
   c->m = m;
   c->prec = prec;
@@ -698,8 +715,9 @@ sem_status cg_query(sem_cg c, sem_cg_result* res, cudaStream_t s) {
 sem_status check_opts(const sem_cg_opts* o) {
   if (!o) return fail(SEM_ERR_ARG, "opts is null");
   if (!(o->rtol >= 0) || o->max_iter < 0 || o->check_every < 1 || (o->precond != 0 && o->precond != 1) ||
-      (o->variant < SEM_AX_STORED || o->variant > SEM_AX_AUTO) ||
-      (o->inner_variant < SEM_AX_STORED || o->inner_variant > SEM_AX_AUTO) || (o->f64_arith != 0 && o->f64_arith != 1))
+      (o->variant < SEM_AX_STORED || o->variant > SEM_AX_OTF_SCALE) ||
+      (o->inner_variant < SEM_AX_STORED || o->inner_variant > SEM_AX_OTF_SCALE) ||
+      (o->f64_arith != 0 && o->f64_arith != 1))
     return fail(SEM_ERR_ARG, "invalid CG options");
   if (o->mixed && (!(o->inner_rtol > 0 && o->inner_rtol < 1) || o->max_outer < 1))
     return fail(SEM_ERR_ARG, "mixed precision needs 0 < inner_rtol < 1 and max_outer >= 1");
@@ -1023,12 +1041,14 @@ extern "C" sem_status sem_autotune(sem_mesh m, sem_prec prec, int reps, sem_tune
   rep->N = m->N;
   rep->prec = prec;
   sem_status st = SEM_OK;
-  for (int vi = 0; vi < 2 && st == SEM_OK; ++vi) {
-    const sem_ax_variant v = static_cast<sem_ax_variant>(vi);
+  for (const sem_ax_variant v : {SEM_AX_STORED, SEM_AX_OTF, SEM_AX_OTF_SCALE}) {
+    if (st != SEM_OK) break;
     if (v == SEM_AX_STORED && !has_factors(m, prec)) continue;
-    if (v == SEM_AX_OTF && prec == SEM_F64X) continue;
+    if (v != SEM_AX_STORED && prec == SEM_F64X) continue;
+    if (v == SEM_AX_OTF_SCALE && !has_scales(m)) continue;
     for (int shape = 0; shape < 2 && st == SEM_OK; ++shape) {
-      if (shape == 1 && (prec == SEM_F64X || ax_elements_per_block(m->N, 1) == ax_elements_per_block(m->N, 0)))
+      if (shape == 1 && (prec == SEM_F64X || v == SEM_AX_OTF_SCALE ||
+                         ax_elements_per_block(m->N, 1) == ax_elements_per_block(m->N, 0)))
         continue;
       AxLaunch a{};
       a.u = u;
@@ -1038,6 +1058,7 @@ extern "C" sem_status sem_autotune(sem_mesh m, sem_prec prec, int reps, sem_tune
       a.shape = shape;
       a.coef = prec == SEM_F32 ? static_cast<const void*>(m->coef32) : static_cast<const void*>(m->coef64);
       a.G = prec == SEM_F32 ? static_cast<const void*>(m->G32) : static_cast<const void*>(m->G64);
+      a.scale = prec == SEM_F32 ? static_cast<const void*>(m->scale32) : static_cast<const void*>(m->scale64);
       auto launch = [&] {
         if (prec == SEM_F64X) return launch_ax_f64x(m->N, v, false, a, s);
         return prec == SEM_F64 ? launch_ax_f64(m->N, v, false, a, s) : launch_ax_f32(m->N, v, false, a, s);
@@ -1067,13 +1088,14 @@ extern "C" sem_status sem_autotune(sem_mesh m, sem_prec prec, int reps, sem_tune
   TuneSlot t;
   t.valid = true;
   double best = 1e300;
-  double best_v[2] = {1e300, 1e300};
+  double best_v[3] = {1e300, 1e300, 1e300};
   for (int q = 0; q < rep->n_candidates; ++q) {
     const sem_tune_entry& c = rep->candidates[q];
-    if (c.ms < best_v[c.variant]) {
-      best_v[c.variant] = c.ms;
-      t.shape[c.variant] = c.shape;
-      t.ms[c.variant] = c.ms;
+    const int slot = vslot(static_cast<sem_ax_variant>(c.variant));
+    if (c.ms < best_v[slot]) {
+      best_v[slot] = c.ms;
+      t.shape[slot] = c.shape;
+      t.ms[slot] = c.ms;
     }
     if (c.ms < best) {
       best = c.ms;
@@ -1090,14 +1112,14 @@ extern "C" sem_status sem_autotune_save(const char* path) {
   if (!path) return fail(SEM_ERR_ARG, "null path");
   std::ofstream f(path);
   if (!f) return fail(SEM_ERR_ARG, std::string("cannot write ") + path);
-  f << "sem-autotune 1 " << device_name() << "\n";
+  f << "sem-autotune 2 " << device_name() << "\n";
   std::lock_guard<std::mutex> lock(g_tune_mu);
   for (int p = 0; p < 3; ++p)
     for (int N = 1; N <= SEM_MAX_N; ++N) {
       const TuneSlot& t = g_tune[p][N];
       if (t.valid)
-        f << p << " " << N << " " << t.best << " " << t.shape[0] << " " << t.shape[1] << " " << t.ms[0] << " "
-          << t.ms[1] << "\n";
+        f << p << " " << N << " " << t.best << " " << t.shape[0] << " " << t.shape[1] << " " << t.shape[2] << " "
+          << t.ms[0] << " " << t.ms[1] << " " << t.ms[2] << "\n";
     }
   return f ? SEM_OK : fail(SEM_ERR_ARG, "write failed");
 }
@@ -1109,21 +1131,24 @@ extern "C" sem_status sem_autotune_load(const char* path) {
   std::string magic, gpu;
   int version = 0;
   f >> magic >> version >> gpu;
-  if (magic != "sem-autotune" || version != 1) return fail(SEM_ERR_ARG, "not a tuning table");
+  if (magic != "sem-autotune" || version != 2) return fail(SEM_ERR_ARG, "not a tuning table");
   if (gpu != device_name()) return fail(SEM_ERR_ARG, "tuning table was made on " + gpu);
-  int p, N, best, s0, s1;
-  double m0, m1;
+  int p, N, best, s0, s1, s2;
+  double m0, m1, m2;
   std::lock_guard<std::mutex> lock(g_tune_mu);
-  while (f >> p >> N >> best >> s0 >> s1 >> m0 >> m1) {
-    if (p < 0 || p > 2 || N < 1 || N > SEM_MAX_N || best < 0 || best > 1 || s0 < 0 || s0 > 1 || s1 < 0 || s1 > 1)
+  while (f >> p >> N >> best >> s0 >> s1 >> s2 >> m0 >> m1 >> m2) {
+    if (p < 0 || p > 2 || N < 1 || N > SEM_MAX_N || !(best == 0 || best == 1 || best == 3) || s0 < 0 || s0 > 1 ||
+        s1 < 0 || s1 > 1 || s2 != 0)
       return fail(SEM_ERR_ARG, "corrupt tuning table");
     TuneSlot& t = g_tune[p][N];
     t.valid = true;
     t.best = static_cast<sem_ax_variant>(best);
     t.shape[0] = s0;
     t.shape[1] = s1;
+    t.shape[2] = s2;
     t.ms[0] = m0;
     t.ms[1] = m1;
+    t.ms[2] = m2;
   }
   return SEM_OK;
 }

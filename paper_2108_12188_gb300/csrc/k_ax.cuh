@@ -71,18 +71,22 @@ __host__ __device__ constexpr int ax_gstride() {
 
 // Dynamic shared memory of k_ax: [factors of the element group (STORED only, TMA target)]
 // [staging buffers A, B] [D] [xi, w] [mbarrier].
-template <int NP, typename T, bool OTF, int EPB>
+template <int NP, typename T, int GEO, int EPB>
 __host__ __device__ constexpr size_t ax_smem_bytes() {
   constexpr size_t P = static_cast<size_t>(NP) * NP * NP;
-  return (OTF ? 0 : static_cast<size_t>(EPB) * ax_gstride<NP, T>() * sizeof(T)) + 2 * EPB * P * sizeof(T) +
+  return (GEO != 0 ? 0 : static_cast<size_t>(EPB) * ax_gstride<NP, T>() * sizeof(T)) + 2 * EPB * P * sizeof(T) +
          (NP * NP + 2 * NP) * sizeof(T) + 16;
 }
 
-template <int NP, typename T, bool OTF, bool CG, int EPB>
+// GEO: 0 stored factors, 1 factors recomputed from the element coefficients, 2 recomputed
+// with the per-point scale w_i w_j w_k / det J read from memory (one word per point, the
+// division moved out of the kernel: Section 5.1's rematerialisation with I/O cost n).
+template <int NP, typename T, int GEO, bool CG, int EPB>
 __global__ void __launch_bounds__(NP * NP * EPB)
     k_ax(const __grid_constant__ GllParam<NP, T> tab, int64_t E, const T* __restrict__ u, T* __restrict__ w,
-         const T* __restrict__ G, const T* __restrict__ coef, const T* __restrict__ z, T* __restrict__ p,
-         CgScalars* __restrict__ st, double* __restrict__ partials, int* __restrict__ err) {
+         const T* __restrict__ G, const T* __restrict__ coef, const T* __restrict__ scale, const T* __restrict__ z,
+         T* __restrict__ p, CgScalars* __restrict__ st, double* __restrict__ partials, int* __restrict__ err) {
+  constexpr bool OTF = GEO != 0;
   constexpr int NP2 = NP * NP, P = NP2 * NP, GS = ax_gstride<NP, T>();
   constexpr size_t kG = OTF ? 0 : static_cast<size_t>(EPB) * GS;
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -196,8 +200,13 @@ __global__ void __launch_bounds__(NP * NP * EPB)
         const Vec3<T> g0{P0.x + gam * Q0.x, P0.y + gam * Q0.y, P0.z + gam * Q0.z};
         const Vec3<T> g1{P1.x + gam * Q1.x, P1.y + gam * Q1.y, P1.z + gam * Q1.z};
         const Vec3<T> c0 = cross(g1, g2), c1 = cross(g2, g0), c2 = cross(g0, g1);
-        const T det = dot3(g0, c0);
-        const T s = valid ? div_fast(wij * tab.w[k], det) : T(0);
+        T s;
+        if constexpr (GEO == 2) {
+          s = valid ? scale[base + k * NP2] : T(0);
+        } else {
+          const T det = dot3(g0, c0);
+          s = valid ? div_fast(wij * tab.w[k], det) : T(0);
+        }
         const Vec3<T> q{c0.x * ur + c1.x * us + c2.x * ut, c0.y * ur + c1.y * us + c2.y * ut,
                         c0.z * ur + c1.z * us + c2.z * ut};
         rR[k] = s * dot3(c0, q);
@@ -251,33 +260,34 @@ __global__ void __launch_bounds__(NP * NP * EPB)
   }
 }
 
-template <int NP, typename T, bool OTF, bool CG, int EPB>
+template <int NP, typename T, int GEO, bool CG, int EPB>
 int ax_max_blocks() {
   // resident blocks per SM x SMs; computed once (thread-safe static initialisation)
   static const int cached = [] {
-    constexpr size_t smem = ax_smem_bytes<NP, T, OTF, EPB>();
-    cudaFuncSetAttribute(k_ax<NP, T, OTF, CG, EPB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    constexpr size_t smem = ax_smem_bytes<NP, T, GEO, EPB>();
+    cudaFuncSetAttribute(k_ax<NP, T, GEO, CG, EPB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          static_cast<int>(smem));
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ax<NP, T, OTF, CG, EPB>, NP * NP * EPB, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ax<NP, T, GEO, CG, EPB>, NP * NP * EPB, smem);
     return (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
   }();
   return cached;
 }
 
-template <int NP, typename T, bool OTF, bool CG, int EPB>
+template <int NP, typename T, int GEO, bool CG, int EPB>
 sem_status launch_ax_t(int N, const AxLaunch& a, cudaStream_t s) {
   const int64_t groups = (a.E + EPB - 1) / EPB;
-  int grid = ax_max_blocks<NP, T, OTF, CG, EPB>();
+  int grid = ax_max_blocks<NP, T, GEO, CG, EPB>();
   if (grid > kRedMax) grid = kRedMax;
   if (groups < grid) grid = static_cast<int>(groups);
   if (a.grid_out) *a.grid_out = grid;
   const GllParam<NP, T> tab = make_gll_param<NP, T>(N);
-  k_ax<NP, T, OTF, CG, EPB><<<grid, NP * NP * EPB, ax_smem_bytes<NP, T, OTF, EPB>(), s>>>(
+  k_ax<NP, T, GEO, CG, EPB><<<grid, NP * NP * EPB, ax_smem_bytes<NP, T, GEO, EPB>(), s>>>(
       tab, a.E, static_cast<const T*>(a.u), static_cast<T*>(a.w), static_cast<const T*>(a.G),
-      static_cast<const T*>(a.coef), static_cast<const T*>(a.z), static_cast<T*>(a.p), a.st, a.partials, a.err);
+      static_cast<const T*>(a.coef), static_cast<const T*>(a.scale), static_cast<const T*>(a.z),
+      static_cast<T*>(a.p), a.st, a.partials, a.err);
   count_launch();
   SEM_CUDA_TRY(cudaGetLastError());
   return SEM_OK;
@@ -286,13 +296,16 @@ sem_status launch_ax_t(int N, const AxLaunch& a, cudaStream_t s) {
 template <int NP, typename T, int EPB>
 sem_status launch_ax_shape(int N, sem_ax_variant v, bool cg, const AxLaunch& a, cudaStream_t s) {
   if (v == SEM_AX_OTF)
-    return cg ? launch_ax_t<NP, T, true, true, EPB>(N, a, s) : launch_ax_t<NP, T, true, false, EPB>(N, a, s);
-  return cg ? launch_ax_t<NP, T, false, true, EPB>(N, a, s) : launch_ax_t<NP, T, false, false, EPB>(N, a, s);
+    return cg ? launch_ax_t<NP, T, 1, true, EPB>(N, a, s) : launch_ax_t<NP, T, 1, false, EPB>(N, a, s);
+  return cg ? launch_ax_t<NP, T, 0, true, EPB>(N, a, s) : launch_ax_t<NP, T, 0, false, EPB>(N, a, s);
 }
 
-// Dispatch over the block shape, the variant and the mode for one order and precision.
+// Dispatch over the block shape, the variant and the mode for one order and precision
+// (the per-point-scale variant is compiled with the default block shape only).
 template <int NP, typename T>
 sem_status launch_ax_np(int N, sem_ax_variant v, bool cg, const AxLaunch& a, cudaStream_t s) {
+  if (v == SEM_AX_OTF_SCALE)
+    return cg ? launch_ax_t<NP, T, 2, true, ax_epb<NP>()>(N, a, s) : launch_ax_t<NP, T, 2, false, ax_epb<NP>()>(N, a, s);
   if (a.shape == 1 && ax_epb_alt<NP>() != ax_epb<NP>()) return launch_ax_shape<NP, T, ax_epb_alt<NP>()>(N, v, cg, a, s);
   return launch_ax_shape<NP, T, ax_epb<NP>()>(N, v, cg, a, s);
 }

@@ -99,7 +99,8 @@ __device__ void point_geometry(const double* a, double xi, double eta, double ga
 
 __global__ void k_geometry(const __grid_constant__ GllAll tab, int Np, int64_t E, const double* __restrict__ coef,
                            double* __restrict__ G64, float* __restrict__ G32, double* __restrict__ B64,
-                           float* __restrict__ B32, int* __restrict__ bad, int64_t gs64, int64_t gs32) {
+                           float* __restrict__ B32, int* __restrict__ bad, int64_t gs64, int64_t gs32,
+                           double* __restrict__ S64, float* __restrict__ S32) {
   const int64_t P = static_cast<int64_t>(Np) * Np * Np;
   const int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (idx >= E * P) return;
@@ -115,6 +116,9 @@ __global__ void k_geometry(const __grid_constant__ GllAll tab, int Np, int64_t E
   }
   if (B64) B64[idx] = B;
   if (B32) B32[idx] = static_cast<float>(B);
+  const double sc = tab.w[i] * tab.w[j] * tab.w[k] / det;  // scale of the on-the-fly factors
+  if (S64) S64[idx] = sc;
+  if (S32) S32[idx] = static_cast<float>(sc);
 }
 
 __global__ void k_coords(const __grid_constant__ GllAll tab, int Np, int64_t E, const double* __restrict__ coef,
@@ -221,11 +225,11 @@ sem_status launch_coefficients(int64_t E, const double* X, double* coef64, float
 }
 
 sem_status launch_geometry(int N, int64_t E, const double* coef64, double* G64, float* G32, double* B64, float* B32,
-                           int* bad, int64_t gs64, int64_t gs32, cudaStream_t s) {
+                           int* bad, int64_t gs64, int64_t gs32, cudaStream_t s, double* S64, float* S32) {
   const int Np = N + 1;
   const int64_t n = E * Np * Np * Np;
   k_geometry<<<ceil_div(n, kThreads), kThreads, 0, s>>>(gll_all(N), Np, E, coef64, G64, G32, B64, B32, bad, gs64,
-                                                        gs32);
+                                                        gs32, S64, S32);
   count_launch();
   SEM_CUDA_TRY(cudaGetLastError());
   return SEM_OK;

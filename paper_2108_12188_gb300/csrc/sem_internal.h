@@ -76,6 +76,8 @@ struct sem_mesh_s {
   float* coef32 = nullptr;    // [E][24] rounded to FP32
   double* G64 = nullptr;      // [E][6][P] or null
   float* G32 = nullptr;       // [E][factor_stride] (the [6][P] block, padded to 16 bytes) or null
+  double* scale64 = nullptr;  // [n] w_i w_j w_k / det J (SEM_MESH_OTF_SCALE) or null
+  float* scale32 = nullptr;
   int32_t* seg_off = nullptr;
   int32_t* seg_idx = nullptr;
   uint8_t* seg_mask = nullptr;
@@ -112,6 +114,7 @@ struct AxLaunch {
   void* w;            // output
   const void* G;      // stored factors or null
   const void* coef;   // trilinear coefficients (otf)
+  const void* scale;  // per-point w/det J (otf with stored scale)
   // CG mode (p = z + beta p prologue, interior part of <p, w> in the epilogue)
   const void* z;
   void* p;
@@ -141,7 +144,8 @@ inline sem_prec data_prec(sem_prec p) { return p == SEM_F32 ? SEM_F32 : SEM_F64;
 sem_status launch_coefficients(int64_t E, const double* X, double* coef64, float* coef32, cudaStream_t s);
 // G64 / G32 (either may be null) are written with element strides gs64 / gs32.
 sem_status launch_geometry(int N, int64_t E, const double* coef64, double* G64, float* G32, double* B64,
-                           float* B32, int* bad_flag, int64_t gs64, int64_t gs32, cudaStream_t s);
+                           float* B32, int* bad_flag, int64_t gs64, int64_t gs32, cudaStream_t s,
+                           double* S64 = nullptr, float* S32 = nullptr);
 sem_status launch_coords(int N, int64_t E, const double* coef64, double* xyz, int64_t n, cudaStream_t s);
 sem_status launch_local_diag(int N, int64_t E, const double* coef64, double* d, cudaStream_t s);
 sem_status launch_rhs_local(int N, int64_t E, const double* coef64, int a, int b, int c, double* out,

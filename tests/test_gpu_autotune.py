@@ -29,7 +29,7 @@ def _check_all(sem, tmp_path, force_shape):
     for dims, N in CASES:
         m = BoxMesh(*dims, jitter=0.12, seed=N)
         prob = so.SemProblem(N, m.vert_xyz, m.elem_verts)
-        mesh = sem.Mesh(N, m.vert_xyz, m.elem_verts, flags=3)
+        mesh = sem.Mesh(N, m.vert_xyz, m.elem_verts, flags=7)
         u = local_field(prob.n, seed=N + 5)
         want = prob.ax_local(u).ravel()
         for prec, tol in ((sem.SEM_F64, 1e-12), (sem.SEM_F32, 2e-6)):
@@ -39,13 +39,13 @@ def _check_all(sem, tmp_path, force_shape):
                 path = tmp_path / "tune.txt"
                 sem.sem_autotune_save(path)
                 lines = path.read_text().splitlines()
-                out = [lines[0]] + [" ".join(l.split()[:3] + [str(force_shape), str(force_shape)] + l.split()[5:])
-                                    for l in lines[1:]]
+                out = [lines[0]] + [" ".join(l.split()[:3] + [str(force_shape), str(force_shape), "0"]
+                                             + l.split()[6:]) for l in lines[1:]]
                 path.write_text("\n".join(out) + "\n")
                 sem.sem_autotune_load(path)
             dt = torch.float64 if prec == sem.SEM_F64 else torch.float32
             ud = torch.tensor(u, dtype=dt, device="cuda")
-            for variant in (sem.SEM_AX_STORED, sem.SEM_AX_OTF, sem.SEM_AX_AUTO):
+            for variant in (sem.SEM_AX_STORED, sem.SEM_AX_OTF, sem.SEM_AX_OTF_SCALE, sem.SEM_AX_AUTO):
                 wd = torch.empty_like(ud)
                 sem.sem_ax(mesh.handle, variant, prec, ud, wd, assemble=False)
                 err = np.linalg.norm(wd.double().cpu().numpy() - want) / np.linalg.norm(want)
@@ -60,7 +60,7 @@ def test_every_candidate_matches_oracle(sem, tmp_path, force_shape):
 
 def test_table_from_another_gpu_is_refused(sem, tmp_path):
     path = tmp_path / "other.txt"
-    path.write_text("sem-autotune 1 Some_Other_GPU\n0 7 0 0 0 1.0 2.0\n")
+    path.write_text("sem-autotune 2 Some_Other_GPU\n0 7 0 0 0 0 1.0 2.0 3.0\n")
     with pytest.raises(sem.SemError) as e:
         sem.sem_autotune_load(path)
     assert e.value.status == sem.SEM_ERR_ARG

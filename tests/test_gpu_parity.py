@@ -14,7 +14,7 @@ from synthetic import BoxMesh, global_field, local_field
 
 pytestmark = pytest.mark.gpu
 
-FLAGS_ALL = 3  # SEM_MESH_F64_STORED | SEM_MESH_F32_STORED
+FLAGS_ALL = 7  # SEM_MESH_F64_STORED | SEM_MESH_F32_STORED | SEM_MESH_OTF_SCALE
 
 
 @pytest.fixture(scope="module")
@@ -104,8 +104,9 @@ def test_geometry(sem, dims, N, jitter, seed):
     np.testing.assert_allclose(_h(xyz), want, rtol=0, atol=4e-15)
 
 
-VARIANTS = [(0, 0, 1e-12), (1, 0, 1e-12), (0, 1, 2e-6), (1, 1, 2e-6), (0, 2, 1e-12)]  # (variant, prec, tol)
-VIDS = ["stored-f64", "otf-f64", "stored-f32", "otf-f32", "stored-f64x"]
+VARIANTS = [(0, 0, 1e-12), (1, 0, 1e-12), (0, 1, 2e-6), (1, 1, 2e-6), (0, 2, 1e-12), (3, 0, 1e-12),
+            (3, 1, 2e-6)]  # (variant, prec, tol)
+VIDS = ["stored-f64", "otf-f64", "stored-f32", "otf-f32", "stored-f64x", "otfscale-f64", "otfscale-f32"]
 
 
 @pytest.mark.parametrize("variant,prec,tol", VARIANTS, ids=VIDS)
