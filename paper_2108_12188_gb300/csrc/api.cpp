@@ -321,7 +321,8 @@ extern "C" sem_status sem_mesh_numbering(int N, int64_t nv, int64_t E, const int
                                          int64_t* n_glob_out) {
   Topology T;
   SEM_TRY(build_topology(N, nv, E, elem_verts, dflags, T));
-  if (glo_out) std::memcpy(glo_out, T.glo.data(), T.glo.size() * sizeof(int64_t));
+  if (glo_out)
+    for (size_t i = 0; i < T.glo.size(); ++i) glo_out[i] = T.glo[i];
   if (mask_out) std::memcpy(mask_out, T.mask.data(), T.mask.size());
   if (n_glob_out) *n_glob_out = T.n_glob;
   return SEM_OK;
@@ -355,7 +356,7 @@ extern "C" sem_status sem_mesh_get_info(sem_mesh m, sem_mesh_info_t* info) {
 
 extern "C" sem_status sem_mesh_get_glo_num(sem_mesh m, int64_t* out) {
   if (!m || !out) return fail(SEM_ERR_ARG, "null argument");
-  std::memcpy(out, m->glo.data(), m->glo.size() * sizeof(int64_t));
+  for (size_t i = 0; i < m->glo.size(); ++i) out[i] = m->glo[i];
   return SEM_OK;
 }
 
@@ -407,7 +408,7 @@ extern "C" sem_status sem_scatter(sem_mesh m, sem_prec prec, const void* ug, voi
   SEM_TRY(check_ptr(ul, "u_local_dev"));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   note_stream(m, s);
-  std::vector<int32_t> g32(m->glo.begin(), m->glo.end());
+  const std::vector<int32_t>& g32 = m->glo;
   int32_t* gd = nullptr;
   SEM_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&gd), g32.size() * 4, s));
   sem_status st = SEM_OK;

@@ -34,7 +34,7 @@ const GllTable& gll_table(int N);  // N in [1, SEM_MAX_N]
 struct Topology {
   int N = 0, Np = 0;
   int64_t E = 0, n = 0, n_glob = 0;
-  std::vector<int64_t> glo;      // [n]
+  std::vector<int32_t> glo;      // [n] (n < 2^31)
   std::vector<uint8_t> mask;     // [n]
   std::vector<uint8_t> mult;     // [n] multiplicity of the node's global id (<= 255)
   std::vector<int32_t> seg_off;  // [n_seg + 1]
@@ -69,7 +69,7 @@ struct sem_mesh_s {
   int N = 0, Np = 0, device = 0;
   unsigned flags = 0;
   int64_t E = 0, n = 0, n_glob = 0, n_seg = 0, n_gs = 0;
-  std::vector<int64_t> glo;   // host copy for the test hooks
+  std::vector<int32_t> glo;   // host copy for the test hooks
   std::vector<uint8_t> mask;  // host copy
   // device arrays
   double* coef64 = nullptr;   // [E][24] trilinear coefficients a0..a7 (x, y, z)

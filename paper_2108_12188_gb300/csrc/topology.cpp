@@ -146,63 +146,96 @@ sem_status build_topology(int N, int64_t nv, int64_t E, const int64_t* ev, const
     return f;
   };
 
-  // ---- numbering
+  // ---- classification of the P positions of an element (the same for every element)
+  struct PosInfo {
+    uint8_t cls;     // 0 element interior, 1 vertex, 2 edge, 3 face
+    uint8_t idx;     // corner (vertex), local edge (edge), local face (face)
+    uint8_t c0, c1;  // coordinate along the edge; the two in-face coordinates
+  };
+  std::vector<PosInfo> pos(P);
+  std::vector<int32_t> bpos;  // element-boundary positions, ascending
+  for (int k = 0; k < Np; ++k)
+    for (int j = 0; j < Np; ++j)
+      for (int i = 0; i < Np; ++i) {
+        const int r = (k * Np + j) * Np + i;
+        const int q[3] = {i, j, k};
+        int end[3], n_end = 0;
+        for (int d = 0; d < 3; ++d) {
+          end[d] = q[d] == 0 ? 0 : (q[d] == N ? 1 : -1);
+          n_end += end[d] >= 0;
+        }
+        PosInfo pi{0, 0, 0, 0};
+        if (n_end == 3) {
+          pi = {1, static_cast<uint8_t>(corner(end[0], end[1], end[2])), 0, 0};
+        } else if (n_end == 2) {
+          const int d = end[0] < 0 ? 0 : (end[1] < 0 ? 1 : 2);
+          const int d1 = d == 0 ? 1 : 0, d2 = d == 2 ? 1 : 2;
+          pi = {2, static_cast<uint8_t>(d * 4 + end[d1] + 2 * end[d2]), static_cast<uint8_t>(q[d]), 0};
+        } else if (n_end == 1) {
+          const int d = end[0] >= 0 ? 0 : (end[1] >= 0 ? 1 : 2);
+          const int d1 = d == 0 ? 1 : 0, d2 = d == 2 ? 1 : 2;
+          pi = {3, static_cast<uint8_t>(d * 2 + end[d]), static_cast<uint8_t>(q[d1]), static_cast<uint8_t>(q[d2])};
+        }
+        pos[r] = pi;
+        if (pi.cls != 0) bpos.push_back(r);
+      }
+
+  // ---- numbering, with the copy count of every global node
   const int64_t Nm1 = N - 1;
   const int64_t K_e = nv, K_f = K_e + n_edges * Nm1, n_keys = K_f + n_faces * Nm1 * Nm1;
   std::vector<int32_t> first_id(n_keys, -1);
+  std::vector<int32_t> count;
+  count.reserve(static_cast<size_t>(n));
   T.glo.assign(n, 0);
-  int64_t next = 0;
   for (int64_t e = 0; e < E; ++e) {
     const ElemFrames f = frames_of(e);
     const int64_t* v = ev + 8 * e;
-    int64_t loc = e * P;
-    for (int k = 0; k < Np; ++k)
-      for (int j = 0; j < Np; ++j)
-        for (int i = 0; i < Np; ++i, ++loc) {
-          const int q[3] = {i, j, k};
-          int end[3], n_end = 0;
-          for (int d = 0; d < 3; ++d) {
-            end[d] = q[d] == 0 ? 0 : (q[d] == N ? 1 : -1);
-            n_end += end[d] >= 0;
-          }
-          int64_t key;
-          if (n_end == 0) {
-            T.glo[loc] = next++;
-            continue;
-          } else if (n_end == 3) {
-            key = v[corner(end[0], end[1], end[2])];
-          } else if (n_end == 2) {
-            const int d = end[0] < 0 ? 0 : (end[1] < 0 ? 1 : 2);
-            const int d1 = d == 0 ? 1 : 0, d2 = d == 2 ? 1 : 2;
-            const int le = d * 4 + end[d1] + 2 * end[d2];
-            const int t = f.edge_rev[le] ? N - q[d] : q[d];
-            key = K_e + f.edge_id[le] * Nm1 + (t - 1);
-          } else {
-            const int d = end[0] >= 0 ? 0 : (end[1] >= 0 ? 1 : 2);
-            const int d1 = d == 0 ? 1 : 0, d2 = d == 2 ? 1 : 2;
-            const int lf = d * 2 + end[d];
-            const int ps = f.face_oa[lf] == 0 ? q[d1] : N - q[d1];
-            const int pt = f.face_ob[lf] == 0 ? q[d2] : N - q[d2];
-            const int p0 = f.face_swap[lf] ? pt : ps, p1 = f.face_swap[lf] ? ps : pt;
-            key = K_f + f.face_id[lf] * Nm1 * Nm1 + (p0 - 1) * Nm1 + (p1 - 1);
-          }
-          int32_t& g = first_id[key];
-          if (g < 0) g = static_cast<int32_t>(next++);
-          T.glo[loc] = g;
+    int32_t* glo = T.glo.data() + e * P;
+    for (int r = 0; r < P; ++r) {
+      const PosInfo pi = pos[r];
+      int64_t key;
+      switch (pi.cls) {
+        case 0:  // element interior: always a new node
+          glo[r] = static_cast<int32_t>(count.size());
+          count.push_back(1);
+          continue;
+        case 1:
+          key = v[pi.idx];
+          break;
+        case 2: {
+          const int t = f.edge_rev[pi.idx] ? N - pi.c0 : pi.c0;
+          key = K_e + f.edge_id[pi.idx] * Nm1 + (t - 1);
+          break;
         }
+        default: {
+          const int lf = pi.idx;
+          const int ps = f.face_oa[lf] == 0 ? pi.c0 : N - pi.c0;
+          const int pt = f.face_ob[lf] == 0 ? pi.c1 : N - pi.c1;
+          const int p0 = f.face_swap[lf] ? pt : ps, p1 = f.face_swap[lf] ? ps : pt;
+          key = K_f + f.face_id[lf] * Nm1 * Nm1 + (p0 - 1) * Nm1 + (p1 - 1);
+          break;
+        }
+      }
+      int32_t& g = first_id[key];
+      if (g < 0) {
+        g = static_cast<int32_t>(count.size());
+        count.push_back(0);
+      }
+      ++count[g];
+      glo[r] = g;
+    }
   }
   std::vector<int32_t>().swap(first_id);
-  const int64_t n_glob = next;
+  const int64_t n_glob = static_cast<int64_t>(count.size());
 
-  // ---- multiplicity
-  std::vector<int32_t> count(n_glob, 0);
-  for (int64_t i = 0; i < n; ++i) ++count[T.glo[i]];
-  T.mult.resize(n);
-  for (int64_t i = 0; i < n; ++i) {
-    const int32_t c = count[T.glo[i]];
-    if (c > 255) return fail(SEM_ERR_MESH, "a global node has more than 255 local copies");
-    T.mult[i] = static_cast<uint8_t>(c);
-  }
+  // ---- multiplicity (element-interior copies have multiplicity 1)
+  T.mult.assign(n, 1);
+  for (int64_t e = 0; e < E; ++e)
+    for (const int32_t r : bpos) {
+      const int32_t c = count[T.glo[e * P + r]];
+      if (c > 255) return fail(SEM_ERR_MESH, "a global node has more than 255 local copies");
+      T.mult[e * P + r] = static_cast<uint8_t>(c);
+    }
 
   // ---- Dirichlet mask: points on the closure of a boundary face (owned by one element)
   std::vector<uint8_t> mglob(n_glob, 0);
@@ -222,40 +255,38 @@ sem_status build_topology(int N, int64_t nv, int64_t E, const int64_t* ev, const
           }
           if (!all) continue;
         }
-        for (int k = 0; k < Np; ++k)
-          for (int j = 0; j < Np; ++j)
-            for (int i = 0; i < Np; ++i) {
-              const int q[3] = {i, j, k};
-              if (q[d] == s * N) mglob[T.glo[e * P + (k * Np + j) * Np + i]] = 1;
-            }
+        for (const int32_t r : bpos) {
+          const int q[3] = {r % Np, (r / Np) % Np, r / (Np * Np)};
+          if (q[d] == s * N) mglob[T.glo[e * P + r]] = 1;
+        }
       }
   }
-  T.mask.resize(n);
-  for (int64_t i = 0; i < n; ++i) T.mask[i] = mglob[T.glo[i]];
+  T.mask.assign(n, 0);  // element-interior points are never on a boundary face
+  for (int64_t e = 0; e < E; ++e)
+    for (const int32_t r : bpos) T.mask[e * P + r] = mglob[T.glo[e * P + r]];
 
-  // ---- gather-scatter segments: global nodes with copies on element boundaries, ascending id
-  auto on_bdry = [&](int64_t loc) {
-    const int64_t r = loc % P;
-    const int i = static_cast<int>(r % Np), j = static_cast<int>((r / Np) % Np), k = static_cast<int>(r / (Np * Np));
-    return i == 0 || i == N || j == 0 || j == N || k == 0 || k == N;
-  };
-  std::fill(count.begin(), count.end(), 0);
-  for (int64_t i = 0; i < n; ++i)
-    if (on_bdry(i)) ++count[T.glo[i]];
+  // ---- gather-scatter segments: global nodes with copies on element boundaries, ascending
+  // id; a boundary node's copies all lie on element boundaries, so its copy count is its size
   std::vector<int32_t> seg_of(n_glob, -1);
+  std::vector<uint8_t> is_bdry(n_glob, 0);
+  for (int64_t e = 0; e < E; ++e)
+    for (const int32_t r : bpos) is_bdry[T.glo[e * P + r]] = 1;
   T.seg_off.clear();
   T.seg_off.push_back(0);
   T.seg_mask.clear();
   for (int64_t g = 0; g < n_glob; ++g)
-    if (count[g] > 0) {
+    if (is_bdry[g]) {
       seg_of[g] = static_cast<int32_t>(T.seg_off.size() - 1);
       T.seg_off.push_back(T.seg_off.back() + count[g]);
       T.seg_mask.push_back(mglob[g]);
     }
   std::vector<int32_t> cursor(T.seg_off.begin(), T.seg_off.end() - 1);
   T.seg_idx.assign(T.seg_off.back(), 0);
-  for (int64_t i = 0; i < n; ++i)
-    if (on_bdry(i)) T.seg_idx[cursor[seg_of[T.glo[i]]]++] = static_cast<int32_t>(i);
+  for (int64_t e = 0; e < E; ++e)
+    for (const int32_t r : bpos) {
+      const int64_t loc = e * P + r;
+      T.seg_idx[cursor[seg_of[T.glo[loc]]]++] = static_cast<int32_t>(loc);
+    }
 
   T.N = N;
   T.Np = Np;
