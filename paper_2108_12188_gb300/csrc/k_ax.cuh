@@ -1,13 +1,13 @@
 // Local SEM operator w = A_L u = D^T G D u (Eq. 4, Section 3.1), one element per NP x NP
 // thread tile, EPB elements per block, grid-stride over element groups.
 //
-// Thread (i, j) of an element holds the column u(i, j, 0..NP-1) in registers and
-// the element field in shared memory:
 //   forward:   ur = sum_l D_il u(l,j,k), us = sum_l D_jl u(i,l,k), ut = sum_l D_kl u(i,j,l)
 //   geometry:  (vr, vs, vt) = G (ur, us, ut), G read from memory (STORED) or rebuilt from
 //              the element's trilinear coefficients (OTF, Section 5.1's rematerialisation)
 //   transpose: w = sum_l D_li vr(l,j,k) + sum_l D_lj vs(i,l,k) + sum_l D_lk vt(i,j,l)
-// The k-direction contractions stay in registers; D for it comes from the constant bank.
+// Each contraction runs on whole lines of NP values held in registers, through the even/odd
+// split of D and D^T (EoMat), which needs about 3/4 of the multiply-adds of the plain sums;
+// the split matrices are kernel parameters, so they are constant-bank operands.
 // STORED: the six factor arrays of an element are one contiguous block; a bulk TMA copy
 // brings the next element group's blocks into shared memory while the current group runs
 // its transposed contractions (bounded mbarrier waits; a timeout sets SEM_ERR_TIMEOUT).
@@ -69,46 +69,67 @@ __host__ __device__ constexpr int ax_gstride() {
   return sizeof(T) == 8 ? 6 * NP * NP * NP : (6 * NP * NP * NP + 3) / 4 * 4;
 }
 
+// Staging buffer of one element in shared memory: position of point (i, j, k). For NP = 8
+// every k-plane has one row of padding and the position inside a row is XOR-swizzled by
+// (j >> 1) | ((k & 1) << 2); then the three access patterns of k_ax (a thread per i-row, a
+// thread per j-line, a thread per k-column, 32 consecutive threads covering four rows, lines
+// or columns) touch every shared-memory bank equally often, for FP64 and FP32 data.
+template <int NP>
+struct Stage {
+  static constexpr int kPlane = NP == 8 ? 72 : NP * NP;
+  static constexpr int kSize = NP * kPlane;
+  __device__ static __forceinline__ int at(int i, int j, int k) {
+    if constexpr (NP == 8)
+      return k * kPlane + j * NP + (i ^ ((j >> 1) | ((k & 1) << 2)));
+    else
+      return k * kPlane + j * NP + i;
+  }
+};
+
 // Dynamic shared memory of k_ax: [factors of the element group (STORED only, TMA target)]
-// [staging buffers A, B] [D] [xi, w] [mbarrier].
+// [staging buffers A, B] [mbarrier].
 template <int NP, typename T, int GEO, int EPB>
 __host__ __device__ constexpr size_t ax_smem_bytes() {
-  constexpr size_t P = static_cast<size_t>(NP) * NP * NP;
-  return (GEO != 0 ? 0 : static_cast<size_t>(EPB) * ax_gstride<NP, T>() * sizeof(T)) + 2 * EPB * P * sizeof(T) +
-         (NP * NP + 2 * NP) * sizeof(T) + 16;
+  return (GEO != 0 ? 0 : static_cast<size_t>(EPB) * ax_gstride<NP, T>() * sizeof(T)) +
+         2 * static_cast<size_t>(EPB) * Stage<NP>::kSize * sizeof(T) + 16;
 }
 
 // GEO: 0 stored factors, 1 factors recomputed from the element coefficients, 2 recomputed
 // with the per-point scale w_i w_j w_k / det J read from memory (one word per point, the
 // division moved out of the kernel: Section 5.1's rematerialisation with I/O cost n).
+//
+// Work of a group of EPB elements; thread t of an element takes i-row (j, k) = (t % NP, t / NP),
+// j-line (i, k) = (t % NP, t / NP) and k-column (i, j) = (t % NP, t / NP), each a line of NP
+// values that it contracts with D or D^T in registers (even/odd split, see EoMat):
+//   0  column of u (or of p = z + beta p) -> registers and buffer A
+//   1  i-rows of A -> ur into B;               column -> ut (registers)
+//   2  j-lines of A -> us, in place in A
+//   3  column: (vr, vs, vt) = G (ur, us, ut); vr, vs in place in B, A; vt in registers
+//   4  i-rows of B -> D^T vr in place;  j-lines of A -> D^T vs in place;  column -> D^T vt
+//   5  column: w = the three sums; stored (CG mode: p.w added over interior points)
+// with a block barrier between phases. Every thread reads and writes only its own line in
+// the in-place phases.
 template <int NP, typename T, int GEO, bool CG, int EPB>
 __global__ void __launch_bounds__(NP * NP * EPB)
     k_ax(const __grid_constant__ GllParam<NP, T> tab, int64_t E, const T* __restrict__ u, T* __restrict__ w,
          const T* __restrict__ G, const T* __restrict__ coef, const T* __restrict__ scale, const T* __restrict__ z,
          T* __restrict__ p, CgScalars* __restrict__ st, double* __restrict__ partials, int* __restrict__ err) {
   constexpr bool OTF = GEO != 0;
-  constexpr int NP2 = NP * NP, P = NP2 * NP, GS = ax_gstride<NP, T>();
+  constexpr int NP2 = NP * NP, P = NP2 * NP, GS = ax_gstride<NP, T>(), SZ = Stage<NP>::kSize;
   constexpr size_t kG = OTF ? 0 : static_cast<size_t>(EPB) * GS;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   T* sG = reinterpret_cast<T*>(smem_raw);
-  T* sA = sG + kG;
-  T* sB = sA + EPB * P;
-  T* sD = sB + EPB * P;
-  T* sXi = sD + NP2;
-  T* sW = sXi + NP;
+  T* sA0 = sG + kG;
+  T* sB0 = sA0 + EPB * SZ;
   uint64_t* bar = reinterpret_cast<uint64_t*>(
-      smem_raw + ((reinterpret_cast<uintptr_t>(sW + NP) - reinterpret_cast<uintptr_t>(smem_raw) + 7) & ~uintptr_t(7)));
+      smem_raw + ((reinterpret_cast<uintptr_t>(sB0 + EPB * SZ) - reinterpret_cast<uintptr_t>(smem_raw) + 7) &
+                  ~uintptr_t(7)));
   __shared__ double sRed[32];
 
   T beta = T(0);
   if constexpr (CG) {
     if (st->done) return;  // uniform over the grid: set by an earlier launch
     beta = static_cast<T>(st->beta);
-  }
-  for (int q = threadIdx.x; q < NP2; q += blockDim.x) sD[q] = tab.D[q];
-  for (int q = threadIdx.x; q < NP; q += blockDim.x) {
-    sXi[q] = tab.xi[q];
-    sW[q] = tab.w[q];
   }
   const int64_t n_groups = (E + EPB - 1) / EPB;
   constexpr unsigned kElemBytes = static_cast<unsigned>(GS * sizeof(T));
@@ -124,7 +145,9 @@ __global__ void __launch_bounds__(NP * NP * EPB)
     }
   }
   const int slot = threadIdx.x / NP2, tid = threadIdx.x % NP2;
-  const int i = tid % NP, j = tid / NP;
+  const int i = tid % NP, j = tid / NP;  // column (i, j); i-row (j, k) = (i, j); j-line (i, k) = (i, j)
+  T* sA = sA0 + slot * SZ;
+  T* sB = sB0 + slot * SZ;
   DotAcc<T> dot;
   unsigned parity = 0;
   __syncthreads();
@@ -133,6 +156,7 @@ __global__ void __launch_bounds__(NP * NP * EPB)
     const int64_t e = grp * EPB + slot;
     const bool valid = e < E;
     const int64_t base = e * P + tid;
+    // phase 0: the column of the input
     T rU[NP];
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
@@ -146,30 +170,33 @@ __global__ void __launch_bounds__(NP * NP * EPB)
         }
       }
       rU[k] = val;
-      sA[slot * P + k * NP2 + tid] = val;
+      sA[Stage<NP>::at(i, j, k)] = val;
     }
+    __syncthreads();
 
-    // OTF: per-thread parts of the Jacobian columns that do not depend on k
-    Vec3<T> g2{}, P0{}, Q0{}, P1{}, Q1{};
-    T wij = T(0);
-    if constexpr (OTF) {
-      if (valid) {
-        const T* a = coef + e * 24;  // a0..a7, each (x, y, z); a0 (the centroid) is not needed
-        const T xi = sXi[i], eta = sXi[j];
-        const Vec3<T> a1{a[3], a[4], a[5]}, a2{a[6], a[7], a[8]}, a3{a[9], a[10], a[11]};
-        const Vec3<T> a4{a[12], a[13], a[14]}, a5{a[15], a[16], a[17]}, a6{a[18], a[19], a[20]};
-        const Vec3<T> a7{a[21], a[22], a[23]};
-        // x(xi,eta,gam) = a0 + a1 xi + a2 eta + a3 gam + a4 xi eta + a5 xi gam + a6 eta gam + a7 xi eta gam
-        g2 = {a3.x + a5.x * xi + a6.x * eta + a7.x * xi * eta, a3.y + a5.y * xi + a6.y * eta + a7.y * xi * eta,
-              a3.z + a5.z * xi + a6.z * eta + a7.z * xi * eta};
-        P0 = {a1.x + a4.x * eta, a1.y + a4.y * eta, a1.z + a4.z * eta};
-        Q0 = {a5.x + a7.x * eta, a5.y + a7.y * eta, a5.z + a7.z * eta};
-        P1 = {a2.x + a4.x * xi, a2.y + a4.y * xi, a2.z + a4.z * xi};
-        Q1 = {a6.x + a7.x * xi, a6.y + a7.y * xi, a6.z + a7.z * xi};
-        wij = sW[i] * sW[j];
-      }
-    } else {
-      const bool ok = mbar_wait_bounded(bar, parity);
+    // phase 1: i-row (j, k) = (i, j) of A -> ur into B; the column -> ut
+    T rT[NP];
+    {
+      T in[NP], out[NP];
+#pragma unroll
+      for (int l = 0; l < NP; ++l) in[l] = sA[Stage<NP>::at(l, i, j)];
+      eo_apply<NP, T>(tab.Df, in, out);
+#pragma unroll
+      for (int l = 0; l < NP; ++l) sB[Stage<NP>::at(l, i, j)] = out[l];
+      eo_apply<NP, T>(tab.Df, rU, rT);
+    }
+    __syncthreads();
+    // phase 2: j-line (i, k) = (i, j) of A -> us, in place
+    {
+      T in[NP], out[NP];
+#pragma unroll
+      for (int l = 0; l < NP; ++l) in[l] = sA[Stage<NP>::at(i, l, j)];
+      eo_apply<NP, T>(tab.Df, in, out);
+#pragma unroll
+      for (int l = 0; l < NP; ++l) sA[Stage<NP>::at(i, l, j)] = out[l];
+    }
+    if constexpr (!OTF) {
+      const bool ok = mbar_wait_bounded(bar, parity);  // this group's factors
       parity ^= 1u;
       if (__syncthreads_or(!ok)) {  // the factor copy did not arrive: report and leave together
         if (threadIdx.x == 0) {
@@ -182,48 +209,68 @@ __global__ void __launch_bounds__(NP * NP * EPB)
         }
         return;
       }
+    } else {
+      __syncthreads();
     }
-    __syncthreads();
 
-    T rR[NP], rS[NP], rT[NP];
+    // phase 3: (vr, vs, vt) = G (ur, us, ut) on the column
+    // OTF: per-thread parts of the Jacobian columns that do not depend on k
+    Vec3<T> g2{}, P0{}, Q0{}, P1{}, Q1{};
+    T wij = T(0);
+    if constexpr (OTF) {
+      if (valid) {
+        const T* a = coef + e * 24;  // a0..a7, each (x, y, z); a0 (the centroid) is not needed
+        const T xi = tab.xi[i], eta = tab.xi[j];
+        const Vec3<T> a1{a[3], a[4], a[5]}, a2{a[6], a[7], a[8]}, a3{a[9], a[10], a[11]};
+        const Vec3<T> a4{a[12], a[13], a[14]}, a5{a[15], a[16], a[17]}, a6{a[18], a[19], a[20]};
+        const Vec3<T> a7{a[21], a[22], a[23]};
+        // x(xi,eta,gam) = a0 + a1 xi + a2 eta + a3 gam + a4 xi eta + a5 xi gam + a6 eta gam + a7 xi eta gam
+        g2 = {a3.x + a5.x * xi + a6.x * eta + a7.x * xi * eta, a3.y + a5.y * xi + a6.y * eta + a7.y * xi * eta,
+              a3.z + a5.z * xi + a6.z * eta + a7.z * xi * eta};
+        P0 = {a1.x + a4.x * eta, a1.y + a4.y * eta, a1.z + a4.z * eta};
+        Q0 = {a5.x + a7.x * eta, a5.y + a7.y * eta, a5.z + a7.z * eta};
+        P1 = {a2.x + a4.x * xi, a2.y + a4.y * xi, a2.z + a4.z * xi};
+        Q1 = {a6.x + a7.x * xi, a6.y + a7.y * xi, a6.z + a7.z * xi};
+        wij = tab.w[i] * tab.w[j];
+      }
+    }
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
-      T ur = T(0), us = T(0), ut = T(0);
-#pragma unroll
-      for (int l = 0; l < NP; ++l) {
-        ur += sD[i * NP + l] * sA[slot * P + k * NP2 + j * NP + l];
-        us += sD[j * NP + l] * sA[slot * P + k * NP2 + l * NP + i];
-        ut += tab.D[k * NP + l] * rU[l];
-      }
+      const int at = Stage<NP>::at(i, j, k);
+      const T ur = sB[at], us = sA[at], ut = rT[k];
+      T vr, vs, vt;
       if constexpr (OTF) {
         const T gam = tab.xi[k];
         const Vec3<T> g0{P0.x + gam * Q0.x, P0.y + gam * Q0.y, P0.z + gam * Q0.z};
         const Vec3<T> g1{P1.x + gam * Q1.x, P1.y + gam * Q1.y, P1.z + gam * Q1.z};
         const Vec3<T> c0 = cross(g1, g2), c1 = cross(g2, g0), c2 = cross(g0, g1);
-        T s;
+        T sc;
         if constexpr (GEO == 2) {
-          s = valid ? scale[base + k * NP2] : T(0);
+          sc = valid ? scale[base + k * NP2] : T(0);
         } else {
           const T det = dot3(g0, c0);
-          s = valid ? div_fast(wij * tab.w[k], det) : T(0);
+          sc = valid ? div_fast(wij * tab.w[k], det) : T(0);
         }
         const Vec3<T> q{c0.x * ur + c1.x * us + c2.x * ut, c0.y * ur + c1.y * us + c2.y * ut,
                         c0.z * ur + c1.z * us + c2.z * ut};
-        rR[k] = s * dot3(c0, q);
-        rS[k] = s * dot3(c1, q);
-        rT[k] = s * dot3(c2, q);
+        vr = sc * dot3(c0, q);
+        vs = sc * dot3(c1, q);
+        vt = sc * dot3(c2, q);
       } else {
         const T* gp = sG + slot * GS + k * NP2 + tid;
         const T g11 = gp[0 * P], g12 = gp[1 * P], g13 = gp[2 * P], g22 = gp[3 * P], g23 = gp[4 * P],
                 g33 = gp[5 * P];
-        rR[k] = g11 * ur + g12 * us + g13 * ut;
-        rS[k] = g12 * ur + g22 * us + g23 * ut;
-        rT[k] = g13 * ur + g23 * us + g33 * ut;
+        vr = g11 * ur + g12 * us + g13 * ut;
+        vs = g12 * ur + g22 * us + g23 * ut;
+        vt = g13 * ur + g23 * us + g33 * ut;
       }
+      sB[at] = vr;
+      sA[at] = vs;
+      rT[k] = vt;
     }
-    __syncthreads();  // staging buffer A (the field) and the factors are consumed
+    __syncthreads();  // the factors are consumed
     if constexpr (!OTF) {
-      if (threadIdx.x == 0 && grp + gridDim.x < n_groups) {  // next group's factors, during the rest
+      if (threadIdx.x == 0 && grp + gridDim.x < n_groups) {  // next group's factors, during phases 4-2
         const int64_t e0 = (grp + gridDim.x) * EPB;
         const int cnt = static_cast<int>(E - e0 < EPB ? E - e0 : EPB);
         fence_proxy_async();
@@ -231,28 +278,37 @@ __global__ void __launch_bounds__(NP * NP * EPB)
         for (int q = 0; q < cnt; ++q) tma_load_1d(sG + q * GS, G + (e0 + q) * GS, kElemBytes, bar);
       }
     }
+
+    // phase 4: D^T on i-rows of B and j-lines of A (in place) and on the column
+    T rW[NP];
+    {
+      T in[NP], out[NP];
 #pragma unroll
-    for (int k = 0; k < NP; ++k) {
-      sA[slot * P + k * NP2 + tid] = rR[k];
-      sB[slot * P + k * NP2 + tid] = rS[k];
+      for (int l = 0; l < NP; ++l) in[l] = sB[Stage<NP>::at(l, i, j)];
+      eo_apply<NP, T>(tab.Dt, in, out);
+#pragma unroll
+      for (int l = 0; l < NP; ++l) sB[Stage<NP>::at(l, i, j)] = out[l];
+#pragma unroll
+      for (int l = 0; l < NP; ++l) in[l] = sA[Stage<NP>::at(i, l, j)];
+      eo_apply<NP, T>(tab.Dt, in, out);
+#pragma unroll
+      for (int l = 0; l < NP; ++l) sA[Stage<NP>::at(i, l, j)] = out[l];
+      eo_apply<NP, T>(tab.Dt, rT, rW);
     }
     __syncthreads();
+
+    // phase 5: w on the column
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
-      T acc = T(0);
-#pragma unroll
-      for (int l = 0; l < NP; ++l) {
-        acc += sD[l * NP + i] * sA[slot * P + k * NP2 + j * NP + l];
-        acc += sD[l * NP + j] * sB[slot * P + k * NP2 + l * NP + i];
-        acc += tab.D[l * NP + k] * rT[l];
-      }
+      const int at = Stage<NP>::at(i, j, k);
+      const T acc = sB[at] + sA[at] + rW[k];
       if (valid) w[base + k * NP2] = acc;
       if constexpr (CG) {
         const bool interior = i > 0 && i < NP - 1 && j > 0 && j < NP - 1 && k > 0 && k < NP - 1;
         if (valid && interior) dot.add(rU[k], acc);
       }
     }
-    __syncthreads();
+    __syncthreads();  // the staging buffers are free for the next group
   }
   if constexpr (CG) {
     const double s = block_sum(dot.value(), sRed);

@@ -10,12 +10,48 @@ namespace sem {
 // GLL nodes, weights and derivative matrix of one order, passed by value as a
 // __grid_constant__ kernel parameter (it lives in the constant bank, so fixed indices
 // become constant operands and no per-module symbol upload is needed).
+//
+// A matrix M with M(N-i, N-l) = -M(i, l) (D and D^T: the GLL nodes are symmetric, so
+// l_{N-b}'(xi_{N-a}) = -l_b'(xi_a)) is kept in its even/odd split (Kopriva's form): with
+// H = NP/2, e_l = u_l + u_{N-l} and o_l = u_l - u_{N-l} (l < H),
+//   A_i = sum_l E(i,l) e_l [+ M(i,m) u_m],  B_i = sum_l O(i,l) o_l   (i < H),
+//   (M u)_i = A_i + B_i,  (M u)_{N-i} = B_i - A_i,  [(M u)_m = sum_l M(m,l) o_l],
+// E(i,l) = (M(i,l) + M(i,N-l)) / 2, O(i,l) = (M(i,l) - M(i,N-l)) / 2; the bracketed terms
+// exist for odd NP only (middle index m = H, where M(m,m) = 0). E carries M(i,m) as its last
+// column and O carries M(m,l) as its last row. A line of NP values then costs 2 H^2 + 4 H
+// (+ 2 H) operations instead of NP^2.
+template <int NP, typename T>
+struct EoMat {
+  static constexpr int H = NP / 2, HC = (NP + 1) / 2;
+  T E[H][HC];
+  T O[HC][H];
+};
+
 template <int NP, typename T>
 struct GllParam {
   T D[NP * NP];  // D[a*NP + b] = l_b'(xi_a)
   T xi[NP];
   T w[NP];
+  EoMat<NP, T> Df;  // split of D
+  EoMat<NP, T> Dt;  // split of D^T
 };
+
+// Even/odd split of the NP x NP matrix M(i, l) = m(i, l) (FP64 on the host).
+template <int NP, typename T, typename F>
+inline EoMat<NP, T> make_eo(F m) {
+  constexpr int H = NP / 2, N = NP - 1;
+  EoMat<NP, T> r{};
+  for (int i = 0; i < H; ++i) {
+    for (int l = 0; l < H; ++l) {
+      r.E[i][l] = static_cast<T>(0.5 * (m(i, l) + m(i, N - l)));
+      r.O[i][l] = static_cast<T>(0.5 * (m(i, l) - m(i, N - l)));
+    }
+    if (NP % 2) r.E[i][(NP + 1) / 2 - 1] = static_cast<T>(m(i, H));
+  }
+  if (NP % 2)
+    for (int l = 0; l < H; ++l) r.O[(NP + 1) / 2 - 1][l] = static_cast<T>(m(H, l));
+  return r;
+}
 
 template <int NP, typename T>
 inline GllParam<NP, T> make_gll_param(int N) {
@@ -26,7 +62,39 @@ inline GllParam<NP, T> make_gll_param(int N) {
     g.xi[a] = static_cast<T>(t.xi[a]);
     g.w[a] = static_cast<T>(t.w[a]);
   }
+  g.Df = make_eo<NP, T>([&](int i, int l) { return t.D[i * NP + l]; });
+  g.Dt = make_eo<NP, T>([&](int i, int l) { return t.D[l * NP + i]; });
   return g;
+}
+
+// out = M in through the even/odd split (see EoMat); `in` and `out` may not alias.
+template <int NP, typename T>
+__device__ __forceinline__ void eo_apply(const EoMat<NP, T>& M, const T (&in)[NP], T (&out)[NP]) {
+  constexpr int H = NP / 2, N = NP - 1;
+  T e[H], o[H];
+#pragma unroll
+  for (int l = 0; l < H; ++l) {
+    e[l] = in[l] + in[N - l];
+    o[l] = in[l] - in[N - l];
+  }
+#pragma unroll
+  for (int i = 0; i < H; ++i) {
+    T a = M.E[i][0] * e[0], b = M.O[i][0] * o[0];
+#pragma unroll
+    for (int l = 1; l < H; ++l) {
+      a += M.E[i][l] * e[l];
+      b += M.O[i][l] * o[l];
+    }
+    if constexpr (NP % 2 == 1) a += M.E[i][H] * in[H];
+    out[i] = a + b;
+    out[N - i] = b - a;
+  }
+  if constexpr (NP % 2 == 1) {
+    T c = M.O[H][0] * o[0];
+#pragma unroll
+    for (int l = 1; l < H; ++l) c += M.O[H][l] * o[l];
+    out[H] = c;
+  }
 }
 
 // Sum of `v` over the block in a fixed order (warp shuffle tree, then warps in order);
