@@ -234,10 +234,18 @@ __global__ void __launch_bounds__(NP * NP * EPB)
         wij = tab.w[i] * tab.w[j];
       }
     }
+    // (all loads first, then the arithmetic, then the stores: the compiler cannot move a load
+    // of the staging buffers above a store to them)
+    T rR[NP], rS[NP];
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
       const int at = Stage<NP>::at(i, j, k);
-      const T ur = sB[at], us = sA[at], ut = rT[k];
+      rR[k] = sB[at];
+      rS[k] = sA[at];
+    }
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      const T ur = rR[k], us = rS[k], ut = rT[k];
       T vr, vs, vt;
       if constexpr (OTF) {
         const T gam = tab.xi[k];
@@ -264,9 +272,15 @@ __global__ void __launch_bounds__(NP * NP * EPB)
         vs = g12 * ur + g22 * us + g23 * ut;
         vt = g13 * ur + g23 * us + g33 * ut;
       }
-      sB[at] = vr;
-      sA[at] = vs;
+      rR[k] = vr;
+      rS[k] = vs;
       rT[k] = vt;
+    }
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      const int at = Stage<NP>::at(i, j, k);
+      sB[at] = rR[k];
+      sA[at] = rS[k];
     }
     __syncthreads();  // the factors are consumed
     if constexpr (!OTF) {
@@ -282,18 +296,20 @@ __global__ void __launch_bounds__(NP * NP * EPB)
     // phase 4: D^T on i-rows of B and j-lines of A (in place) and on the column
     T rW[NP];
     {
-      T in[NP], out[NP];
+      T inR[NP], inS[NP], outR[NP], outS[NP];
 #pragma unroll
-      for (int l = 0; l < NP; ++l) in[l] = sB[Stage<NP>::at(l, i, j)];
-      eo_apply<NP, T>(tab.Dt, in, out);
-#pragma unroll
-      for (int l = 0; l < NP; ++l) sB[Stage<NP>::at(l, i, j)] = out[l];
-#pragma unroll
-      for (int l = 0; l < NP; ++l) in[l] = sA[Stage<NP>::at(i, l, j)];
-      eo_apply<NP, T>(tab.Dt, in, out);
-#pragma unroll
-      for (int l = 0; l < NP; ++l) sA[Stage<NP>::at(i, l, j)] = out[l];
+      for (int l = 0; l < NP; ++l) {
+        inR[l] = sB[Stage<NP>::at(l, i, j)];
+        inS[l] = sA[Stage<NP>::at(i, l, j)];
+      }
+      eo_apply<NP, T>(tab.Dt, inR, outR);
+      eo_apply<NP, T>(tab.Dt, inS, outS);
       eo_apply<NP, T>(tab.Dt, rT, rW);
+#pragma unroll
+      for (int l = 0; l < NP; ++l) {
+        sB[Stage<NP>::at(l, i, j)] = outR[l];
+        sA[Stage<NP>::at(i, l, j)] = outS[l];
+      }
     }
     __syncthreads();
 

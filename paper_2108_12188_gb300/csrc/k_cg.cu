@@ -6,9 +6,12 @@
 //
 // Weights c = 1 / multiplicity come from a per-point multiplicity byte and a 256-entry
 // table of exact reciprocals (interior points have multiplicity 1). Dot products are
-// accumulated in FP64 per thread and combined in a fixed order, so they are bitwise
-// reproducible for a given mesh and launch.
+// accumulated per thread and combined in FP64 in a fixed order, so they are bitwise
+// reproducible for a given mesh and launch. In the FP64 update the two dots run in
+// double-float arithmetic on the FP32 pipes (k_df.cuh): GB300's FP64 pipe, 1/64 of the FP32
+// rate, would otherwise bound the kernel above its HBM time.
 #include "k_common.cuh"
+#include "k_df.cuh"
 
 namespace sem {
 namespace {
@@ -111,19 +114,46 @@ __global__ void k_cg_update(int64_t n, T* __restrict__ x, const T* __restrict__ 
   __shared__ double sRed[kThreads / 32];
   if (st->done) return;
   const T alpha = static_cast<T>(st->alpha);
-  DotAcc<T> rz, rr;
-  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
-       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    x[i] += alpha * p[i];
-    const T ri = r[i] - alpha * w[i];
-    const T zi = minv ? minv[i] * ri : ri;
-    r[i] = ri;
-    z[i] = zi;
-    const T c = weight_t<T>(mult, ctab, i);
-    rz.add(ri, c * zi);
-    rr.add(ri, c * ri);
+  double v[2];
+  if constexpr (sizeof(T) == 8) {
+    // x, r, z: three FP64 operations per point. <r, z, c> and <r, r, c>: r and z as float
+    // pairs (integer split), c as a float pair from a shared table, (c r) an error-free
+    // product, then rz += (c r) z and rr += (c r) r in double-float.
+    __shared__ df2 sC[256];
+    for (int m = threadIdx.x; m < 256; m += blockDim.x) sC[m] = m == 1 ? df2{1.f, 0.f} : df_from_double(ctab[m]);
+    __syncthreads();
+    df2 rz{0.f, 0.f}, rr{0.f, 0.f};
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+      x[i] += alpha * p[i];
+      const T ri = r[i] - alpha * w[i];
+      const T zi = minv ? minv[i] * ri : ri;
+      r[i] = ri;
+      z[i] = zi;
+      const df2 r2 = df_from_double(ri), z2 = df_from_double(zi), c2 = sC[mult[i]];
+      float ch, cl;
+      df_prod(c2.h, c2.l, r2.h, r2.l, ch, cl);
+      df_fma_acc(rz, ch, cl, z2.h, z2.l);
+      df_fma_acc(rr, ch, cl, r2.h, r2.l);
+    }
+    v[0] = block_sum(static_cast<double>(rz.h) + static_cast<double>(rz.l), sRed);
+    v[1] = block_sum(static_cast<double>(rr.h) + static_cast<double>(rr.l), sRed);
+  } else {
+    DotAcc<T> rz, rr;
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+      x[i] += alpha * p[i];
+      const T ri = r[i] - alpha * w[i];
+      const T zi = minv ? minv[i] * ri : ri;
+      r[i] = ri;
+      z[i] = zi;
+      const T c = weight_t<T>(mult, ctab, i);
+      rz.add(ri, c * zi);
+      rr.add(ri, c * ri);
+    }
+    v[0] = block_sum(rz.value(), sRed);
+    v[1] = block_sum(rr.value(), sRed);
   }
-  const double v[2] = {block_sum(rz.value(), sRed), block_sum(rr.value(), sRed)};
   if (publish_partials<2>(v, partials, &st->ticket[1])) {
     const double srz = sum_partials(partials, gridDim.x, 2, 0, sRed);
     const double srr = sum_partials(partials, gridDim.x, 2, 1, sRed);
