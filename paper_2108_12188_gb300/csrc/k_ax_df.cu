@@ -2,14 +2,18 @@
 // computed in double-float arithmetic on the FP32 pipes (k_df.cuh): GB300 issues FP32
 // FMAs 61 times faster than FP64 ones, and the FP64 kernel is bound by the FP64 pipe.
 //
-// Same decomposition as k_ax: thread (i, j) of an element owns the column (i, j, 0..NP-1);
-// the element's field and the weighted derivatives vr, vs are staged in shared memory as
-// (h, l) float pairs; the k-direction stays in registers. Each contraction forms its
-// error-free products first and adds them with a pairwise two-sum tree.
+// Same decomposition as k_ax: thread t of an element contracts whole lines of NP values
+// (its i-row, its j-line and its k-column) in registers through the even/odd split of D and
+// D^T (EoMat), with the element staged in shared memory as (h, l) float pairs in the
+// swizzled layout of Stage. A line costs, per output, about 60 FP32 operations instead of
+// about 90 for the plain sums: the even and odd combinations are two-sums, each of the H
+// products is error-free, the H terms are added by a pairwise two-sum tree, and the pair
+// outputs A + B and B - A are renormalised.
 //
-// The six factor arrays of an element are one contiguous 24 KB block (N = 7): a bulk TMA
-// copy brings the next element group's block into shared memory while the current group
-// runs its transposed contractions, so the FP32 pipes do not wait on factor loads.
+// The six factor arrays of an element are one contiguous block (24 KB at N = 7): a bulk TMA
+// copy brings the next element group's block into shared memory during the rest of the
+// current group, so the FP32 pipes do not wait on factor loads (bounded mbarrier waits; a
+// timeout sets SEM_ERR_TIMEOUT).
 //
 // CG mode (Algorithm 1 steps 5-6): p = z + beta p in FP64 (one FMA per point), stored, and
 // the element-interior part of <p, w> accumulated in double-float.
@@ -20,30 +24,80 @@
 namespace sem {
 namespace {
 
+// Even/odd split of D and D^T (EoMat, computed in FP64) with every entry as a float pair.
 template <int NP>
-struct DfTab {
-  float Dh[NP * NP];  // D[a*NP + b] = Dh + Dl
-  float Dl[NP * NP];
+struct DfEo {
+  static constexpr int H = NP / 2, HC = (NP + 1) / 2;
+  float Eh[H][HC], El[H][HC];
+  float Oh[HC][H], Ol[HC][H];
 };
 
 template <int NP>
-DfTab<NP> make_df_tab(int N) {
-  const GllTable& t = gll_table(N);
-  DfTab<NP> d;
-  for (int a = 0; a < NP * NP; ++a) {
-    const double v = t.D[a];
-    d.Dh[a] = static_cast<float>(v);
-    d.Dl[a] = static_cast<float>(v - static_cast<double>(d.Dh[a]));
-  }
+struct DfTab {
+  DfEo<NP> Df, Dt;
+};
+
+template <int NP>
+DfEo<NP> split_eo(const EoMat<NP, double>& m) {
+  constexpr int H = NP / 2, HC = (NP + 1) / 2;
+  DfEo<NP> d{};
+  for (int a = 0; a < H; ++a)
+    for (int b = 0; b < HC; ++b) {
+      d.Eh[a][b] = static_cast<float>(m.E[a][b]);
+      d.El[a][b] = static_cast<float>(m.E[a][b] - static_cast<double>(d.Eh[a][b]));
+    }
+  for (int a = 0; a < HC; ++a)
+    for (int b = 0; b < H; ++b) {
+      d.Oh[a][b] = static_cast<float>(m.O[a][b]);
+      d.Ol[a][b] = static_cast<float>(m.O[a][b] - static_cast<double>(d.Oh[a][b]));
+    }
   return d;
+}
+
+template <int NP>
+DfTab<NP> make_df_tab(int N) {
+  const GllParam<NP, double> g = make_gll_param<NP, double>(N);
+  return {split_eo<NP>(g.Df), split_eo<NP>(g.Dt)};
+}
+
+// out = M in in double-float (see EoMat for the split); `in` and `out` may not alias.
+template <int NP>
+__device__ __forceinline__ void eo_apply_df(const DfEo<NP>& M, const df2 (&in)[NP], df2 (&out)[NP]) {
+  constexpr int H = NP / 2, N = NP - 1, HA = H + NP % 2;
+  df2 e[H], o[H];
+#pragma unroll
+  for (int l = 0; l < H; ++l) {
+    e[l] = df_add_nr(in[l], in[N - l]);
+    o[l] = df_add_nr(in[l], df_neg(in[N - l]));
+  }
+#pragma unroll
+  for (int i = 0; i < H; ++i) {
+    float pa[HA], ea[HA], pb[H], eb[H];
+#pragma unroll
+    for (int l = 0; l < H; ++l) {
+      df_prod(M.Eh[i][l], M.El[i][l], e[l].h, e[l].l, pa[l], ea[l]);
+      df_prod(M.Oh[i][l], M.Ol[i][l], o[l].h, o[l].l, pb[l], eb[l]);
+    }
+    if constexpr (NP % 2 == 1) df_prod(M.Eh[i][H], M.El[i][H], in[H].h, in[H].l, pa[H], ea[H]);
+    const df2 A = df_tree_sum_nr<HA>(pa, ea);
+    const df2 B = df_tree_sum_nr<H>(pb, eb);
+    out[i] = df_norm(df_add_nr(A, B));
+    out[N - i] = df_norm(df_add_nr(B, df_neg(A)));
+  }
+  if constexpr (NP % 2 == 1) {
+    float pc[H], ec[H];
+#pragma unroll
+    for (int l = 0; l < H; ++l) df_prod(M.Oh[H][l], M.Ol[H][l], o[l].h, o[l].l, pc[l], ec[l]);
+    out[H] = df_tree_sum<H>(pc, ec);
+  }
 }
 
 template <int NP>
 constexpr size_t df_smem_bytes() {
   constexpr int P = NP * NP * NP, EPB = ax_epb<NP>();
-  return static_cast<size_t>(EPB) * 6 * P * sizeof(double)  // factors of the element group (TMA target)
-         + 3 * static_cast<size_t>(EPB) * P * sizeof(df2)     // u, vr, vs as float pairs
-         + 2 * NP * NP * sizeof(float) + 16;                  // D split, mbarrier
+  return static_cast<size_t>(EPB) * 6 * P * sizeof(double)                // factors of the group (TMA target)
+         + 2 * static_cast<size_t>(EPB) * Stage<NP>::kSize * sizeof(df2)  // staging buffers A, B
+         + 16;                                                             // mbarrier
 }
 
 // Copies the factors of the element group starting at element e0 (count elements, each a
@@ -57,31 +111,29 @@ __device__ __forceinline__ void prefetch_factors(double* sG, const double* G, in
   for (int q = 0; q < count; ++q) tma_load_1d(sG + q * 6 * P, G + (e0 + q) * 6 * P, kElemBytes, bar);
 }
 
+// Phases of a group, as in k_ax (barrier between phases; each thread owns one i-row, one
+// j-line and one k-column of its element in the in-place phases):
+//   0 column of u (or p = z + beta p) -> registers and A;  1 i-rows of A -> ur into B, column -> ut;
+//   2 j-lines of A -> us in place;  3 column: G (ur, us, ut);  4 D^T on rows, lines, column;
+//   5 column: w = sum of the three, converted to FP64 and stored.
 template <int NP, bool CG>
 __global__ void __launch_bounds__(NP * NP * ax_epb<NP>())
     k_ax_df(const __grid_constant__ DfTab<NP> tab, int64_t E, const double* __restrict__ u, double* __restrict__ w,
             const double* __restrict__ G, const double* __restrict__ z, double* __restrict__ p,
             CgScalars* __restrict__ st, double* __restrict__ partials, int* __restrict__ err) {
-  constexpr int NP2 = NP * NP, P = NP2 * NP, EPB = ax_epb<NP>();
+  constexpr int NP2 = NP * NP, P = NP2 * NP, EPB = ax_epb<NP>(), SZ = Stage<NP>::kSize;
   extern __shared__ __align__(128) unsigned char smem[];
   double* sG = reinterpret_cast<double*>(smem);
-  df2* sU = reinterpret_cast<df2*>(sG + EPB * 6 * P);
-  df2* sR = sU + EPB * P;
-  df2* sS = sR + EPB * P;
-  float* sDh = reinterpret_cast<float*>(sS + EPB * P);
-  float* sDl = sDh + NP2;
-  // byte offset of sDl + NP2 is EPB*6*P*8 + 3*EPB*P*8 + 8*NP2: a multiple of 8, as the mbarrier needs
-  uint64_t* bar = reinterpret_cast<uint64_t*>(sDl + NP2);
+  df2* sA0 = reinterpret_cast<df2*>(sG + EPB * 6 * P);
+  df2* sB0 = sA0 + EPB * SZ;
+  // byte offset EPB*6*P*8 + 2*EPB*SZ*8: a multiple of 8, as the mbarrier needs
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sB0 + EPB * SZ);
   __shared__ double sRed[32];
 
   double beta = 0.0;
   if constexpr (CG) {
     if (st->done) return;
     beta = st->beta;
-  }
-  for (int q = threadIdx.x; q < NP2; q += blockDim.x) {
-    sDh[q] = tab.Dh[q];
-    sDl[q] = tab.Dl[q];
   }
   const int64_t n_groups = (E + EPB - 1) / EPB;
   if (threadIdx.x == 0) {
@@ -90,7 +142,9 @@ __global__ void __launch_bounds__(NP * NP * ax_epb<NP>())
     prefetch_factors<NP>(sG, G, e0, static_cast<int>(E - e0 < EPB ? E - e0 : EPB), bar);
   }
   const int slot = threadIdx.x / NP2, tid = threadIdx.x % NP2;
-  const int i = tid % NP, j = tid / NP;
+  const int i = tid % NP, j = tid / NP;  // column (i, j); i-row (j, k) = (i, j); j-line (i, k) = (i, j)
+  df2* sA = sA0 + slot * SZ;
+  df2* sB = sB0 + slot * SZ;
   df2 dot{0.f, 0.f};
   unsigned parity = 0;
   __syncthreads();
@@ -99,6 +153,7 @@ __global__ void __launch_bounds__(NP * NP * ax_epb<NP>())
     const int64_t e = grp * EPB + slot;
     const bool valid = e < E;
     const int64_t base = e * P + tid;
+    // phase 0
     df2 rU[NP];
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
@@ -112,9 +167,31 @@ __global__ void __launch_bounds__(NP * NP * ax_epb<NP>())
         }
       }
       rU[k] = df_from_double(val);
-      sU[slot * P + k * NP2 + tid] = rU[k];
+      sA[Stage<NP>::at(i, j, k)] = rU[k];
     }
-    const bool ok = mbar_wait_bounded(bar, parity);
+    __syncthreads();
+    // phase 1
+    df2 rT[NP];
+    {
+      df2 in[NP], out[NP];
+#pragma unroll
+      for (int l = 0; l < NP; ++l) in[l] = sA[Stage<NP>::at(l, i, j)];
+      eo_apply_df<NP>(tab.Df, in, out);
+#pragma unroll
+      for (int l = 0; l < NP; ++l) sB[Stage<NP>::at(l, i, j)] = out[l];
+      eo_apply_df<NP>(tab.Df, rU, rT);
+    }
+    __syncthreads();
+    // phase 2
+    {
+      df2 in[NP], out[NP];
+#pragma unroll
+      for (int l = 0; l < NP; ++l) in[l] = sA[Stage<NP>::at(i, l, j)];
+      eo_apply_df<NP>(tab.Df, in, out);
+#pragma unroll
+      for (int l = 0; l < NP; ++l) sA[Stage<NP>::at(i, l, j)] = out[l];
+    }
+    const bool ok = mbar_wait_bounded(bar, parity);  // this group's factors
     parity ^= 1u;
     if (__syncthreads_or(!ok)) {  // the factor copy did not arrive: report and leave together
       if (threadIdx.x == 0) {
@@ -127,66 +204,79 @@ __global__ void __launch_bounds__(NP * NP * ax_epb<NP>())
       }
       return;
     }
-
-    const double* gE = sG + slot * 6 * P;
-    df2 rT[NP];
+    // phase 3
+    {
+      const double* gE = sG + slot * 6 * P;
+      df2 rR[NP], rS[NP];
 #pragma unroll
-    for (int k = 0; k < NP; ++k) {
-      float pr[NP], er[NP], ps[NP], es[NP], pt[NP], et[NP];
-#pragma unroll
-      for (int l = 0; l < NP; ++l) {
-        const df2 a = sU[slot * P + k * NP2 + j * NP + l];
-        const df2 b = sU[slot * P + k * NP2 + l * NP + i];
-        df_prod(sDh[i * NP + l], sDl[i * NP + l], a.h, a.l, pr[l], er[l]);
-        df_prod(sDh[j * NP + l], sDl[j * NP + l], b.h, b.l, ps[l], es[l]);
-        df_prod(tab.Dh[k * NP + l], tab.Dl[k * NP + l], rU[l].h, rU[l].l, pt[l], et[l]);
+      for (int k = 0; k < NP; ++k) {
+        const int at = Stage<NP>::at(i, j, k);
+        rR[k] = sB[at];
+        rS[k] = sA[at];
       }
-      const df2 ur = df_tree_sum<NP>(pr, er);
-      const df2 us = df_tree_sum<NP>(ps, es);
-      const df2 ut = df_tree_sum<NP>(pt, et);
-      df2 g[6];
 #pragma unroll
-      for (int m = 0; m < 6; ++m) g[m] = df_from_double(gE[m * P + k * NP2 + tid]);
-      float p3[3], e3[3];
-      df_prod(g[0].h, g[0].l, ur.h, ur.l, p3[0], e3[0]);
-      df_prod(g[1].h, g[1].l, us.h, us.l, p3[1], e3[1]);
-      df_prod(g[2].h, g[2].l, ut.h, ut.l, p3[2], e3[2]);
-      sR[slot * P + k * NP2 + tid] = df_tree_sum<3>(p3, e3);
-      df_prod(g[1].h, g[1].l, ur.h, ur.l, p3[0], e3[0]);
-      df_prod(g[3].h, g[3].l, us.h, us.l, p3[1], e3[1]);
-      df_prod(g[4].h, g[4].l, ut.h, ut.l, p3[2], e3[2]);
-      sS[slot * P + k * NP2 + tid] = df_tree_sum<3>(p3, e3);
-      df_prod(g[2].h, g[2].l, ur.h, ur.l, p3[0], e3[0]);
-      df_prod(g[4].h, g[4].l, us.h, us.l, p3[1], e3[1]);
-      df_prod(g[5].h, g[5].l, ut.h, ut.l, p3[2], e3[2]);
-      rT[k] = df_tree_sum<3>(p3, e3);
+      for (int k = 0; k < NP; ++k) {
+        df2 g[6];
+#pragma unroll
+        for (int m = 0; m < 6; ++m) g[m] = df_from_double(gE[m * P + k * NP2 + tid]);
+        const df2 ur = rR[k], us = rS[k], ut = rT[k];
+        float p3[3], e3[3];
+        df_prod(g[0].h, g[0].l, ur.h, ur.l, p3[0], e3[0]);
+        df_prod(g[1].h, g[1].l, us.h, us.l, p3[1], e3[1]);
+        df_prod(g[2].h, g[2].l, ut.h, ut.l, p3[2], e3[2]);
+        rR[k] = df_tree_sum<3>(p3, e3);
+        df_prod(g[1].h, g[1].l, ur.h, ur.l, p3[0], e3[0]);
+        df_prod(g[3].h, g[3].l, us.h, us.l, p3[1], e3[1]);
+        df_prod(g[4].h, g[4].l, ut.h, ut.l, p3[2], e3[2]);
+        rS[k] = df_tree_sum<3>(p3, e3);
+        df_prod(g[2].h, g[2].l, ur.h, ur.l, p3[0], e3[0]);
+        df_prod(g[4].h, g[4].l, us.h, us.l, p3[1], e3[1]);
+        df_prod(g[5].h, g[5].l, ut.h, ut.l, p3[2], e3[2]);
+        rT[k] = df_tree_sum<3>(p3, e3);
+      }
+#pragma unroll
+      for (int k = 0; k < NP; ++k) {
+        const int at = Stage<NP>::at(i, j, k);
+        sB[at] = rR[k];
+        sA[at] = rS[k];
+      }
     }
-    __syncthreads();  // sG and sU consumed; sR, sS complete
+    __syncthreads();  // the factors are consumed
     if (threadIdx.x == 0 && grp + gridDim.x < n_groups) {
       const int64_t e0 = (grp + gridDim.x) * EPB;
       prefetch_factors<NP>(sG, G, e0, static_cast<int>(E - e0 < EPB ? E - e0 : EPB), bar);
     }
-#pragma unroll
-    for (int k = 0; k < NP; ++k) {
-      float pr[NP], er[NP], ps[NP], es[NP], pt[NP], et[NP];
+    // phase 4
+    df2 rW[NP];
+    {
+      df2 inR[NP], inS[NP], outR[NP], outS[NP];
 #pragma unroll
       for (int l = 0; l < NP; ++l) {
-        const df2 a = sR[slot * P + k * NP2 + j * NP + l];
-        const df2 b = sS[slot * P + k * NP2 + l * NP + i];
-        df_prod(sDh[l * NP + i], sDl[l * NP + i], a.h, a.l, pr[l], er[l]);
-        df_prod(sDh[l * NP + j], sDl[l * NP + j], b.h, b.l, ps[l], es[l]);
-        df_prod(tab.Dh[l * NP + k], tab.Dl[l * NP + k], rT[l].h, rT[l].l, pt[l], et[l]);
+        inR[l] = sB[Stage<NP>::at(l, i, j)];
+        inS[l] = sA[Stage<NP>::at(i, l, j)];
       }
-      const df2 wr = df_tree_sum<NP>(pr, er);
-      const df2 ws = df_tree_sum<NP>(ps, es);
-      const df2 wt = df_tree_sum<NP>(pt, et);
-      const df2 acc = df_add(df_add(wr, ws), wt);
+      eo_apply_df<NP>(tab.Dt, inR, outR);
+      eo_apply_df<NP>(tab.Dt, inS, outS);
+      eo_apply_df<NP>(tab.Dt, rT, rW);
+#pragma unroll
+      for (int l = 0; l < NP; ++l) {
+        sB[Stage<NP>::at(l, i, j)] = outR[l];
+        sA[Stage<NP>::at(i, l, j)] = outS[l];
+      }
+    }
+    __syncthreads();
+    // phase 5
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      const int at = Stage<NP>::at(i, j, k);
+      const df2 acc = df_norm(df_add_nr(df_add_nr(sB[at], sA[at]), rW[k]));
       if (valid) w[base + k * NP2] = df_to_double(acc);
       if constexpr (CG) {
         const bool interior = i > 0 && i < NP - 1 && j > 0 && j < NP - 1 && k > 0 && k < NP - 1;
         if (valid && interior) df_fma_acc(dot, rU[k].h, rU[k].l, acc.h, acc.l);
       }
     }
+    __syncthreads();  // the staging buffers are free for the next group
   }
   if constexpr (CG) {
     const double s = block_sum(static_cast<double>(dot.h) + static_cast<double>(dot.l), sRed);

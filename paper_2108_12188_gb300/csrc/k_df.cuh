@@ -104,9 +104,37 @@ __device__ __forceinline__ void df_prod(float ah, float al, float bh, float bl, 
   e = __fmaf_rn(al, bh, e);
 }
 
+// a + b without the final renormalisation: (s, t + a.l + b.l) with s + t = a.h + b.h exactly
+// (Knuth's two-sum); the pair is a valid operand of df_prod and df_add.
+__device__ __forceinline__ df2 df_add_nr(df2 a, df2 b) {
+  const float s = __fadd_rn(a.h, b.h);
+  const float bb = __fsub_rn(s, a.h);
+  const float t = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, bb)), __fsub_rn(b.h, bb));
+  return {s, __fadd_rn(t, __fadd_rn(a.l, b.l))};
+}
+
+__device__ __forceinline__ df2 df_neg(df2 a) { return {-a.h, -a.l}; }
+
 // Sum of K terms (p[q] + e[q]) by a pairwise two-sum tree over the high parts; the exact
 // rounding errors are gathered into the low parts along the same tree. The critical path
-// is log2(K) two-sums instead of K - 1. Returns the renormalised pair.
+// is log2(K) two-sums instead of K - 1. Returns the pair without renormalisation.
+template <int K>
+__device__ __forceinline__ df2 df_tree_sum_nr(float (&p)[K], float (&e)[K]) {
+#pragma unroll
+  for (int w = 1; w < K; w *= 2) {
+#pragma unroll
+    for (int a = 0; a + w < K; a += 2 * w) {
+      const float s = __fadd_rn(p[a], p[a + w]);
+      const float bb = __fsub_rn(s, p[a]);
+      const float t = __fadd_rn(__fsub_rn(p[a], __fsub_rn(s, bb)), __fsub_rn(p[a + w], bb));
+      p[a] = s;
+      e[a] = __fadd_rn(e[a], __fadd_rn(t, e[a + w]));
+    }
+  }
+  return {p[0], e[0]};
+}
+
+// The same sum, renormalised.
 template <int K>
 __device__ __forceinline__ df2 df_tree_sum(float (&p)[K], float (&e)[K]) {
 #pragma unroll
