@@ -241,17 +241,33 @@ def oracle_cg_sample(nel: int = 12, budget_s: float = 10.0) -> dict:
                       f"{iters} oracle Jacobi-PCG iterations"}
 
 
-def run_cpu_baseline(budget_s: float = 10.0) -> dict:
-    """Runs oracle_cg_sample in a fresh single-threaded process (no CUDA state inherited)."""
+def _oracle_procs(count: int, budget_s: float) -> list:
+    """Runs oracle_cg_sample in `count` fresh single-threaded processes at the same time (no
+    CUDA state inherited); returns their results."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     code = ("import json, bench; print('RESULT ' + json.dumps(bench.oracle_cg_sample(budget_s=%r)))" % budget_s)
-    p = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
-    for ln in p.stdout.splitlines():
-        if ln.startswith("RESULT "):
-            r = json.loads(ln[7:])
-            return {"value": r["gdof_s"], "unit": "GDOF/s", "cores": 1, "kind": "oracle", "sample": r["sample"],
-                    "s_per_iter": r["s_per_iter"]}
-    raise RuntimeError("cpu baseline failed: " + p.stderr[-2000:])
+    procs = [subprocess.Popen([sys.executable, "-c", code], cwd=ROOT, env=env, stdout=subprocess.PIPE,
+                              stderr=subprocess.PIPE, text=True) for _ in range(count)]
+    out = []
+    for p in procs:
+        so_, se_ = p.communicate(timeout=900)
+        res = [json.loads(ln[7:]) for ln in so_.splitlines() if ln.startswith("RESULT ")]
+        if not res:
+            raise RuntimeError("cpu baseline failed: " + se_[-2000:])
+        out.append(res[0])
+    return out
+
+
+def run_cpu_baseline(budget_s: float = 10.0) -> dict:
+    """The oracle on the host cores: one process alone, then one process per core at once
+    (the oracle is single-threaded; each process times its own sample)."""
+    single = _oracle_procs(1, budget_s)[0]
+    cores = max(1, min(os.cpu_count() or 1, 72))
+    many = _oracle_procs(cores, budget_s) if cores > 1 else [single]
+    total = sum(r["gdof_s"] for r in many)
+    return {"value": total, "unit": "GDOF/s", "cores": cores, "kind": "oracle",
+            "sample": f"{single['sample']}; one such sample per core, {cores} single-threaded processes at once",
+            "single_core_value": single["gdof_s"], "s_per_iter_single_core": single["s_per_iter"]}
 
 
 # ---------------------------------------------------------------------------

@@ -408,7 +408,7 @@ extern "C" sem_status sem_scatter(sem_mesh m, sem_prec prec, const void* ug, voi
   SEM_TRY(check_ptr(ul, "u_local_dev"));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   note_stream(m, s);
-  const std::vector<int32_t>& g32 = m->glo;
+  const HostVec<int32_t>& g32 = m->glo;
   int32_t* gd = nullptr;
   SEM_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&gd), g32.size() * 4, s));
   sem_status st = SEM_OK;

@@ -4,7 +4,9 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <memory>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/sem.h"
@@ -31,15 +33,38 @@ struct GllTable {
 const GllTable& gll_table(int N);  // N in [1, SEM_MAX_N]
 
 // ---- host topology builder (topology.cpp) ----
+// Allocator whose resize() leaves new elements uninitialised: the builder writes every
+// element from its worker threads, so the pages are first touched in parallel.
+template <typename T>
+struct NoInitAlloc : std::allocator<T> {
+  template <typename U>
+  struct rebind {
+    using other = NoInitAlloc<U>;
+  };
+  NoInitAlloc() = default;
+  template <typename U>
+  NoInitAlloc(const NoInitAlloc<U>&) noexcept {}
+  template <typename U>
+  void construct(U* p) noexcept {
+    ::new (static_cast<void*>(p)) U;
+  }
+  template <typename U, typename... A>
+  void construct(U* p, A&&... a) {
+    ::new (static_cast<void*>(p)) U(std::forward<A>(a)...);
+  }
+};
+template <typename T>
+using HostVec = std::vector<T, NoInitAlloc<T>>;
+
 struct Topology {
   int N = 0, Np = 0;
   int64_t E = 0, n = 0, n_glob = 0;
-  std::vector<int32_t> glo;      // [n] (n < 2^31)
-  std::vector<uint8_t> mask;     // [n]
-  std::vector<uint8_t> mult;     // [n] multiplicity of the node's global id (<= 255)
-  std::vector<int32_t> seg_off;  // [n_seg + 1]
-  std::vector<int32_t> seg_idx;  // [n_gs]
-  std::vector<uint8_t> seg_mask; // [n_seg]
+  HostVec<int32_t> glo;      // [n] (n < 2^31)
+  HostVec<uint8_t> mask;     // [n]
+  HostVec<uint8_t> mult;     // [n] multiplicity of the node's global id (<= 255)
+  HostVec<int32_t> seg_off;  // [n_seg + 1]
+  HostVec<int32_t> seg_idx;  // [n_gs]
+  HostVec<uint8_t> seg_mask; // [n_seg]
 };
 sem_status build_topology(int N, int64_t num_vertices, int64_t E, const int64_t* elem_verts,
                           const uint8_t* dirichlet_flags, Topology& out);
@@ -69,8 +94,8 @@ struct sem_mesh_s {
   int N = 0, Np = 0, device = 0;
   unsigned flags = 0;
   int64_t E = 0, n = 0, n_glob = 0, n_seg = 0, n_gs = 0;
-  std::vector<int32_t> glo;   // host copy for the test hooks
-  std::vector<uint8_t> mask;  // host copy
+  sem::HostVec<int32_t> glo;   // host copy for the test hooks
+  sem::HostVec<uint8_t> mask;  // host copy
   // device arrays
   double* coef64 = nullptr;   // [E][24] trilinear coefficients a0..a7 (x, y, z)
   float* coef32 = nullptr;    // [E][24] rounded to FP32

@@ -9,12 +9,20 @@
 // corner and whose first axis points to the origin's lower-id neighbour. Global ids are
 // assigned in order of first occurrence in the local order (element, k, j, i).
 //
-// Implementation: edges and faces get ids by sorting their vertex keys; every entity
-// position then maps to a dense integer key, and a single pass over the local points
-// hands out ids at first sight. Element-interior points are always new.
+// Implementation: edges and faces get ids by sorting their vertex keys (ties by position, so
+// every entity lists the elements that hold it in ascending order); each vertex, edge and
+// face knows the first element that holds it, how many elements hold it and whether it lies
+// on a Dirichlet face. A node is new in element e iff its entity's first element is e, so
+// the count of new nodes per element, a prefix sum over elements and two passes over the
+// elements (new nodes, then the nodes seen before) number every point; these passes, the
+// multiplicities, the mask and the segment lists run on all host threads, element by
+// element, and give the same result as a sequential pass. Element-interior points are
+// always new.
 #include <algorithm>
 #include <array>
+#include <memory>
 #include <numeric>
+#include <thread>
 
 #include "sem_internal.h"
 
@@ -29,6 +37,41 @@ struct ElemFrames {
   int64_t face_id[6];
   int8_t face_oa[6], face_ob[6];
   bool face_swap[6];   // true if the canonical first axis is the local second free axis
+};
+
+// Calls f(begin, end) on contiguous chunks of [0, n), one per host thread (at most 32, and
+// chunks of at least `grain` items); the calling thread takes the first chunk. f must not
+// throw. If a thread cannot be started its chunk runs on the calling thread.
+template <typename F>
+void parallel_for(int64_t n, int64_t grain, const F& f) {
+  if (n <= 0) return;
+  const unsigned hw = std::thread::hardware_concurrency();
+  int64_t T = hw == 0 ? 1 : std::min<int64_t>(hw, 32);
+  T = std::max<int64_t>(1, std::min<int64_t>(T, (n + grain - 1) / grain));
+  const int64_t chunk = (n + T - 1) / T;
+  std::vector<std::thread> th;
+  th.reserve(static_cast<size_t>(T));
+  for (int64_t t = 1; t < T; ++t) {
+    const int64_t b = t * chunk, e = std::min(n, b + chunk);
+    if (b >= e) break;
+    try {
+      th.emplace_back([&f, b, e] { f(b, e); });
+    } catch (...) {
+      f(b, e);
+    }
+  }
+  f(int64_t(0), std::min(n, chunk));
+  for (auto& x : th) x.join();
+}
+
+// Entity of an element-boundary position: dense key of the node, first element holding the
+// entity, number of elements holding it, Dirichlet flag, rank of this element among them.
+struct PosEntity {
+  int64_t key;
+  int64_t first;
+  int32_t count;
+  uint8_t dir;
+  int32_t rank;
 };
 
 }  // namespace
@@ -48,103 +91,138 @@ sem_status build_topology(int N, int64_t nv, int64_t E, const int64_t* ev, const
         if (v[a] == v[b]) return fail(SEM_ERR_MESH, "element " + std::to_string(e) + " repeats a vertex id");
     }
   }
+  constexpr int64_t kGrain = 256;  // elements per chunk at least
 
-  // ---- edges: local edge d*4 + x + 2y runs along axis d; the other two axes (in order) sit at ends x, y
-  std::vector<std::array<int64_t, 2>> ekey(E * 12);
-  for (int64_t e = 0; e < E; ++e) {
-    const int64_t* v = ev + 8 * e;
-    for (int d = 0; d < 3; ++d)
-      for (int xy = 0; xy < 4; ++xy) {
-        int lo[3], hi[3];
-        const int d1 = d == 0 ? 1 : 0, d2 = d == 2 ? 1 : 2;
-        lo[d] = 0; hi[d] = 1;
-        lo[d1] = hi[d1] = xy & 1;
-        lo[d2] = hi[d2] = xy >> 1;
-        int64_t a = v[corner(lo[0], lo[1], lo[2])], b = v[corner(hi[0], hi[1], hi[2])];
-        ekey[e * 12 + d * 4 + xy] = {std::min(a, b), std::max(a, b)};
-      }
+  // ---- vertices: the elements holding each vertex, ascending, and each element's rank
+  std::vector<int32_t> vcount(nv, 0);
+  for (int64_t q = 0; q < 8 * E; ++q) ++vcount[ev[q]];
+  for (int64_t x = 0; x < nv; ++x)
+    if (vcount[x] > 255) return fail(SEM_ERR_MESH, "a global node has more than 255 local copies");
+  std::vector<int64_t> vfirst(nv, -1);
+  std::vector<int32_t> vseen(nv, 0);
+  std::vector<uint8_t> vrank(8 * E);
+  for (int64_t q = 0; q < 8 * E; ++q) {
+    const int64_t x = ev[q];
+    if (vfirst[x] < 0) vfirst[x] = q / 8;
+    vrank[q] = static_cast<uint8_t>(vseen[x]++);
   }
-  std::vector<int64_t> eorder(E * 12);
-  std::iota(eorder.begin(), eorder.end(), 0);
-  std::sort(eorder.begin(), eorder.end(), [&](int64_t p, int64_t q) { return ekey[p] < ekey[q]; });
-  std::vector<int64_t> edge_of(E * 12);
-  int64_t n_edges = 0;
-  for (size_t r = 0; r < eorder.size(); ++r) {
-    if (r > 0 && ekey[eorder[r]] != ekey[eorder[r - 1]]) ++n_edges;
-    edge_of[eorder[r]] = n_edges;
-  }
-  ++n_edges;
-  std::vector<std::array<int64_t, 2>>().swap(ekey);
+  std::vector<int32_t>().swap(vseen);
 
-  // ---- faces: local face d*2 + s has axis d at end s; corners c[a][b] over the other axes (in order)
-  std::vector<std::array<int64_t, 4>> fkey(E * 6);
-  for (int64_t e = 0; e < E; ++e) {
-    const int64_t* v = ev + 8 * e;
-    for (int d = 0; d < 3; ++d)
-      for (int s = 0; s < 2; ++s) {
-        const int d1 = d == 0 ? 1 : 0, d2 = d == 2 ? 1 : 2;
-        std::array<int64_t, 4> k4;
-        for (int ab = 0; ab < 4; ++ab) {
-          int c3[3];
-          c3[d] = s; c3[d1] = ab & 1; c3[d2] = ab >> 1;
-          k4[ab] = v[corner(c3[0], c3[1], c3[2])];
+  // ---- edges: local edge d*4 + x + 2y runs along axis d; the other two axes (in order) sit at ends x, y.
+  // Records (low vertex, high vertex, position e*12 + edge) sorted; ties by position.
+  std::vector<std::array<int64_t, 3>> erec(E * 12);
+  parallel_for(E, kGrain, [&](int64_t b0, int64_t b1) {
+    for (int64_t e = b0; e < b1; ++e) {
+      const int64_t* v = ev + 8 * e;
+      for (int d = 0; d < 3; ++d)
+        for (int xy = 0; xy < 4; ++xy) {
+          int lo[3], hi[3];
+          const int d1 = d == 0 ? 1 : 0, d2 = d == 2 ? 1 : 2;
+          lo[d] = 0; hi[d] = 1;
+          lo[d1] = hi[d1] = xy & 1;
+          lo[d2] = hi[d2] = xy >> 1;
+          const int64_t a = v[corner(lo[0], lo[1], lo[2])], c = v[corner(hi[0], hi[1], hi[2])];
+          erec[e * 12 + d * 4 + xy] = {std::min(a, c), std::max(a, c), e * 12 + d * 4 + xy};
         }
-        std::sort(k4.begin(), k4.end());
-        fkey[e * 6 + d * 2 + s] = k4;
-      }
+    }
+  });
+  // ---- faces: local face d*2 + s has axis d at end s; corners c[a][b] over the other axes (in order).
+  // Records (sorted four vertex ids, position e*6 + face) sorted; ties by position.
+  std::vector<std::array<int64_t, 5>> frec(E * 6);
+  parallel_for(E, kGrain, [&](int64_t b0, int64_t b1) {
+    for (int64_t e = b0; e < b1; ++e) {
+      const int64_t* v = ev + 8 * e;
+      for (int d = 0; d < 3; ++d)
+        for (int s = 0; s < 2; ++s) {
+          const int d1 = d == 0 ? 1 : 0, d2 = d == 2 ? 1 : 2;
+          std::array<int64_t, 5> k5;
+          for (int ab = 0; ab < 4; ++ab) {
+            int c3[3];
+            c3[d] = s; c3[d1] = ab & 1; c3[d2] = ab >> 1;
+            k5[ab] = v[corner(c3[0], c3[1], c3[2])];
+          }
+          std::sort(k5.begin(), k5.begin() + 4);
+          k5[4] = e * 6 + d * 2 + s;
+          frec[e * 6 + d * 2 + s] = k5;
+        }
+    }
+  });
+  parallel_for(2, 1, [&](int64_t b0, int64_t b1) {  // the two sorts side by side
+    for (int64_t w = b0; w < b1; ++w) {
+      if (w == 0)
+        std::sort(erec.begin(), erec.end());
+      else
+        std::sort(frec.begin(), frec.end());
+    }
+  });
+  std::vector<int64_t> edge_of(E * 12), efirst;
+  std::vector<int32_t> ecount;
+  std::vector<uint8_t> erank(E * 12);
+  for (size_t r = 0; r < erec.size(); ++r) {
+    if (r == 0 || erec[r][0] != erec[r - 1][0] || erec[r][1] != erec[r - 1][1]) {
+      efirst.push_back(erec[r][2] / 12);
+      ecount.push_back(0);
+    }
+    edge_of[erec[r][2]] = static_cast<int64_t>(efirst.size()) - 1;
+    if (ecount.back() >= 255) return fail(SEM_ERR_MESH, "a global node has more than 255 local copies");
+    erank[erec[r][2]] = static_cast<uint8_t>(ecount.back()++);
   }
-  std::vector<int64_t> forder(E * 6);
-  std::iota(forder.begin(), forder.end(), 0);
-  std::sort(forder.begin(), forder.end(), [&](int64_t p, int64_t q) { return fkey[p] < fkey[q]; });
-  std::vector<int64_t> face_of(E * 6);
+  const int64_t n_edges = static_cast<int64_t>(efirst.size());
+  std::vector<std::array<int64_t, 3>>().swap(erec);
+  std::vector<int64_t> face_of(E * 6), ffirst;
   std::vector<int32_t> face_count;
-  int64_t n_faces = 0;
-  for (size_t r = 0; r < forder.size(); ++r) {
-    if (r > 0 && fkey[forder[r]] != fkey[forder[r - 1]]) ++n_faces;
-    face_of[forder[r]] = n_faces;
-    if (static_cast<int64_t>(face_count.size()) <= n_faces) face_count.push_back(0);
-    ++face_count[n_faces];
+  std::vector<uint8_t> frank(E * 6);
+  for (size_t r = 0; r < frec.size(); ++r) {
+    if (r == 0 || !std::equal(frec[r].begin(), frec[r].begin() + 4, frec[r - 1].begin())) {
+      ffirst.push_back(frec[r][4] / 6);
+      face_count.push_back(0);
+    }
+    face_of[frec[r][4]] = static_cast<int64_t>(ffirst.size()) - 1;
+    frank[frec[r][4]] = static_cast<uint8_t>(face_count.back()++);
+    if (face_count.back() > 2) return fail(SEM_ERR_MESH, "a face is shared by more than two elements");
   }
-  ++n_faces;
-  for (int32_t c : face_count)
-    if (c > 2) return fail(SEM_ERR_MESH, "a face is shared by more than two elements");
-  std::vector<std::array<int64_t, 4>>().swap(fkey);
+  const int64_t n_faces = static_cast<int64_t>(ffirst.size());
+  std::vector<std::array<int64_t, 5>>().swap(frec);
 
   // ---- per-element frames
-  auto frames_of = [&](int64_t e) {
-    ElemFrames f;
-    const int64_t* v = ev + 8 * e;
-    for (int d = 0; d < 3; ++d) {
-      const int d1 = d == 0 ? 1 : 0, d2 = d == 2 ? 1 : 2;
-      for (int xy = 0; xy < 4; ++xy) {
-        int lo[3], hi[3];
-        lo[d] = 0; hi[d] = 1;
-        lo[d1] = hi[d1] = xy & 1;
-        lo[d2] = hi[d2] = xy >> 1;
-        f.edge_id[d * 4 + xy] = edge_of[e * 12 + d * 4 + xy];
-        f.edge_rev[d * 4 + xy] = v[corner(lo[0], lo[1], lo[2])] > v[corner(hi[0], hi[1], hi[2])];
-      }
-      for (int s = 0; s < 2; ++s) {
-        int64_t c[2][2];
-        for (int a = 0; a < 2; ++a)
-          for (int b = 0; b < 2; ++b) {
-            int c3[3];
-            c3[d] = s; c3[d1] = a; c3[d2] = b;
-            c[a][b] = v[corner(c3[0], c3[1], c3[2])];
-          }
-        int oa = 0, ob = 0;
-        for (int a = 0; a < 2; ++a)
-          for (int b = 0; b < 2; ++b)
-            if (c[a][b] < c[oa][ob]) { oa = a; ob = b; }
-        const int lf = d * 2 + s;
-        f.face_id[lf] = face_of[e * 6 + lf];
-        f.face_oa[lf] = static_cast<int8_t>(oa);
-        f.face_ob[lf] = static_cast<int8_t>(ob);
-        f.face_swap[lf] = !(c[1 - oa][ob] < c[oa][1 - ob]);
+  std::vector<ElemFrames> frames(E);
+  parallel_for(E, kGrain, [&](int64_t b0, int64_t b1) {
+    for (int64_t e = b0; e < b1; ++e) {
+      ElemFrames& f = frames[e];
+      const int64_t* v = ev + 8 * e;
+      for (int d = 0; d < 3; ++d) {
+        const int d1 = d == 0 ? 1 : 0, d2 = d == 2 ? 1 : 2;
+        for (int xy = 0; xy < 4; ++xy) {
+          int lo[3], hi[3];
+          lo[d] = 0; hi[d] = 1;
+          lo[d1] = hi[d1] = xy & 1;
+          lo[d2] = hi[d2] = xy >> 1;
+          f.edge_id[d * 4 + xy] = edge_of[e * 12 + d * 4 + xy];
+          f.edge_rev[d * 4 + xy] = v[corner(lo[0], lo[1], lo[2])] > v[corner(hi[0], hi[1], hi[2])];
+        }
+        for (int s = 0; s < 2; ++s) {
+          int64_t c[2][2];
+          for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 2; ++b) {
+              int c3[3];
+              c3[d] = s; c3[d1] = a; c3[d2] = b;
+              c[a][b] = v[corner(c3[0], c3[1], c3[2])];
+            }
+          int oa = 0, ob = 0;
+          for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 2; ++b)
+              if (c[a][b] < c[oa][ob]) { oa = a; ob = b; }
+          const int lf = d * 2 + s;
+          f.face_id[lf] = face_of[e * 6 + lf];
+          f.face_oa[lf] = static_cast<int8_t>(oa);
+          f.face_ob[lf] = static_cast<int8_t>(ob);
+          f.face_swap[lf] = !(c[1 - oa][ob] < c[oa][1 - ob]);
+        }
       }
     }
-    return f;
-  };
+  });
+  std::vector<int64_t>().swap(edge_of);
+  std::vector<int64_t>().swap(face_of);
 
   // ---- classification of the P positions of an element (the same for every element)
   struct PosInfo {
@@ -180,71 +258,16 @@ sem_status build_topology(int N, int64_t nv, int64_t E, const int64_t* ev, const
         if (pi.cls != 0) bpos.push_back(r);
       }
 
-  // ---- numbering, with the copy count of every global node
-  const int64_t Nm1 = N - 1;
-  const int64_t K_e = nv, K_f = K_e + n_edges * Nm1, n_keys = K_f + n_faces * Nm1 * Nm1;
-  std::vector<int32_t> first_id(n_keys, -1);
-  std::vector<int32_t> count;
-  count.reserve(static_cast<size_t>(n));
-  T.glo.assign(n, 0);
-  for (int64_t e = 0; e < E; ++e) {
-    const ElemFrames f = frames_of(e);
-    const int64_t* v = ev + 8 * e;
-    int32_t* glo = T.glo.data() + e * P;
-    for (int r = 0; r < P; ++r) {
-      const PosInfo pi = pos[r];
-      int64_t key;
-      switch (pi.cls) {
-        case 0:  // element interior: always a new node
-          glo[r] = static_cast<int32_t>(count.size());
-          count.push_back(1);
-          continue;
-        case 1:
-          key = v[pi.idx];
-          break;
-        case 2: {
-          const int t = f.edge_rev[pi.idx] ? N - pi.c0 : pi.c0;
-          key = K_e + f.edge_id[pi.idx] * Nm1 + (t - 1);
-          break;
-        }
-        default: {
-          const int lf = pi.idx;
-          const int ps = f.face_oa[lf] == 0 ? pi.c0 : N - pi.c0;
-          const int pt = f.face_ob[lf] == 0 ? pi.c1 : N - pi.c1;
-          const int p0 = f.face_swap[lf] ? pt : ps, p1 = f.face_swap[lf] ? ps : pt;
-          key = K_f + f.face_id[lf] * Nm1 * Nm1 + (p0 - 1) * Nm1 + (p1 - 1);
-          break;
-        }
-      }
-      int32_t& g = first_id[key];
-      if (g < 0) {
-        g = static_cast<int32_t>(count.size());
-        count.push_back(0);
-      }
-      ++count[g];
-      glo[r] = g;
-    }
-  }
-  std::vector<int32_t>().swap(first_id);
-  const int64_t n_glob = static_cast<int64_t>(count.size());
-
-  // ---- multiplicity (element-interior copies have multiplicity 1)
-  T.mult.assign(n, 1);
-  for (int64_t e = 0; e < E; ++e)
-    for (const int32_t r : bpos) {
-      const int32_t c = count[T.glo[e * P + r]];
-      if (c > 255) return fail(SEM_ERR_MESH, "a global node has more than 255 local copies");
-      T.mult[e * P + r] = static_cast<uint8_t>(c);
-    }
-
-  // ---- Dirichlet mask: points on the closure of a boundary face (owned by one element)
-  std::vector<uint8_t> mglob(n_glob, 0);
+  // ---- Dirichlet entities: boundary faces (owned by one element; with vertex flags, only
+  // those whose four vertices are flagged) and the edges and vertices of their closure
+  std::vector<uint8_t> fdir(n_faces, 0), edir(n_edges, 0), vdir(nv, 0);
   for (int64_t e = 0; e < E; ++e) {
     const int64_t* v = ev + 8 * e;
+    const ElemFrames& f = frames[e];
     for (int d = 0; d < 3; ++d)
       for (int s = 0; s < 2; ++s) {
         const int lf = d * 2 + s;
-        if (face_count[face_of[e * 6 + lf]] != 1) continue;
+        if (face_count[f.face_id[lf]] != 1) continue;
         if (dflags) {
           const int d1 = d == 0 ? 1 : 0, d2 = d == 2 ? 1 : 2;
           bool all = true;
@@ -255,38 +278,155 @@ sem_status build_topology(int N, int64_t nv, int64_t E, const int64_t* ev, const
           }
           if (!all) continue;
         }
+        fdir[f.face_id[lf]] = 1;
         for (const int32_t r : bpos) {
           const int q[3] = {r % Np, (r / Np) % Np, r / (Np * Np)};
-          if (q[d] == s * N) mglob[T.glo[e * P + r]] = 1;
+          if (q[d] != s * N) continue;
+          if (pos[r].cls == 1) vdir[v[pos[r].idx]] = 1;
+          if (pos[r].cls == 2) edir[f.edge_id[pos[r].idx]] = 1;
         }
       }
   }
-  T.mask.assign(n, 0);  // element-interior points are never on a boundary face
-  for (int64_t e = 0; e < E; ++e)
-    for (const int32_t r : bpos) T.mask[e * P + r] = mglob[T.glo[e * P + r]];
 
-  // ---- gather-scatter segments: global nodes with copies on element boundaries, ascending
-  // id; a boundary node's copies all lie on element boundaries, so its copy count is its size
-  std::vector<int32_t> seg_of(n_glob, -1);
-  std::vector<uint8_t> is_bdry(n_glob, 0);
-  for (int64_t e = 0; e < E; ++e)
-    for (const int32_t r : bpos) is_bdry[T.glo[e * P + r]] = 1;
-  T.seg_off.clear();
-  T.seg_off.push_back(0);
-  T.seg_mask.clear();
-  for (int64_t g = 0; g < n_glob; ++g)
-    if (is_bdry[g]) {
-      seg_of[g] = static_cast<int32_t>(T.seg_off.size() - 1);
-      T.seg_off.push_back(T.seg_off.back() + count[g]);
-      T.seg_mask.push_back(mglob[g]);
+  // ---- the entity of a boundary position of element e
+  const int64_t Nm1 = N - 1;
+  const int64_t K_e = nv, K_f = K_e + n_edges * Nm1, n_keys = K_f + n_faces * Nm1 * Nm1;
+  auto entity = [&](int64_t e, const ElemFrames& f, const PosInfo& pi) -> PosEntity {
+    const int64_t* v = ev + 8 * e;
+    if (pi.cls == 1) {
+      const int64_t x = v[pi.idx];
+      return {x, vfirst[x], vcount[x], vdir[x], vrank[8 * e + pi.idx]};
     }
-  std::vector<int32_t> cursor(T.seg_off.begin(), T.seg_off.end() - 1);
-  T.seg_idx.assign(T.seg_off.back(), 0);
-  for (int64_t e = 0; e < E; ++e)
-    for (const int32_t r : bpos) {
-      const int64_t loc = e * P + r;
-      T.seg_idx[cursor[seg_of[T.glo[loc]]]++] = static_cast<int32_t>(loc);
+    if (pi.cls == 2) {
+      const int64_t id = f.edge_id[pi.idx];
+      const int t = f.edge_rev[pi.idx] ? N - pi.c0 : pi.c0;
+      return {K_e + id * Nm1 + (t - 1), efirst[id], ecount[id], edir[id], erank[12 * e + pi.idx]};
     }
+    const int lf = pi.idx;
+    const int64_t id = f.face_id[lf];
+    const int ps = f.face_oa[lf] == 0 ? pi.c0 : N - pi.c0;
+    const int pt = f.face_ob[lf] == 0 ? pi.c1 : N - pi.c1;
+    const int p0 = f.face_swap[lf] ? pt : ps, p1 = f.face_swap[lf] ? ps : pt;
+    return {K_f + id * Nm1 * Nm1 + (p0 - 1) * Nm1 + (p1 - 1), ffirst[id], face_count[id], fdir[id],
+            frank[6 * e + lf]};
+  };
+
+  // ---- new nodes per element and the first id of each element's new nodes (prefix sum)
+  const int64_t n_int = Nm1 * Nm1 * Nm1;
+  std::vector<int64_t> base(E + 1, 0);
+  parallel_for(E, kGrain, [&](int64_t b0, int64_t b1) {
+    for (int64_t e = b0; e < b1; ++e) {
+      const int64_t* v = ev + 8 * e;
+      const ElemFrames& f = frames[e];
+      int64_t c = n_int;
+      for (int a = 0; a < 8; ++a) c += vfirst[v[a]] == e;
+      for (int le = 0; le < 12; ++le) c += efirst[f.edge_id[le]] == e ? Nm1 : 0;
+      for (int lf = 0; lf < 6; ++lf) c += ffirst[f.face_id[lf]] == e ? Nm1 * Nm1 : 0;
+      base[e + 1] = c;
+    }
+  });
+  for (int64_t e = 0; e < E; ++e) base[e + 1] += base[e];
+  const int64_t n_glob = base[E];
+
+  // ---- ids: new nodes at first sight, then the nodes first seen in earlier elements
+  std::unique_ptr<int32_t[]> first_id(new int32_t[n_keys]);
+  std::unique_ptr<uint8_t[]> gcount(new uint8_t[n_glob]);  // copies of a boundary node, 0 if interior
+  std::unique_ptr<uint8_t[]> gdir(new uint8_t[n_glob]);
+  T.glo.resize(n);  // every element written below
+  T.mult.resize(n);
+  T.mask.resize(n);
+  parallel_for(E, kGrain, [&](int64_t b0, int64_t b1) {
+    for (int64_t e = b0; e < b1; ++e) {
+      const ElemFrames& f = frames[e];
+      int32_t* glo = T.glo.data() + e * P;
+      int64_t id = base[e];
+      for (int r = 0; r < P; ++r) {
+        const PosInfo pi = pos[r];
+        if (pi.cls == 0) {  // element interior: a new node, one copy, never on a boundary face
+          gcount[id] = 0;
+          gdir[id] = 0;
+          T.mult[e * P + r] = 1;
+          T.mask[e * P + r] = 0;
+          glo[r] = static_cast<int32_t>(id++);
+          continue;
+        }
+        const PosEntity pe = entity(e, f, pi);
+        T.mult[e * P + r] = static_cast<uint8_t>(pe.count);
+        T.mask[e * P + r] = pe.dir;
+        if (pe.first == e) {
+          first_id[pe.key] = static_cast<int32_t>(id);
+          gcount[id] = static_cast<uint8_t>(pe.count);
+          gdir[id] = pe.dir;
+          glo[r] = static_cast<int32_t>(id++);
+        }
+      }
+    }
+  });
+  parallel_for(E, kGrain, [&](int64_t b0, int64_t b1) {
+    for (int64_t e = b0; e < b1; ++e) {
+      const ElemFrames& f = frames[e];
+      int32_t* glo = T.glo.data() + e * P;
+      for (const int32_t r : bpos) {
+        const PosEntity pe = entity(e, f, pos[r]);
+        if (pe.first != e) glo[r] = first_id[pe.key];
+      }
+    }
+  });
+  first_id.reset();
+
+  // ---- gather-scatter segments: boundary nodes in ascending id (chunked prefix sums over
+  // the global ids); the copies of a node sit in the ascending list of the elements that hold
+  // its entity, so a copy's slot is its segment's start plus its element's rank in that list
+  HostVec<int32_t> seg_of;
+  seg_of.resize(n_glob);  // every element written below
+  const int64_t gchunk = int64_t(1) << 20, n_gch = (n_glob + gchunk - 1) / gchunk;
+  std::vector<int64_t> ch_seg(n_gch + 1, 0), ch_cp(n_gch + 1, 0);
+  parallel_for(n_gch, 1, [&](int64_t c0, int64_t c1) {
+    for (int64_t c = c0; c < c1; ++c) {
+      int64_t s = 0, cp = 0;
+      for (int64_t g = c * gchunk; g < std::min(n_glob, (c + 1) * gchunk); ++g) {
+        s += gcount[g] > 0;
+        cp += gcount[g];
+      }
+      ch_seg[c + 1] = s;
+      ch_cp[c + 1] = cp;
+    }
+  });
+  for (int64_t c = 0; c < n_gch; ++c) {
+    ch_seg[c + 1] += ch_seg[c];
+    ch_cp[c + 1] += ch_cp[c];
+  }
+  const int64_t S = ch_seg[n_gch];
+  T.seg_off.resize(S + 1);  // every element written below
+  T.seg_mask.resize(S);
+  T.seg_off[S] = static_cast<int32_t>(ch_cp[n_gch]);
+  parallel_for(n_gch, 1, [&](int64_t c0, int64_t c1) {
+    for (int64_t c = c0; c < c1; ++c) {
+      int64_t s = ch_seg[c], cp = ch_cp[c];
+      for (int64_t g = c * gchunk; g < std::min(n_glob, (c + 1) * gchunk); ++g) {
+        if (gcount[g] == 0) {
+          seg_of[g] = -1;
+          continue;
+        }
+        seg_of[g] = static_cast<int32_t>(s);
+        T.seg_off[s] = static_cast<int32_t>(cp);
+        T.seg_mask[s] = gdir[g];
+        ++s;
+        cp += gcount[g];
+      }
+    }
+  });
+  T.seg_idx.resize(T.seg_off[S]);  // every slot written once below
+  parallel_for(E, kGrain, [&](int64_t b0, int64_t b1) {
+    for (int64_t e = b0; e < b1; ++e) {
+      const ElemFrames& f = frames[e];
+      for (const int32_t r : bpos) {
+        const int64_t loc = e * P + r;
+        const PosEntity pe = entity(e, f, pos[r]);
+        T.seg_idx[T.seg_off[seg_of[T.glo[loc]]] + pe.rank] = static_cast<int32_t>(loc);
+      }
+    }
+  });
 
   T.N = N;
   T.Np = Np;

@@ -96,6 +96,18 @@ def test_host_errors(sem):
         with pytest.raises(sem.SemError) as e:
             sem.sem_mesh_numbering(N, m.num_vertices, m.elem_verts)
         assert e.value.status == sem.SEM_ERR_UNSUPPORTED
+    # empty mesh
+    with pytest.raises(sem.SemError) as e:
+        sem.sem_mesh_numbering(3, m.num_vertices, np.empty((0, 8), dtype=np.int64))
+    assert e.value.status == sem.SEM_ERR_ARG
+    # largest size: E (N+1)^3 must stay below 2^31 (checked before any vertex is read)
+    lib = sem.load_library()
+    E_max = (1 << 31) // 12 ** 3
+    ev_big = np.zeros((E_max + 1, 8), dtype=np.int64)
+    glo, msk, ng = np.empty(1, dtype=np.int64), np.empty(1, dtype=np.uint8), sem.C.c_int64()
+    st = lib.sem_mesh_numbering(11, 8, E_max + 1, ev_big.ctypes.data, None, glo.ctypes.data, msk.ctypes.data,
+                                sem.C.byref(ng))
+    assert st == sem.SEM_ERR_ARG
     # three hexahedra on one face: not a manifold mesh
     ev3 = np.concatenate([m.elem_verts, m.elem_verts[:, [0, 1, 2, 3, 4, 5, 6, 7]] + 0], axis=0)
     with pytest.raises(sem.SemError):

@@ -118,3 +118,20 @@ def test_cg_stateful_and_limits(sem, c1):
     x.zero_()
     res = sem.sem_cg_solve(mesh.handle, bad, x, sem.sem_cg_default_opts())
     assert res["status"] == sem.SEM_ERR_BREAKDOWN
+
+
+@pytest.mark.parametrize("mixed", [0, 1], ids=["fp64", "mixed"])
+def test_cg_single_element(sem, mixed):
+    """Degenerate mesh: one element (every boundary face Dirichlet, (N-1)^3 unknowns), so each
+    kernel's grid is a single partial element group."""
+    m = BoxMesh(1, 1, 1)
+    prob = so.SemProblem(7, m.vert_xyz, m.elem_verts)
+    b = prob.rhs()
+    ref = so.pcg(prob, b, rtol=1e-10)
+    mesh = sem.Mesh(7, m.vert_xyz, m.elem_verts, flags=3)
+    res, x = _solve(sem, mesh, prob, sem.sem_cg_default_opts(rtol=1e-10, mixed=mixed, inner_variant=sem.SEM_AX_OTF))
+    mesh.close()
+    assert res["status"] == sem.SEM_OK, res
+    assert _true_rel(prob, b, x) <= 1e-10 * (1 + 1e-3)
+    if not mixed:
+        assert abs(res["iters"] - ref.iterations) <= max(1, 0.02 * ref.iterations), (res["iters"], ref.iterations)

@@ -57,7 +57,8 @@ def _rel(a, b):
 
 CASES = [((4, 4, 4), 7, 0.1, 0), ((5, 3, 1), 7, 0.15, 2), ((3, 2, 2), 1, 0.1, 3), ((3, 3, 2), 2, 0.1, 4),
          ((2, 3, 3), 3, 0.15, 5), ((3, 2, 3), 4, 0.1, 6), ((2, 2, 3), 5, 0.1, 7), ((2, 2, 2), 6, 0.1, 8),
-         ((3, 1, 2), 8, 0.1, 9), ((2, 2, 1), 9, 0.1, 10), ((1, 2, 2), 10, 0.1, 11), ((2, 1, 2), 11, 0.1, 12)]
+         ((3, 1, 2), 8, 0.1, 9), ((2, 2, 1), 9, 0.1, 10), ((1, 2, 2), 10, 0.1, 11), ((2, 1, 2), 11, 0.1, 12),
+         ((1, 1, 1), 7, 0.0, 13)]  # the last: a single element, a grid of one partial element group
 IDS = [f"{d[0]}x{d[1]}x{d[2]}-N{N}" for d, N, _, _ in CASES]
 
 
