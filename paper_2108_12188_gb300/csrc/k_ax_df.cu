@@ -8,7 +8,9 @@
 // swizzled layout of Stage. A line costs, per output, about 60 FP32 operations instead of
 // about 90 for the plain sums: the even and odd combinations are two-sums, each of the H
 // products is error-free, the H terms are added by a pairwise two-sum tree, and the pair
-// outputs A + B and B - A are renormalised.
+// outputs A + B and B - A are two-sums left unnormalised (the low part may exceed half an ulp
+// of the high part; products and sums downstream take such pairs exactly). Each output point
+// is renormalised once before it is rounded to FP64.
 //
 // The six factor arrays of an element are one contiguous block (24 KB at N = 7): a bulk TMA
 // copy brings the next element group's block into shared memory during the rest of the
@@ -81,8 +83,8 @@ __device__ __forceinline__ void eo_apply_df(const DfEo<NP>& M, const df2 (&in)[N
     if constexpr (NP % 2 == 1) df_prod(M.Eh[i][H], M.El[i][H], in[H].h, in[H].l, pa[H], ea[H]);
     const df2 A = df_tree_sum_nr<HA>(pa, ea);
     const df2 B = df_tree_sum_nr<H>(pb, eb);
-    out[i] = df_norm(df_add_nr(A, B));
-    out[N - i] = df_norm(df_add_nr(B, df_neg(A)));
+    out[i] = df_add_nr(A, B);  // unnormalised pairs: exact sums, valid operands downstream
+    out[N - i] = df_add_nr(B, df_neg(A));
   }
   if constexpr (NP % 2 == 1) {
     float pc[H], ec[H];
