@@ -3,6 +3,7 @@
 #include <atomic>
 #include <chrono>
 #include <cmath>
+#include <algorithm>
 #include <cstring>
 #include <cstdio>
 #include <fstream>
@@ -114,9 +115,13 @@ void free_mesh(sem_mesh m) {
   dfree(m->G32, h);
   dfree(m->scale64, h);
   dfree(m->scale32, h);
-  dfree(m->seg_off, h);
-  dfree(m->seg_idx, h);
-  dfree(m->seg_mask, h);
+  for (int c = 0; c < kGsClasses; ++c) {
+    dfree(m->gs_rec[c], h);
+    dfree(m->gs_msk[c], h);
+  }
+  dfree(m->gs_xoff, h);
+  dfree(m->gs_xidx, h);
+  dfree(m->gs_xmsk, h);
   dfree(m->mult, h);
   dfree(m->minv64, h);
   dfree(m->minv32, h);
@@ -191,8 +196,7 @@ sem_status ensure_jacobi(sem_mesh m, cudaStream_t s) {
   if ((st = dmalloc(&m->minv64, m->n, &bytes, s)) == SEM_OK && (st = dmalloc(&m->minv32, m->n, &bytes, s)) == SEM_OK &&
       (st = launch_local_diag(m->N, m->E, m->coef64, d, s)) == SEM_OK &&
       (st = launch_invert(m->n, d, m->minv64, m->minv32, s)) == SEM_OK &&
-      (st = launch_dssum_invert(m->n_seg, m->seg_off, m->seg_idx, m->seg_mask, d, m->minv64, m->minv32, s)) ==
-          SEM_OK) {
+      (st = launch_dssum_invert(m->gs, d, m->minv64, m->minv32, s)) == SEM_OK) {
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) st = cuda_fail(e, "cudaStreamSynchronize (Jacobi set-up)");
   }
@@ -282,9 +286,15 @@ extern "C" sem_status sem_mesh_create(int N, int64_t nv, const double* vert_xyz,
     SEM_STEP(dmalloc(&m->scale64, static_cast<size_t>(E * P), &acc, s));
     SEM_STEP(dmalloc(&m->scale32, static_cast<size_t>(E * P), &acc, s));
   }
-  SEM_STEP(dmalloc(&m->seg_off, T.seg_off.size(), &acc, s));
-  SEM_STEP(dmalloc(&m->seg_idx, T.seg_idx.size(), &acc, s));
-  SEM_STEP(dmalloc(&m->seg_mask, T.seg_mask.size(), &acc, s));
+  GsHost H;
+  build_gs_host(T, H);
+  for (int c = 0; c < kGsClasses; ++c) {
+    SEM_STEP(dmalloc(&m->gs_rec[c], H.rec[c].size(), &acc, s));
+    SEM_STEP(dmalloc(&m->gs_msk[c], H.msk[c].size(), &acc, s));
+  }
+  SEM_STEP(dmalloc(&m->gs_xoff, H.xoff.size(), &acc, s));
+  SEM_STEP(dmalloc(&m->gs_xidx, H.xidx.size(), &acc, s));
+  SEM_STEP(dmalloc(&m->gs_xmsk, H.xmsk.size(), &acc, s));
   SEM_STEP(dmalloc(&m->mult, T.mult.size(), &acc, s));
   SEM_STEP(dmalloc(&m->ctab, 256, &acc, s));
   SEM_STEP(dmalloc(&m->partials, kRedMax, &acc, s));
@@ -292,9 +302,24 @@ extern "C" sem_status sem_mesh_create(int N, int64_t nv, const double* vert_xyz,
   SEM_STEP(dmalloc(&m->dev_err, 1, &acc, s));
   SEM_CSTEP(cudaMemsetAsync(m->dev_err, 0, sizeof(int), s));
   SEM_CSTEP(cudaMemcpyAsync(Xd, X.data(), X.size() * sizeof(double), cudaMemcpyHostToDevice, s));
-  SEM_CSTEP(cudaMemcpyAsync(m->seg_off, T.seg_off.data(), T.seg_off.size() * 4, cudaMemcpyHostToDevice, s));
-  SEM_CSTEP(cudaMemcpyAsync(m->seg_idx, T.seg_idx.data(), T.seg_idx.size() * 4, cudaMemcpyHostToDevice, s));
-  SEM_CSTEP(cudaMemcpyAsync(m->seg_mask, T.seg_mask.data(), T.seg_mask.size(), cudaMemcpyHostToDevice, s));
+  for (int c = 0; c < kGsClasses; ++c) {
+    m->gs.n[c] = static_cast<int64_t>(H.msk[c].size());
+    m->gs.rec[c] = m->gs_rec[c];
+    m->gs.msk[c] = m->gs_msk[c];
+    if (!H.msk[c].empty()) {
+      SEM_CSTEP(cudaMemcpyAsync(m->gs_rec[c], H.rec[c].data(), H.rec[c].size() * 4, cudaMemcpyHostToDevice, s));
+      SEM_CSTEP(cudaMemcpyAsync(m->gs_msk[c], H.msk[c].data(), H.msk[c].size(), cudaMemcpyHostToDevice, s));
+    }
+  }
+  m->gs.nx = static_cast<int64_t>(H.xmsk.size());
+  m->gs.xoff = m->gs_xoff;
+  m->gs.xidx = m->gs_xidx;
+  m->gs.xmsk = m->gs_xmsk;
+  SEM_CSTEP(cudaMemcpyAsync(m->gs_xoff, H.xoff.data(), H.xoff.size() * 4, cudaMemcpyHostToDevice, s));
+  if (!H.xmsk.empty()) {
+    SEM_CSTEP(cudaMemcpyAsync(m->gs_xidx, H.xidx.data(), H.xidx.size() * 4, cudaMemcpyHostToDevice, s));
+    SEM_CSTEP(cudaMemcpyAsync(m->gs_xmsk, H.xmsk.data(), H.xmsk.size(), cudaMemcpyHostToDevice, s));
+  }
   SEM_CSTEP(cudaMemcpyAsync(m->mult, T.mult.data(), T.mult.size(), cudaMemcpyHostToDevice, s));
   SEM_CSTEP(cudaMemcpyAsync(m->ctab, ctab.data(), 256 * sizeof(double), cudaMemcpyHostToDevice, s));
   SEM_CSTEP(cudaMemsetAsync(m->ticket, 0, sizeof(unsigned int), s));
@@ -366,11 +391,57 @@ extern "C" sem_status sem_mesh_get_mask(sem_mesh m, uint8_t* out) {
   return SEM_OK;
 }
 
+// Rebuilt from the device plan: every segment's copies (records without padding, CSR lists)
+// with its flag, segments in ascending order of their first copy (= ascending global id).
 extern "C" sem_status sem_mesh_get_segments(sem_mesh m, int32_t* off, int32_t* idx, uint8_t* smask) {
   SEM_TRY(check_mesh(m));
-  if (off) SEM_CUDA_TRY(cudaMemcpy(off, m->seg_off, (m->n_seg + 1) * 4, cudaMemcpyDeviceToHost));
-  if (idx) SEM_CUDA_TRY(cudaMemcpy(idx, m->seg_idx, m->n_gs * 4, cudaMemcpyDeviceToHost));
-  if (smask) SEM_CUDA_TRY(cudaMemcpy(smask, m->seg_mask, m->n_seg, cudaMemcpyDeviceToHost));
+  static constexpr int kW[kGsClasses] = {1, 2, 4, 8};
+  struct Seg {
+    int32_t first;
+    int cls;
+    int64_t at;
+  };
+  std::vector<int32_t> rec[kGsClasses], xoff(m->gs.nx + 1), xidx;
+  std::vector<uint8_t> msk[kGsClasses], xmsk(m->gs.nx);
+  std::vector<Seg> segs;
+  segs.reserve(static_cast<size_t>(m->n_seg));
+  for (int c = 0; c < kGsClasses; ++c) {
+    rec[c].resize(m->gs.n[c] * kW[c]);
+    msk[c].resize(m->gs.n[c]);
+    if (m->gs.n[c] == 0) continue;
+    SEM_CUDA_TRY(cudaMemcpy(rec[c].data(), m->gs_rec[c], rec[c].size() * 4, cudaMemcpyDeviceToHost));
+    SEM_CUDA_TRY(cudaMemcpy(msk[c].data(), m->gs_msk[c], msk[c].size(), cudaMemcpyDeviceToHost));
+    for (int64_t q = 0; q < m->gs.n[c]; ++q) segs.push_back({rec[c][q * kW[c]], c, q});
+  }
+  SEM_CUDA_TRY(cudaMemcpy(xoff.data(), m->gs_xoff, xoff.size() * 4, cudaMemcpyDeviceToHost));
+  if (m->gs.nx > 0) {
+    xidx.resize(xoff.back());
+    SEM_CUDA_TRY(cudaMemcpy(xidx.data(), m->gs_xidx, xidx.size() * 4, cudaMemcpyDeviceToHost));
+    SEM_CUDA_TRY(cudaMemcpy(xmsk.data(), m->gs_xmsk, xmsk.size(), cudaMemcpyDeviceToHost));
+    for (int64_t q = 0; q < m->gs.nx; ++q) segs.push_back({xidx[xoff[q]], kGsClasses, q});
+  }
+  std::sort(segs.begin(), segs.end(), [](const Seg& a, const Seg& b) { return a.first < b.first; });
+  int64_t o = 0;
+  for (size_t k = 0; k < segs.size(); ++k) {
+    const Seg& g = segs[k];
+    if (off) off[k] = static_cast<int32_t>(o);
+    if (g.cls < kGsClasses) {
+      if (smask) smask[k] = msk[g.cls][g.at];
+      for (int q = 0; q < kW[g.cls]; ++q) {
+        const int32_t v = rec[g.cls][g.at * kW[g.cls] + q];
+        if (v < 0) break;
+        if (idx) idx[o] = v;
+        ++o;
+      }
+    } else {
+      if (smask) smask[k] = xmsk[g.at];
+      for (int32_t q = xoff[g.at]; q < xoff[g.at + 1]; ++q) {
+        if (idx) idx[o] = xidx[q];
+        ++o;
+      }
+    }
+  }
+  if (off) off[segs.size()] = static_cast<int32_t>(o);
   return SEM_OK;
 }
 
@@ -436,7 +507,7 @@ extern "C" sem_status sem_ax(sem_mesh m, sem_ax_variant v, sem_prec prec, const 
   a.u = u;
   a.w = w;
   SEM_TRY(launch_ax_any(m, prec, v, false, a, s));
-  if (assemble) SEM_TRY(launch_dssum(data_prec(prec), m->n_seg, m->seg_off, m->seg_idx, m->seg_mask, w, 1, s));
+  if (assemble) SEM_TRY(launch_dssum(data_prec(prec), m->gs, w, 1, s));
   return SEM_OK;
 }
 
@@ -445,7 +516,7 @@ extern "C" sem_status sem_dssum(sem_mesh m, sem_prec prec, void* u, int apply_ma
   SEM_TRY(check_prec(prec));
   SEM_TRY(check_ptr(u, "u_dev"));
   note_stream(m, static_cast<cudaStream_t>(stream));
-  return launch_dssum(data_prec(prec), m->n_seg, m->seg_off, m->seg_idx, m->seg_mask, u, apply_mask,
+  return launch_dssum(data_prec(prec), m->gs, u, apply_mask,
                       static_cast<cudaStream_t>(stream));
 }
 
@@ -484,7 +555,7 @@ extern "C" sem_status sem_rhs_sine(sem_mesh m, int a, int b, int c, sem_prec pre
   double* tmp = static_cast<double*>(rhs);
   if (prec == SEM_F32) SEM_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&tmp), m->n * sizeof(double), s));
   sem_status st = launch_rhs_local(m->N, m->E, m->coef64, a, b, c, tmp, s);
-  if (st == SEM_OK) st = launch_dssum(SEM_F64, m->n_seg, m->seg_off, m->seg_idx, m->seg_mask, tmp, 1, s);
+  if (st == SEM_OK) st = launch_dssum(SEM_F64, m->gs, tmp, 1, s);
   if (prec == SEM_F32) {
     if (st == SEM_OK) st = launch_cast(m->n, tmp, static_cast<float*>(rhs), s);
     cudaFreeAsync(tmp, s);
@@ -631,7 +702,7 @@ sem_status cg_start(sem_cg c, const void* b, void* x, bool x0_is_zero, cudaStrea
     a.u = x;
     a.w = c->w;
     SEM_TRY(launch_ax_any(m, c->prec, c->variant, false, a, s));
-    SEM_TRY(launch_dssum(data_prec(c->prec), m->n_seg, m->seg_off, m->seg_idx, m->seg_mask, c->w, 1, s));
+    SEM_TRY(launch_dssum(data_prec(c->prec), m->gs, c->w, 1, s));
     ax0 = c->w;
   }
   SEM_TRY(launch_cg_init(data_prec(c->prec), m->n, b, ax0, c->r, c->z, c->p, minv_of(c), m->mult, m->ctab, c->st, c->init_part,
@@ -653,7 +724,7 @@ sem_status cg_enqueue_iteration(sem_cg c, cudaStream_t s) {
   a.partials = c->ax_part;
   a.grid_out = &c->ax_blocks;
   SEM_TRY(launch_ax_any(m, c->prec, c->variant, true, a, s));
-  SEM_TRY(launch_dssum_cg(data_prec(c->prec), m->n_seg, m->seg_off, m->seg_idx, m->seg_mask, c->w, c->p, c->st, c->ax_part,
+  SEM_TRY(launch_dssum_cg(data_prec(c->prec), m->gs, c->w, c->p, c->st, c->ax_part,
                           c->ax_blocks, c->gs_part, s));
   SEM_TRY(launch_cg_update(data_prec(c->prec), m->n, c->x, c->p, c->r, c->w, c->z, minv_of(c), m->mult, m->ctab, c->st,
                            c->upd_part, s));
@@ -781,7 +852,7 @@ sem_status solve_mixed(sem_mesh m, const double* b, double* x, const sem_cg_opts
     if ((st = launch_ax_any(m, o->f64_arith ? SEM_F64X : SEM_F64, static_cast<sem_ax_variant>(o->variant), false, a,
                             s)) != SEM_OK)
       break;
-    if ((st = launch_dssum(SEM_F64, m->n_seg, m->seg_off, m->seg_idx, m->seg_mask, w64, 1, s)) != SEM_OK) break;
+    if ((st = launch_dssum(SEM_F64, m->gs, w64, 1, s)) != SEM_OK) break;
     cudaError_t e = cudaMemcpyAsync(ost, &oinit, sizeof(CgScalars), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) { st = cuda_fail(e, "cudaMemcpyAsync"); break; }
     if ((st = launch_ir_residual(m->n, b, w64, r64, r32, m->mult, m->ctab, ost, opart, s)) != SEM_OK) break;
@@ -893,7 +964,7 @@ extern "C" sem_status sem_cg_iterate_timed(sem_cg c, int k, double* total_ms, do
     st = launch_ax_any(m, c->prec, c->variant, true, a, s);
     cudaEventRecord(ev[3 * q + 1], s);
     if (st == SEM_OK)
-      st = launch_dssum_cg(data_prec(c->prec), m->n_seg, m->seg_off, m->seg_idx, m->seg_mask, c->w, c->p, c->st, c->ax_part,
+      st = launch_dssum_cg(data_prec(c->prec), m->gs, c->w, c->p, c->st, c->ax_part,
                            c->ax_blocks, c->gs_part, s);
     cudaEventRecord(ev[3 * q + 2], s);
     if (st == SEM_OK)

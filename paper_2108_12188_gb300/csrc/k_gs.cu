@@ -1,10 +1,14 @@
 // Gather-scatter QQ^T with the Dirichlet mask (Eq. 5; Section 4.3; Algorithm 1 step 7).
 //
 // Segments are the global nodes that have copies on element boundaries (n_gs copies in
-// all, Eq. 9), in ascending global id; the copies of a segment are listed in ascending
-// local index. One thread owns one segment: it sums the copies left to right, replaces
-// the sum by 0 if the node is Dirichlet, and writes the result to every copy. No atomics,
-// and the floating-point result does not depend on the launch shape.
+// all, Eq. 9); the copies of a segment are added in ascending local index. One thread owns
+// one segment at a time: it reads the segment's copy indices (one vector load from the
+// fixed-width record of its class, see GsPlan), loads the copies, sums them left to right,
+// replaces the sum by 0 if the node is Dirichlet, and writes the result to every copy. No
+// atomics, and the floating-point result does not depend on the launch shape or on the
+// order in which segments are visited.
+#include <type_traits>
+
 #include "k_common.cuh"
 
 namespace sem {
@@ -18,16 +22,77 @@ int seg_grid(int64_t n_seg) {
   return static_cast<int>(b < cap ? (b > 0 ? b : 1) : cap);
 }
 
+// Copy indices of segment s of a class of width W (padding entries are -1).
+template <int W>
+__device__ __forceinline__ void load_rec(const int32_t* __restrict__ rec, int64_t s, int (&ix)[W]) {
+  if constexpr (W == 1) {
+    ix[0] = __ldg(rec + s);
+  } else if constexpr (W == 2) {
+    const int2 v = __ldg(reinterpret_cast<const int2*>(rec) + s);
+    ix[0] = v.x;
+    ix[1] = v.y;
+  } else {
+#pragma unroll
+    for (int q = 0; q < W / 4; ++q) {
+      const int4 v = __ldg(reinterpret_cast<const int4*>(rec) + s * (W / 4) + q);
+      ix[4 * q] = v.x;
+      ix[4 * q + 1] = v.y;
+      ix[4 * q + 2] = v.z;
+      ix[4 * q + 3] = v.w;
+    }
+  }
+}
+
+// Sum of the copies in record order (ascending local index), padding skipped; the loads
+// are issued before the additions.
+template <int W, typename T>
+__device__ __forceinline__ T seg_sum(const T* __restrict__ u, const int (&ix)[W]) {
+  T v[W];
+#pragma unroll
+  for (int q = 0; q < W; ++q) v[q] = (q == 0 || ix[q] >= 0) ? u[ix[q]] : T(0);
+  T s = v[0];
+#pragma unroll
+  for (int q = 1; q < W; ++q)
+    if (ix[q] >= 0) s += v[q];
+  return s;
+}
+
+template <int W, typename T>
+__device__ __forceinline__ void seg_store(T* __restrict__ u, const int (&ix)[W], T s) {
+#pragma unroll
+  for (int q = 0; q < W; ++q)
+    if (q == 0 || ix[q] >= 0) u[ix[q]] = s;
+}
+
+// Visits the segments of fixed-width class c (records of width W): f(ix, masked).
+template <int W, typename F>
+__device__ __forceinline__ void for_class(const GsPlan& g, int c, int64_t t0, int64_t stride, F&& f) {
+  for (int64_t s = t0; s < g.n[c]; s += stride) {
+    int ix[W];
+    load_rec<W>(g.rec[c], s, ix);
+    f(ix, g.msk[c][s] != 0);
+  }
+}
+
 template <typename T>
-__global__ void k_dssum(int64_t n_seg, const int32_t* __restrict__ off, const int32_t* __restrict__ idx,
-                        const uint8_t* __restrict__ smask, T* __restrict__ u, int apply_mask) {
-  for (int64_t g = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; g < n_seg;
-       g += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const int o0 = off[g], o1 = off[g + 1];
-    T s = u[idx[o0]];
-    for (int o = o0 + 1; o < o1; ++o) s += u[idx[o]];
-    if (apply_mask && smask[g]) s = T(0);
-    for (int o = o0; o < o1; ++o) u[idx[o]] = s;
+__global__ void k_dssum(const GsPlan g, T* __restrict__ u, int apply_mask) {
+  const int64_t t0 = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  auto body = [&](const auto& ix, bool masked) {
+    constexpr int W = std::extent<std::remove_reference_t<decltype(ix)>>::value;
+    const T s = (apply_mask && masked) ? T(0) : seg_sum<W>(u, ix);
+    seg_store<W>(u, ix, s);
+  };
+  for_class<2>(g, 1, t0, stride, body);
+  for_class<4>(g, 2, t0, stride, body);
+  for_class<8>(g, 3, t0, stride, body);
+  for_class<1>(g, 0, t0, stride, body);
+  for (int64_t x = t0; x < g.nx; x += stride) {
+    const int o0 = g.xoff[x], o1 = g.xoff[x + 1];
+    T s = u[g.xidx[o0]];
+    for (int o = o0 + 1; o < o1; ++o) s += u[g.xidx[o]];
+    if (apply_mask && g.xmsk[x]) s = T(0);
+    for (int o = o0; o < o1; ++o) u[g.xidx[o]] = s;
   }
 }
 
@@ -36,21 +101,32 @@ __global__ void k_dssum(int64_t n_seg, const int32_t* __restrict__ off, const in
 // segment contributes p * w once. The last block adds the Ax kernel's element-interior
 // partials, forms <p, w, c> and alpha = rho / <p, w, c> (Algorithm 1 step 8).
 template <typename T>
-__global__ void k_dssum_cg(int64_t n_seg, const int32_t* __restrict__ off, const int32_t* __restrict__ idx,
-                           const uint8_t* __restrict__ smask, T* __restrict__ w, const T* __restrict__ p,
-                           CgScalars* __restrict__ st, const double* __restrict__ ax_partials, int ax_blocks,
-                           double* __restrict__ partials) {
+__global__ void k_dssum_cg(const GsPlan g, T* __restrict__ w, const T* __restrict__ p, CgScalars* __restrict__ st,
+                           const double* __restrict__ ax_partials, int ax_blocks, double* __restrict__ partials) {
   __shared__ double sRed[kThreads / 32];
   if (st->done) return;
+  const int64_t t0 = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   DotAcc<T> dot;
-  for (int64_t g = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; g < n_seg;
-       g += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const int o0 = off[g], o1 = off[g + 1];
-    const int first = idx[o0];
+  auto body = [&](const auto& ix, bool masked) {
+    constexpr int W = std::extent<std::remove_reference_t<decltype(ix)>>::value;
+    const T pf = p[ix[0]];
+    T s = seg_sum<W>(w, ix);
+    if (masked) s = T(0);
+    seg_store<W>(w, ix, s);
+    dot.add(pf, s);
+  };
+  for_class<2>(g, 1, t0, stride, body);
+  for_class<4>(g, 2, t0, stride, body);
+  for_class<8>(g, 3, t0, stride, body);
+  for_class<1>(g, 0, t0, stride, body);
+  for (int64_t x = t0; x < g.nx; x += stride) {
+    const int o0 = g.xoff[x], o1 = g.xoff[x + 1];
+    const int first = g.xidx[o0];
     T s = w[first];
-    for (int o = o0 + 1; o < o1; ++o) s += w[idx[o]];
-    if (smask[g]) s = T(0);
-    for (int o = o0; o < o1; ++o) w[idx[o]] = s;
+    for (int o = o0 + 1; o < o1; ++o) s += w[g.xidx[o]];
+    if (g.xmsk[x]) s = T(0);
+    for (int o = o0; o < o1; ++o) w[g.xidx[o]] = s;
     dot.add(p[first], s);
   }
   const double v[1] = {block_sum(dot.value(), sRed)};
@@ -71,55 +147,63 @@ __global__ void k_dssum_cg(int64_t n_seg, const int32_t* __restrict__ off, const
 }
 
 // Jacobi: out = 1 / (sum of the local diagonals of a segment), or 0 if Dirichlet.
-__global__ void k_dssum_invert(int64_t n_seg, const int32_t* __restrict__ off, const int32_t* __restrict__ idx,
-                               const uint8_t* __restrict__ smask, const double* __restrict__ d,
-                               double* __restrict__ m64, float* __restrict__ m32) {
-  for (int64_t g = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; g < n_seg;
-       g += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const int o0 = off[g], o1 = off[g + 1];
-    double s = d[idx[o0]];
-    for (int o = o0 + 1; o < o1; ++o) s += d[idx[o]];
-    const double v = smask[g] ? 0.0 : 1.0 / s;
+__global__ void k_dssum_invert(const GsPlan g, const double* __restrict__ d, double* __restrict__ m64,
+                               float* __restrict__ m32) {
+  const int64_t t0 = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  auto body = [&](const auto& ix, bool masked) {
+    constexpr int W = std::extent<std::remove_reference_t<decltype(ix)>>::value;
+    const double v = masked ? 0.0 : 1.0 / seg_sum<W>(d, ix);
+    if (m64) seg_store<W>(m64, ix, v);
+    if (m32) seg_store<W>(m32, ix, static_cast<float>(v));
+  };
+  for_class<2>(g, 1, t0, stride, body);
+  for_class<4>(g, 2, t0, stride, body);
+  for_class<8>(g, 3, t0, stride, body);
+  for_class<1>(g, 0, t0, stride, body);
+  for (int64_t x = t0; x < g.nx; x += stride) {
+    const int o0 = g.xoff[x], o1 = g.xoff[x + 1];
+    double s = d[g.xidx[o0]];
+    for (int o = o0 + 1; o < o1; ++o) s += d[g.xidx[o]];
+    const double v = g.xmsk[x] ? 0.0 : 1.0 / s;
     for (int o = o0; o < o1; ++o) {
-      if (m64) m64[idx[o]] = v;
-      if (m32) m32[idx[o]] = static_cast<float>(v);
+      if (m64) m64[g.xidx[o]] = v;
+      if (m32) m32[g.xidx[o]] = static_cast<float>(v);
     }
   }
 }
 
 }  // namespace
 
-sem_status launch_dssum(sem_prec prec, int64_t n_seg, const int32_t* off, const int32_t* idx, const uint8_t* smask,
-                        void* u, int apply_mask, cudaStream_t s) {
-  if (n_seg == 0) return SEM_OK;
+sem_status launch_dssum(sem_prec prec, const GsPlan& g, void* u, int apply_mask, cudaStream_t s) {
+  if (g.total() == 0) return SEM_OK;
+  const int grid = seg_grid(g.total());
   if (prec == SEM_F64)
-    k_dssum<double><<<seg_grid(n_seg), kThreads, 0, s>>>(n_seg, off, idx, smask, static_cast<double*>(u), apply_mask);
+    k_dssum<double><<<grid, kThreads, 0, s>>>(g, static_cast<double*>(u), apply_mask);
   else
-    k_dssum<float><<<seg_grid(n_seg), kThreads, 0, s>>>(n_seg, off, idx, smask, static_cast<float*>(u), apply_mask);
+    k_dssum<float><<<grid, kThreads, 0, s>>>(g, static_cast<float*>(u), apply_mask);
   count_launch();
   SEM_CUDA_TRY(cudaGetLastError());
   return SEM_OK;
 }
 
-sem_status launch_dssum_cg(sem_prec prec, int64_t n_seg, const int32_t* off, const int32_t* idx,
-                           const uint8_t* smask, void* w, const void* p, CgScalars* st, const double* ax_partials,
-                           int ax_blocks, double* partials, cudaStream_t s) {
-  const int grid = seg_grid(n_seg);
+sem_status launch_dssum_cg(sem_prec prec, const GsPlan& g, void* w, const void* p, CgScalars* st,
+                           const double* ax_partials, int ax_blocks, double* partials, cudaStream_t s) {
+  const int grid = seg_grid(g.total());
   if (prec == SEM_F64)
-    k_dssum_cg<double><<<grid, kThreads, 0, s>>>(n_seg, off, idx, smask, static_cast<double*>(w),
-                                                 static_cast<const double*>(p), st, ax_partials, ax_blocks, partials);
+    k_dssum_cg<double><<<grid, kThreads, 0, s>>>(g, static_cast<double*>(w), static_cast<const double*>(p), st,
+                                                 ax_partials, ax_blocks, partials);
   else
-    k_dssum_cg<float><<<grid, kThreads, 0, s>>>(n_seg, off, idx, smask, static_cast<float*>(w),
-                                                static_cast<const float*>(p), st, ax_partials, ax_blocks, partials);
+    k_dssum_cg<float><<<grid, kThreads, 0, s>>>(g, static_cast<float*>(w), static_cast<const float*>(p), st,
+                                                ax_partials, ax_blocks, partials);
   count_launch();
   SEM_CUDA_TRY(cudaGetLastError());
   return SEM_OK;
 }
 
-sem_status launch_dssum_invert(int64_t n_seg, const int32_t* off, const int32_t* idx, const uint8_t* smask,
-                               const double* d, double* m64, float* m32, cudaStream_t s) {
-  if (n_seg == 0) return SEM_OK;
-  k_dssum_invert<<<seg_grid(n_seg), kThreads, 0, s>>>(n_seg, off, idx, smask, d, m64, m32);
+sem_status launch_dssum_invert(const GsPlan& g, const double* d, double* m64, float* m32, cudaStream_t s) {
+  if (g.total() == 0) return SEM_OK;
+  k_dssum_invert<<<seg_grid(g.total()), kThreads, 0, s>>>(g, d, m64, m32);
   count_launch();
   SEM_CUDA_TRY(cudaGetLastError());
   return SEM_OK;

@@ -69,6 +69,16 @@ struct Topology {
 sem_status build_topology(int N, int64_t num_vertices, int64_t E, const int64_t* elem_verts,
                           const uint8_t* dirichlet_flags, Topology& out);
 
+// Host arrays of the gather-scatter plan (see GsPlan below): the segments of T grouped by
+// copy count, each class in ascending segment order.
+struct GsHost {
+  HostVec<int32_t> rec[4];  // fixed-width records, widths 1, 2, 4, 8, padded with -1
+  HostVec<uint8_t> msk[4];
+  HostVec<int32_t> xoff, xidx;  // segments with more than 8 copies
+  HostVec<uint8_t> xmsk;
+};
+void build_gs_host(const Topology& T, GsHost& out);
+
 // ---- device-side CG scalars ----
 struct CgScalars {
   double rho, alpha, beta, pw, rz, rr, bb, rtol2;
@@ -87,6 +97,24 @@ inline int64_t factor_stride(int Np, bool fp32) {
 // ---- reduction scratch ----
 constexpr int kRedMax = 8192;  // upper bound of blocks of any reducing launch
 
+// Device gather-scatter plan (k_gs.cu). The segments (global nodes with copies on element
+// boundaries) are grouped by copy count: class c holds the segments with at most kGsWidth[c]
+// copies as fixed-width records of copy indices (ascending local index, padded with -1),
+// in ascending segment order, so one vector load gives all copies of a segment; segments
+// with more copies keep CSR lists. Every class has a Dirichlet flag per segment.
+constexpr int kGsClasses = 4;
+constexpr int kGsWidth[kGsClasses] = {1, 2, 4, 8};
+struct GsPlan {
+  int64_t n[kGsClasses] = {0, 0, 0, 0};
+  const int32_t* rec[kGsClasses] = {nullptr, nullptr, nullptr, nullptr};
+  const uint8_t* msk[kGsClasses] = {nullptr, nullptr, nullptr, nullptr};
+  int64_t nx = 0;
+  const int32_t* xoff = nullptr;  // [nx + 1]
+  const int32_t* xidx = nullptr;
+  const uint8_t* xmsk = nullptr;
+  int64_t total() const { return n[0] + n[1] + n[2] + n[3] + nx; }
+};
+
 }  // namespace sem
 
 // The mesh object behind the opaque handle.
@@ -103,9 +131,12 @@ struct sem_mesh_s {
   float* G32 = nullptr;       // [E][factor_stride] (the [6][P] block, padded to 16 bytes) or null
   double* scale64 = nullptr;  // [n] w_i w_j w_k / det J (SEM_MESH_OTF_SCALE) or null
   float* scale32 = nullptr;
-  int32_t* seg_off = nullptr;
-  int32_t* seg_idx = nullptr;
-  uint8_t* seg_mask = nullptr;
+  int32_t* gs_rec[sem::kGsClasses] = {};  // gather-scatter plan (views in gs)
+  uint8_t* gs_msk[sem::kGsClasses] = {};
+  int32_t* gs_xoff = nullptr;
+  int32_t* gs_xidx = nullptr;
+  uint8_t* gs_xmsk = nullptr;
+  sem::GsPlan gs;
   uint8_t* mult = nullptr;    // [n]
   double* minv64 = nullptr;   // lazily built Jacobi inverse
   float* minv32 = nullptr;
@@ -180,16 +211,13 @@ sem_status launch_invert(int64_t n, const double* d, double* m64, float* m32, cu
 sem_status launch_cast(int64_t n, const double* in, float* out, cudaStream_t s);
 
 // gather-scatter (k_gs.cu)
-sem_status launch_dssum(sem_prec prec, int64_t n_seg, const int32_t* off, const int32_t* idx,
-                        const uint8_t* smask, void* u, int apply_mask, cudaStream_t s);
+sem_status launch_dssum(sem_prec prec, const GsPlan& g, void* u, int apply_mask, cudaStream_t s);
 // CG variant: also the boundary part of <p, w, c>; the last block combines it with
 // the Ax kernel's interior partials and sets alpha (or a breakdown status).
-sem_status launch_dssum_cg(sem_prec prec, int64_t n_seg, const int32_t* off, const int32_t* idx,
-                           const uint8_t* smask, void* w, const void* p, CgScalars* st, const double* ax_partials,
-                           int ax_blocks, double* partials, cudaStream_t s);
+sem_status launch_dssum_cg(sem_prec prec, const GsPlan& g, void* w, const void* p, CgScalars* st,
+                           const double* ax_partials, int ax_blocks, double* partials, cudaStream_t s);
 // Jacobi: assembled diagonal inverted (0 on Dirichlet nodes) on every element-boundary copy.
-sem_status launch_dssum_invert(int64_t n_seg, const int32_t* off, const int32_t* idx, const uint8_t* smask,
-                               const double* d, double* m64, float* m32, cudaStream_t s);
+sem_status launch_dssum_invert(const GsPlan& g, const double* d, double* m64, float* m32, cudaStream_t s);
 
 // CG vector kernels (k_cg.cu)
 sem_status launch_glsc3(sem_prec prec, int64_t n, const void* a, const void* b, const uint8_t* mult,

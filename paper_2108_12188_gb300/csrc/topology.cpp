@@ -436,4 +436,51 @@ sem_status build_topology(int N, int64_t nv, int64_t E, const int64_t* ev, const
   return SEM_OK;
 }
 
+void build_gs_host(const Topology& T, GsHost& H) {
+  static constexpr int kW[4] = {1, 2, 4, 8};
+  const int64_t S = static_cast<int64_t>(T.seg_mask.size());
+  auto cls = [](int c) { return c <= 1 ? 0 : c <= 2 ? 1 : c <= 4 ? 2 : c <= 8 ? 3 : 4; };
+  // per chunk of segments: how many fall in each class (and copies of the CSR class)
+  const int64_t chunk = int64_t(1) << 18, n_ch = (S + chunk - 1) / chunk;
+  std::vector<std::array<int64_t, 6>> cnt(n_ch + 1, std::array<int64_t, 6>{0, 0, 0, 0, 0, 0});
+  parallel_for(n_ch, 1, [&](int64_t c0, int64_t c1) {
+    for (int64_t c = c0; c < c1; ++c) {
+      std::array<int64_t, 6> k{0, 0, 0, 0, 0, 0};
+      for (int64_t s = c * chunk; s < std::min(S, (c + 1) * chunk); ++s) {
+        const int n = T.seg_off[s + 1] - T.seg_off[s];
+        ++k[cls(n)];
+        if (cls(n) == 4) k[5] += n;
+      }
+      cnt[c + 1] = k;
+    }
+  });
+  for (int64_t c = 0; c < n_ch; ++c)
+    for (int q = 0; q < 6; ++q) cnt[c + 1][q] += cnt[c][q];
+  for (int q = 0; q < 4; ++q) {
+    H.rec[q].resize(cnt[n_ch][q] * kW[q]);
+    H.msk[q].resize(cnt[n_ch][q]);
+  }
+  H.xoff.resize(cnt[n_ch][4] + 1);
+  H.xidx.resize(cnt[n_ch][5]);
+  H.xmsk.resize(cnt[n_ch][4]);
+  H.xoff[cnt[n_ch][4]] = static_cast<int32_t>(cnt[n_ch][5]);
+  parallel_for(n_ch, 1, [&](int64_t c0, int64_t c1) {
+    for (int64_t c = c0; c < c1; ++c) {
+      std::array<int64_t, 6> at = cnt[c];
+      for (int64_t s = c * chunk; s < std::min(S, (c + 1) * chunk); ++s) {
+        const int o0 = T.seg_off[s], n = T.seg_off[s + 1] - o0, q = cls(n);
+        if (q < 4) {
+          int32_t* r = H.rec[q].data() + at[q] * kW[q];
+          for (int k = 0; k < kW[q]; ++k) r[k] = k < n ? T.seg_idx[o0 + k] : -1;
+          H.msk[q][at[q]++] = T.seg_mask[s];
+        } else {
+          H.xoff[at[4]] = static_cast<int32_t>(at[5]);
+          for (int k = 0; k < n; ++k) H.xidx[at[5]++] = T.seg_idx[o0 + k];
+          H.xmsk[at[4]++] = T.seg_mask[s];
+        }
+      }
+    }
+  });
+}
+
 }  // namespace sem
