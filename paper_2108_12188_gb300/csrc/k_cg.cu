@@ -105,7 +105,24 @@ __global__ void k_cg_init(int64_t n, const T* __restrict__ b, const T* __restric
   }
 }
 
-// Algorithm 1 steps 9-13 with z = M^-1 r.
+// Vector of 16 bytes of T (two doubles, four floats) and the matching multiplicity bytes.
+template <typename T>
+struct Vec16;
+template <>
+struct Vec16<double> {
+  using type = double2;
+  using mtype = uchar2;
+  static constexpr int V = 2;
+};
+template <>
+struct Vec16<float> {
+  using type = float4;
+  using mtype = uchar4;
+  static constexpr int V = 4;
+};
+
+// Algorithm 1 steps 9-13 with z = M^-1 r. Each thread takes 16 bytes of every vector per
+// step (vector loads and stores); the last n mod (16 / sizeof(T)) points are done singly.
 template <typename T>
 __global__ void k_cg_update(int64_t n, T* __restrict__ x, const T* __restrict__ p, T* __restrict__ r,
                             const T* __restrict__ w, T* __restrict__ z, const T* __restrict__ minv,
@@ -113,7 +130,13 @@ __global__ void k_cg_update(int64_t n, T* __restrict__ x, const T* __restrict__ 
                             double* __restrict__ partials) {
   __shared__ double sRed[kThreads / 32];
   if (st->done) return;
+  using VT = typename Vec16<T>::type;
+  using MT = typename Vec16<T>::mtype;
+  constexpr int V = Vec16<T>::V;
   const T alpha = static_cast<T>(st->alpha);
+  const int64_t t0 = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  const int64_t nv = n / V;
   double v[2];
   if constexpr (sizeof(T) == 8) {
     // x, r, z: three FP64 operations per point. <r, z, c> and <r, r, c>: r and z as float
@@ -123,33 +146,65 @@ __global__ void k_cg_update(int64_t n, T* __restrict__ x, const T* __restrict__ 
     for (int m = threadIdx.x; m < 256; m += blockDim.x) sC[m] = m == 1 ? df2{1.f, 0.f} : df_from_double(ctab[m]);
     __syncthreads();
     df2 rz{0.f, 0.f}, rr{0.f, 0.f};
-    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
-         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-      x[i] += alpha * p[i];
-      const T ri = r[i] - alpha * w[i];
-      const T zi = minv ? minv[i] * ri : ri;
-      r[i] = ri;
-      z[i] = zi;
-      const df2 r2 = df_from_double(ri), z2 = df_from_double(zi), c2 = sC[mult[i]];
+    auto point = [&](T& xi, T pi, T& ri, T wi, T& zi, T mi, unsigned m) {
+      xi += alpha * pi;
+      ri = ri - alpha * wi;
+      zi = minv ? mi * ri : ri;
+      const df2 r2 = df_from_double(ri), z2 = df_from_double(zi), c2 = sC[m];
       float ch, cl;
       df_prod(c2.h, c2.l, r2.h, r2.l, ch, cl);
       df_fma_acc(rz, ch, cl, z2.h, z2.l);
       df_fma_acc(rr, ch, cl, r2.h, r2.l);
+    };
+    for (int64_t q = t0; q < nv; q += stride) {
+      VT xv = reinterpret_cast<const VT*>(x)[q], rv = reinterpret_cast<const VT*>(r)[q], zv;
+      const VT pv = reinterpret_cast<const VT*>(p)[q], wv = reinterpret_cast<const VT*>(w)[q];
+      const VT mv = minv ? reinterpret_cast<const VT*>(minv)[q] : VT{};
+      const MT cv = reinterpret_cast<const MT*>(mult)[q];
+      point(xv.x, pv.x, rv.x, wv.x, zv.x, mv.x, cv.x);
+      point(xv.y, pv.y, rv.y, wv.y, zv.y, mv.y, cv.y);
+      reinterpret_cast<VT*>(x)[q] = xv;
+      reinterpret_cast<VT*>(r)[q] = rv;
+      reinterpret_cast<VT*>(z)[q] = zv;
+    }
+    for (int64_t i = nv * V + t0; i < n; i += stride) {
+      T xi = x[i], ri = r[i], zi;
+      point(xi, p[i], ri, w[i], zi, minv ? minv[i] : T(0), mult[i]);
+      x[i] = xi;
+      r[i] = ri;
+      z[i] = zi;
     }
     v[0] = block_sum(static_cast<double>(rz.h) + static_cast<double>(rz.l), sRed);
     v[1] = block_sum(static_cast<double>(rr.h) + static_cast<double>(rr.l), sRed);
   } else {
     DotAcc<T> rz, rr;
-    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
-         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-      x[i] += alpha * p[i];
-      const T ri = r[i] - alpha * w[i];
-      const T zi = minv ? minv[i] * ri : ri;
-      r[i] = ri;
-      z[i] = zi;
-      const T c = weight_t<T>(mult, ctab, i);
+    auto point = [&](T& xi, T pi, T& ri, T wi, T& zi, T mi, unsigned m) {
+      xi += alpha * pi;
+      ri = ri - alpha * wi;
+      zi = minv ? mi * ri : ri;
+      const T c = m == 1u ? T(1) : static_cast<T>(__ldg(ctab + m));
       rz.add(ri, c * zi);
       rr.add(ri, c * ri);
+    };
+    for (int64_t q = t0; q < nv; q += stride) {
+      VT xv = reinterpret_cast<const VT*>(x)[q], rv = reinterpret_cast<const VT*>(r)[q], zv;
+      const VT pv = reinterpret_cast<const VT*>(p)[q], wv = reinterpret_cast<const VT*>(w)[q];
+      const VT mv = minv ? reinterpret_cast<const VT*>(minv)[q] : VT{};
+      const MT cv = reinterpret_cast<const MT*>(mult)[q];
+      point(xv.x, pv.x, rv.x, wv.x, zv.x, mv.x, cv.x);
+      point(xv.y, pv.y, rv.y, wv.y, zv.y, mv.y, cv.y);
+      point(xv.z, pv.z, rv.z, wv.z, zv.z, mv.z, cv.z);
+      point(xv.w, pv.w, rv.w, wv.w, zv.w, mv.w, cv.w);
+      reinterpret_cast<VT*>(x)[q] = xv;
+      reinterpret_cast<VT*>(r)[q] = rv;
+      reinterpret_cast<VT*>(z)[q] = zv;
+    }
+    for (int64_t i = nv * V + t0; i < n; i += stride) {
+      T xi = x[i], ri = r[i], zi;
+      point(xi, p[i], ri, w[i], zi, minv ? minv[i] : T(0), mult[i]);
+      x[i] = xi;
+      r[i] = ri;
+      z[i] = zi;
     }
     v[0] = block_sum(rz.value(), sRed);
     v[1] = block_sum(rr.value(), sRed);
