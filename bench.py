@@ -241,6 +241,19 @@ def oracle_cg_sample(nel: int = 12, budget_s: float = 10.0) -> dict:
                       f"{iters} oracle Jacobi-PCG iterations"}
 
 
+def oracle_c1_solve() -> dict:
+    """The oracle's Jacobi-PCG solve of the small configuration (4^3 hexahedra, jitter 0.1h,
+    seed 0, N = 7, sine right-hand side, rtol 1e-10), timed whole (set-up excluded)."""
+    from oracle import sem_oracle as so
+    from synthetic import BoxMesh
+    m = BoxMesh(4, 4, 4, jitter=0.1, seed=0)
+    prob = so.SemProblem(NORD, m.vert_xyz, m.elem_verts)
+    b = prob.rhs()
+    t0 = time.perf_counter()
+    ref = so.pcg(prob, b, rtol=1e-10)
+    return {"seconds": time.perf_counter() - t0, "iterations": ref.iterations}
+
+
 def _oracle_procs(count: int, budget_s: float) -> list:
     """Runs oracle_cg_sample in `count` fresh single-threaded processes at the same time (no
     CUDA state inherited); returns their results."""
@@ -260,14 +273,20 @@ def _oracle_procs(count: int, budget_s: float) -> list:
 
 def run_cpu_baseline(budget_s: float = 10.0) -> dict:
     """The oracle on the host cores: one process alone, then one process per core at once
-    (the oracle is single-threaded; each process times its own sample)."""
+    (the oracle is single-threaded; each process times its own sample); and the oracle's
+    whole solve of the small configuration, single-threaded."""
     single = _oracle_procs(1, budget_s)[0]
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = "import json, bench; print('RESULT ' + json.dumps(bench.oracle_c1_solve()))"
+    pr = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
+    c1 = [json.loads(ln[7:]) for ln in pr.stdout.splitlines() if ln.startswith("RESULT ")]
     cores = max(1, min(os.cpu_count() or 1, 72))
     many = _oracle_procs(cores, budget_s) if cores > 1 else [single]
     total = sum(r["gdof_s"] for r in many)
     return {"value": total, "unit": "GDOF/s", "cores": cores, "kind": "oracle",
             "sample": f"{single['sample']}; one such sample per core, {cores} single-threaded processes at once",
-            "single_core_value": single["gdof_s"], "s_per_iter_single_core": single["s_per_iter"]}
+            "single_core_value": single["gdof_s"], "s_per_iter_single_core": single["s_per_iter"],
+            "config1_solve": c1[0] if c1 else None}
 
 
 # ---------------------------------------------------------------------------
