@@ -417,7 +417,8 @@ def run_gpu(args):
 
     m = BoxMesh(NEL, NEL, NEL, jitter=JITTER, seed=SEED)
     mesh = sem.Mesh(NORD, m.vert_xyz, m.elem_verts,
-                    flags=sem.SEM_MESH_F64_STORED | sem.SEM_MESH_F32_STORED | sem.SEM_MESH_OTF_SCALE)
+                    flags=sem.SEM_MESH_F64_STORED | sem.SEM_MESH_F32_STORED | sem.SEM_MESH_OTF_SCALE
+                    | sem.SEM_MESH_F64X_STORED)
     n = mesh.n
     info = mesh.info
     u_glob = torch.tensor(global_field(info["n_glob"], SEED, start=m.draws_used), dtype=torch.float64, device="cuda")
@@ -618,7 +619,7 @@ def run_solve(args):
     nel = args.nel
     t0 = time.perf_counter()
     m = BoxMesh(nel, nel, nel, jitter=JITTER, seed=2)
-    mesh = sem.Mesh(NORD, m.vert_xyz, m.elem_verts, flags=sem.SEM_MESH_F64_STORED)
+    mesh = sem.Mesh(NORD, m.vert_xyz, m.elem_verts, flags=sem.SEM_MESH_F64_STORED | sem.SEM_MESH_F64X_STORED)
     setup_s = time.perf_counter() - t0
     n = mesh.n
     b = torch.empty(n, dtype=torch.float64, device="cuda")

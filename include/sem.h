@@ -57,7 +57,8 @@ typedef enum {
  * SEM_F64X: FP64 data (double* vectors, FP64 stored factors); the local operator runs in
  * double-float arithmetic (pairs of floats with error-free products and sums, about 47
  * significant bits) on the FP32 pipes, which GB300 issues 61 times faster than FP64. Only
- * sem_ax with SEM_AX_STORED (and the CG options' f64_arith) use it; every other call treats
+ * sem_ax with SEM_AX_STORED (and the CG options' f64_arith) use it, with the float-pair factors of
+ * SEM_MESH_F64X_STORED if the mesh has them, else the FP64 ones; every other call treats
  * SEM_F64X like SEM_F64. Values below 2^-126 in magnitude are flushed to zero inside it. */
 typedef enum { SEM_F64 = 0, SEM_F32 = 1, SEM_F64X = 2 } sem_prec;
 
@@ -78,6 +79,8 @@ typedef enum { SEM_AX_STORED = 0, SEM_AX_OTF = 1, SEM_AX_AUTO = 2, SEM_AX_OTF_SC
 #define SEM_MESH_F64_STORED 1u /* G in FP64: 48 bytes per local point */
 #define SEM_MESH_F32_STORED 2u /* G in FP32: 24 bytes per local point */
 #define SEM_MESH_OTF_SCALE 4u  /* w_i w_j w_k / det J per point, FP64 and FP32: 12 bytes per local point */
+#define SEM_MESH_F64X_STORED 8u /* G as float pairs (high, low: 48 significant bits) for SEM_F64X: 48 bytes
+                                 * per local point; without it SEM_F64X splits the FP64 factors itself */
 
 typedef struct sem_mesh_s* sem_mesh;
 typedef struct sem_cg_s* sem_cg;

@@ -113,6 +113,7 @@ void free_mesh(sem_mesh m) {
   dfree(m->coef32, h);
   dfree(m->G64, h);
   dfree(m->G32, h);
+  dfree(m->Gx, h);
   dfree(m->scale64, h);
   dfree(m->scale32, h);
   for (int c = 0; c < kGsClasses; ++c) {
@@ -149,7 +150,21 @@ inline int vslot(sem_ax_variant v) { return v == SEM_AX_OTF_SCALE ? 2 : static_c
 std::mutex g_tune_mu;
 TuneSlot g_tune[3][SEM_MAX_N + 1];
 
-bool has_factors(sem_mesh m, sem_prec prec) { return prec == SEM_F32 ? m->G32 != nullptr : m->G64 != nullptr; }
+// Stored factors the local operator of precision `prec` reads: FP32 for SEM_F32; for SEM_F64X the
+// float pairs if the mesh has them, else the FP64 factors (split in the kernel); FP64 otherwise.
+const void* stored_factors(sem_mesh m, sem_prec prec, bool* pairs) {
+  *pairs = false;
+  if (prec == SEM_F32) return m->G32;
+  if (prec == SEM_F64X && m->Gx) {
+    *pairs = true;
+    return m->Gx;
+  }
+  return m->G64;
+}
+bool has_factors(sem_mesh m, sem_prec prec) {
+  bool pairs;
+  return stored_factors(m, prec, &pairs) != nullptr;
+}
 bool has_scales(sem_mesh m) { return m->scale64 != nullptr; }
 
 // Resolves SEM_AX_AUTO and picks the tuned block shape.
@@ -175,7 +190,7 @@ sem_status launch_ax_any(sem_mesh m, sem_prec prec, sem_ax_variant v, bool cg, A
   a.err = m->dev_err;
   const bool fp64_data = prec != SEM_F32;
   a.coef = fp64_data ? static_cast<const void*>(m->coef64) : static_cast<const void*>(m->coef32);
-  a.G = fp64_data ? static_cast<const void*>(m->G64) : static_cast<const void*>(m->G32);
+  a.G = stored_factors(m, prec, &a.g_pairs);
   a.scale = fp64_data ? static_cast<const void*>(m->scale64) : static_cast<const void*>(m->scale32);
   if (v == SEM_AX_STORED && !a.G)
     return fail(SEM_ERR_ARG, "stored factors of this precision were not requested at mesh creation");
@@ -225,7 +240,7 @@ extern "C" sem_status sem_mesh_create(int N, int64_t nv, const double* vert_xyz,
   if (!out) return fail(SEM_ERR_ARG, "out is null");
   *out = nullptr;
   if (!vert_xyz || !elem_verts) return fail(SEM_ERR_ARG, "vert_xyz and elem_verts must be given");
-  if (flags & ~(SEM_MESH_F64_STORED | SEM_MESH_F32_STORED | SEM_MESH_OTF_SCALE))
+  if (flags & ~(SEM_MESH_F64_STORED | SEM_MESH_F32_STORED | SEM_MESH_OTF_SCALE | SEM_MESH_F64X_STORED))
     return fail(SEM_ERR_ARG, "unknown mesh flags");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   Topology T;
@@ -280,6 +295,7 @@ extern "C" sem_status sem_mesh_create(int N, int64_t nv, const double* vert_xyz,
   SEM_STEP(dmalloc(&m->coef64, static_cast<size_t>(E) * 24, &acc, s));
   SEM_STEP(dmalloc(&m->coef32, static_cast<size_t>(E) * 24, &acc, s));
   if (flags & SEM_MESH_F64_STORED) SEM_STEP(dmalloc(&m->G64, static_cast<size_t>(E * 6 * P), &acc, s));
+  if (flags & SEM_MESH_F64X_STORED) SEM_STEP(dmalloc(&m->Gx, static_cast<size_t>(2 * E * 6 * P), &acc, s));
   if (flags & SEM_MESH_F32_STORED)
     SEM_STEP(dmalloc(&m->G32, static_cast<size_t>(E * factor_stride(m->Np, true)), &acc, s));
   if (flags & SEM_MESH_OTF_SCALE) {
@@ -327,7 +343,7 @@ extern "C" sem_status sem_mesh_create(int N, int64_t nv, const double* vert_xyz,
   SEM_STEP(launch_coefficients(E, Xd, m->coef64, m->coef32, s));
   // geometric factors (and the det J > 0 check at every GLL point)
   SEM_STEP(launch_geometry(N, E, m->coef64, m->G64, m->G32, nullptr, nullptr, bad, factor_stride(m->Np, false),
-                           factor_stride(m->Np, true), s, m->scale64, m->scale32));
+                           factor_stride(m->Np, true), s, m->scale64, m->scale32, m->Gx));
   int bad_h = 0;
   SEM_CSTEP(cudaMemcpyAsync(&bad_h, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
   SEM_CSTEP(cudaStreamSynchronize(s));
@@ -623,7 +639,7 @@ void cg_free(sem_cg c) {
 sem_status cg_alloc(sem_mesh m, sem_prec prec, sem_ax_variant v, int precond, double rtol, int max_iter, int use_graph,
                     sem_cg* out) {
   *out = nullptr;
-  if (v == SEM_AX_STORED && !(prec == SEM_F32 ? m->G32 != nullptr : m->G64 != nullptr))
+  if (v == SEM_AX_STORED && !has_factors(m, prec))
     return fail(SEM_ERR_ARG, "stored factors of this precision were not requested at mesh creation");
   if (prec == SEM_F64X && (v == SEM_AX_OTF || v == SEM_AX_OTF_SCALE))
     return fail(SEM_ERR_UNSUPPORTED, "double-float FP64 arithmetic runs the stored-factor variant only");
@@ -1129,7 +1145,7 @@ extern "C" sem_status sem_autotune(sem_mesh m, sem_prec prec, int reps, sem_tune
       a.err = m->dev_err;
       a.shape = shape;
       a.coef = prec == SEM_F32 ? static_cast<const void*>(m->coef32) : static_cast<const void*>(m->coef64);
-      a.G = prec == SEM_F32 ? static_cast<const void*>(m->G32) : static_cast<const void*>(m->G64);
+      a.G = stored_factors(m, prec, &a.g_pairs);
       a.scale = prec == SEM_F32 ? static_cast<const void*>(m->scale32) : static_cast<const void*>(m->scale64);
       auto launch = [&] {
         if (prec == SEM_F64X) return launch_ax_f64x(m->N, v, false, a, s);

@@ -15,7 +15,8 @@
 // The six factor arrays of an element are one contiguous block (24 KB at N = 7): a bulk TMA
 // copy brings the next element group's block into shared memory during the rest of the
 // current group, so the FP32 pipes do not wait on factor loads (bounded mbarrier waits; a
-// timeout sets SEM_ERR_TIMEOUT).
+// timeout sets SEM_ERR_TIMEOUT). The factors are FP64 values, split into float pairs by
+// integer operations, or (SEM_MESH_F64X_STORED) float pairs already, in the same 8 bytes.
 //
 // CG mode (Algorithm 1 steps 5-6): p = z + beta p in FP64 (one FMA per point), stored, and
 // the element-interior part of <p, w> accumulated in double-float.
@@ -118,7 +119,7 @@ __device__ __forceinline__ void prefetch_factors(double* sG, const double* G, in
 //   0 column of u (or p = z + beta p) -> registers and A;  1 i-rows of A -> ur into B, column -> ut;
 //   2 j-lines of A -> us in place;  3 column: G (ur, us, ut);  4 D^T on rows, lines, column;
 //   5 column: w = sum of the three, converted to FP64 and stored.
-template <int NP, bool CG>
+template <int NP, bool CG, bool PAIRS>
 __global__ void __launch_bounds__(NP * NP * ax_epb<NP>())
     k_ax_df(const __grid_constant__ DfTab<NP> tab, int64_t E, const double* __restrict__ u, double* __restrict__ w,
             const double* __restrict__ G, const double* __restrict__ z, double* __restrict__ p,
@@ -220,7 +221,14 @@ __global__ void __launch_bounds__(NP * NP * ax_epb<NP>())
       for (int k = 0; k < NP; ++k) {
         df2 g[6];
 #pragma unroll
-        for (int m = 0; m < 6; ++m) g[m] = df_from_double(gE[m * P + k * NP2 + tid]);
+        for (int m = 0; m < 6; ++m) {
+          if constexpr (PAIRS) {  // factors stored as float pairs: no split needed
+            const float2 v = reinterpret_cast<const float2*>(gE)[m * P + k * NP2 + tid];
+            g[m] = {v.x, v.y};
+          } else {
+            g[m] = df_from_double(gE[m * P + k * NP2 + tid]);
+          }
+        }
         const df2 ur = rR[k], us = rS[k], ut = rT[k];
         float p3[3], e3[3];
         df_prod(g[0].h, g[0].l, ur.h, ur.l, p3[0], e3[0]);
@@ -286,24 +294,24 @@ __global__ void __launch_bounds__(NP * NP * ax_epb<NP>())
   }
 }
 
-template <int NP, bool CG>
+template <int NP, bool CG, bool PAIRS>
 sem_status launch_df_t(int N, const AxLaunch& a, cudaStream_t s) {
   constexpr int EPB = ax_epb<NP>();
   constexpr size_t smem = df_smem_bytes<NP>();
   // resident blocks per SM x SMs, with the dynamic shared-memory limit raised first; once
   static const int max_blocks = [] {
-    cudaFuncSetAttribute(k_ax_df<NP, CG>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    cudaFuncSetAttribute(k_ax_df<NP, CG, PAIRS>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ax_df<NP, CG>, NP * NP * EPB, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ax_df<NP, CG, PAIRS>, NP * NP * EPB, smem);
     return (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
   }();
   const int64_t groups = (a.E + EPB - 1) / EPB;
   int grid = max_blocks < kRedMax ? max_blocks : kRedMax;
   if (groups < grid) grid = static_cast<int>(groups);
   if (a.grid_out) *a.grid_out = grid;
-  k_ax_df<NP, CG><<<grid, NP * NP * EPB, smem, s>>>(make_df_tab<NP>(N), a.E, static_cast<const double*>(a.u),
+  k_ax_df<NP, CG, PAIRS><<<grid, NP * NP * EPB, smem, s>>>(make_df_tab<NP>(N), a.E, static_cast<const double*>(a.u),
                                                      static_cast<double*>(a.w), static_cast<const double*>(a.G),
                                                      static_cast<const double*>(a.z), static_cast<double*>(a.p),
                                                      a.st, a.partials, a.err);
@@ -314,7 +322,8 @@ sem_status launch_df_t(int N, const AxLaunch& a, cudaStream_t s) {
 
 template <int NP>
 sem_status launch_df_np(int N, bool cg, const AxLaunch& a, cudaStream_t s) {
-  return cg ? launch_df_t<NP, true>(N, a, s) : launch_df_t<NP, false>(N, a, s);
+  if (a.g_pairs) return cg ? launch_df_t<NP, true, true>(N, a, s) : launch_df_t<NP, false, true>(N, a, s);
+  return cg ? launch_df_t<NP, true, false>(N, a, s) : launch_df_t<NP, false, false>(N, a, s);
 }
 
 }  // namespace

@@ -100,7 +100,7 @@ __device__ void point_geometry(const double* a, double xi, double eta, double ga
 __global__ void k_geometry(const __grid_constant__ GllAll tab, int Np, int64_t E, const double* __restrict__ coef,
                            double* __restrict__ G64, float* __restrict__ G32, double* __restrict__ B64,
                            float* __restrict__ B32, int* __restrict__ bad, int64_t gs64, int64_t gs32,
-                           double* __restrict__ S64, float* __restrict__ S32) {
+                           double* __restrict__ S64, float* __restrict__ S32, float* __restrict__ GX) {
   const int64_t P = static_cast<int64_t>(Np) * Np * Np;
   const int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (idx >= E * P) return;
@@ -113,6 +113,11 @@ __global__ void k_geometry(const __grid_constant__ GllAll tab, int Np, int64_t E
   for (int m = 0; m < 6; ++m) {
     if (G64) G64[e * gs64 + m * P + r] = G[m];
     if (G32) G32[e * gs32 + m * P + r] = static_cast<float>(G[m]);
+    if (GX) {  // float pair (high, low): high = G rounded to FP32, low = the rest rounded to FP32
+      const float h = static_cast<float>(G[m]);
+      GX[2 * (e * gs64 + m * P + r)] = h;
+      GX[2 * (e * gs64 + m * P + r) + 1] = static_cast<float>(G[m] - static_cast<double>(h));
+    }
   }
   if (B64) B64[idx] = B;
   if (B32) B32[idx] = static_cast<float>(B);
@@ -225,11 +230,12 @@ sem_status launch_coefficients(int64_t E, const double* X, double* coef64, float
 }
 
 sem_status launch_geometry(int N, int64_t E, const double* coef64, double* G64, float* G32, double* B64, float* B32,
-                           int* bad, int64_t gs64, int64_t gs32, cudaStream_t s, double* S64, float* S32) {
+                           int* bad, int64_t gs64, int64_t gs32, cudaStream_t s, double* S64, float* S32,
+                           float* GX) {
   const int Np = N + 1;
   const int64_t n = E * Np * Np * Np;
   k_geometry<<<ceil_div(n, kThreads), kThreads, 0, s>>>(gll_all(N), Np, E, coef64, G64, G32, B64, B32, bad, gs64,
-                                                        gs32, S64, S32);
+                                                        gs32, S64, S32, GX);
   count_launch();
   SEM_CUDA_TRY(cudaGetLastError());
   return SEM_OK;

@@ -129,6 +129,7 @@ struct sem_mesh_s {
   float* coef32 = nullptr;    // [E][24] rounded to FP32
   double* G64 = nullptr;      // [E][6][P] or null
   float* G32 = nullptr;       // [E][factor_stride] (the [6][P] block, padded to 16 bytes) or null
+  float* Gx = nullptr;        // [E][6][P] float pairs (high, low) of G for SEM_F64X, or null
   double* scale64 = nullptr;  // [n] w_i w_j w_k / det J (SEM_MESH_OTF_SCALE) or null
   float* scale32 = nullptr;
   int32_t* gs_rec[sem::kGsClasses] = {};  // gather-scatter plan (views in gs)
@@ -169,6 +170,7 @@ struct AxLaunch {
   const void* u;      // input (plain mode)
   void* w;            // output
   const void* G;      // stored factors or null
+  bool g_pairs;       // SEM_F64X: G holds float pairs (high, low) instead of FP64 values
   const void* coef;   // trilinear coefficients (otf)
   const void* scale;  // per-point w/det J (otf with stored scale)
   // CG mode (p = z + beta p prologue, interior part of <p, w> in the epilogue)
@@ -201,7 +203,7 @@ sem_status launch_coefficients(int64_t E, const double* X, double* coef64, float
 // G64 / G32 (either may be null) are written with element strides gs64 / gs32.
 sem_status launch_geometry(int N, int64_t E, const double* coef64, double* G64, float* G32, double* B64,
                            float* B32, int* bad_flag, int64_t gs64, int64_t gs32, cudaStream_t s,
-                           double* S64 = nullptr, float* S32 = nullptr);
+                           double* S64 = nullptr, float* S32 = nullptr, float* GX = nullptr);
 sem_status launch_coords(int N, int64_t E, const double* coef64, double* xyz, int64_t n, cudaStream_t s);
 sem_status launch_local_diag(int N, int64_t E, const double* coef64, double* d, cudaStream_t s);
 sem_status launch_rhs_local(int N, int64_t E, const double* coef64, int a, int b, int c, double* out,

@@ -88,7 +88,7 @@ void run_request(sem_server srv, Request* r) {
   const double t0 = now_ms();
   if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) st = SEM_ERR_CUDA;
   unsigned flags = 0;
-  if (r->opts.variant == SEM_AX_STORED) flags |= SEM_MESH_F64_STORED;
+  if (r->opts.variant == SEM_AX_STORED) flags |= r->opts.f64_arith ? SEM_MESH_F64X_STORED : SEM_MESH_F64_STORED;
   if (r->opts.mixed && r->opts.inner_variant == SEM_AX_STORED) flags |= SEM_MESH_F32_STORED;
   if (st == SEM_OK)
     st = sem_mesh_create(r->N, static_cast<int64_t>(r->vxyz.size() / 3), r->vxyz.data(),

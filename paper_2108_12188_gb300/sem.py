@@ -19,7 +19,7 @@ SEM_OK, SEM_ERR_ARG, SEM_ERR_MESH, SEM_ERR_OOM, SEM_ERR_CUDA = 0, 1, 2, 3, 4
 SEM_ERR_NOT_CONVERGED, SEM_ERR_BREAKDOWN, SEM_ERR_TIMEOUT, SEM_ERR_BUSY, SEM_ERR_UNSUPPORTED = 5, 6, 7, 8, 9
 SEM_F64, SEM_F32, SEM_F64X = 0, 1, 2
 SEM_AX_STORED, SEM_AX_OTF, SEM_AX_AUTO, SEM_AX_OTF_SCALE = 0, 1, 2, 3
-SEM_MESH_F64_STORED, SEM_MESH_F32_STORED, SEM_MESH_OTF_SCALE = 1, 2, 4
+SEM_MESH_F64_STORED, SEM_MESH_F32_STORED, SEM_MESH_OTF_SCALE, SEM_MESH_F64X_STORED = 1, 2, 4, 8
 SEM_MAX_N = 11
 
 # every symbol include/sem.h declares (checked by the tests)

@@ -29,7 +29,7 @@ def full():
     sem_mod.load_library()
     torch.cuda.set_device(0)
     m = BoxMesh(NEL, NEL, NEL, jitter=JITTER, seed=SEED)
-    mesh = sem_mod.Mesh(N, m.vert_xyz, m.elem_verts, flags=7)
+    mesh = sem_mod.Mesh(N, m.vert_xyz, m.elem_verts, flags=15)  # every stored-factor form
     yield sem_mod, m, mesh
     mesh.close()
 

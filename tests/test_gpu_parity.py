@@ -14,7 +14,7 @@ from synthetic import BoxMesh, global_field, local_field
 
 pytestmark = pytest.mark.gpu
 
-FLAGS_ALL = 7  # SEM_MESH_F64_STORED | SEM_MESH_F32_STORED | SEM_MESH_OTF_SCALE
+FLAGS_ALL = 15  # SEM_MESH_F64_STORED | SEM_MESH_F32_STORED | SEM_MESH_OTF_SCALE | SEM_MESH_F64X_STORED
 
 
 @pytest.fixture(scope="module")
@@ -121,6 +121,20 @@ def test_ax_local(sem, dims, N, jitter, seed, variant, prec, tol):
     sem.sem_ax(mesh.handle, variant, prec, ud, wd, assemble=False)
     err = _rel(_h(wd), want)
     assert err <= tol, err
+
+
+@pytest.mark.parametrize("dims,N,jitter,seed", CASES[:3] + CASES[-1:], ids=IDS[:3] + IDS[-1:])
+def test_ax_f64x_from_fp64_factors(sem, dims, N, jitter, seed):
+    """SEM_F64X on a mesh without float-pair factors: the kernel splits the FP64 factors."""
+    m = BoxMesh(*dims, jitter=jitter, seed=seed)
+    prob = so.SemProblem(N, m.vert_xyz, m.elem_verts)
+    mesh = sem.Mesh(N, m.vert_xyz, m.elem_verts, flags=1)
+    u = local_field(prob.n, seed=seed + 300)
+    ud = _t(u, 0)
+    wd = ud.new_empty(ud.shape)
+    sem.sem_ax(mesh.handle, 0, 2, ud, wd, assemble=False)
+    mesh.close()
+    assert _rel(_h(wd), prob.ax_local(u).ravel()) <= 1e-12
 
 
 @pytest.mark.parametrize("variant,prec,tol", VARIANTS, ids=VIDS)
