@@ -13,9 +13,9 @@
 // is renormalised once before it is rounded to FP64.
 //
 // The six factor arrays of an element are one contiguous block (24 KB at N = 7): a bulk TMA
-// copy brings the next element group's block into shared memory during the rest of the
-// current group, so the FP32 pipes do not wait on factor loads (bounded mbarrier waits; a
-// timeout sets SEM_ERR_TIMEOUT). The factors are FP64 values, split into float pairs by
+// copy brings the next element group's first three arrays into shared memory (and a bulk
+// prefetch the other three into L2) during the rest of the current group, so the FP32 pipes
+// do not wait on factor loads (bounded mbarrier waits; a timeout sets SEM_ERR_TIMEOUT). The factors are FP64 values, split into float pairs by
 // integer operations, or (SEM_MESH_F64X_STORED) float pairs already, in the same 8 bytes.
 //
 // CG mode (Algorithm 1 steps 5-6): p = z + beta p in FP64 (one FMA per point), stored, and
@@ -95,23 +95,33 @@ __device__ __forceinline__ void eo_apply_df(const DfEo<NP>& M, const df2 (&in)[N
   }
 }
 
+// Factor values staged in shared memory per element: the first three arrays (G11, G12, G13)
+// when P is even (their bytes are then a multiple of 16, as bulk copies need), all six
+// otherwise. Unstaged arrays are prefetched into L2 with the copy and read from there. The
+// smaller stage lets more blocks share an SM, which this issue-bound kernel needs.
+template <int NP>
+__host__ __device__ constexpr int df_gst() { return NP % 2 == 0 ? 3 * NP * NP * NP : 6 * NP * NP * NP; }
 template <int NP>
 constexpr size_t df_smem_bytes() {
   constexpr int P = NP * NP * NP, EPB = ax_epb<NP>();
-  return static_cast<size_t>(EPB) * 6 * P * sizeof(double)                // factors of the group (TMA target)
+  return static_cast<size_t>(EPB) * df_gst<NP>() * sizeof(double)                // factors of the group (TMA target)
          + 2 * static_cast<size_t>(EPB) * Stage<NP>::kSize * sizeof(df2)  // staging buffers A, B
          + 16;                                                             // mbarrier
 }
 
-// Copies the factors of the element group starting at element e0 (count elements, each a
-// contiguous [6][P] FP64 block) into sG; one thread announces the bytes and issues the copies.
+// Copies the staged factors of the element group starting at element e0 (count elements, each
+// a contiguous [6][P] block of 8-byte values) into sG and prefetches the rest into L2; one
+// thread announces the bytes and issues the copies.
 template <int NP>
 __device__ __forceinline__ void prefetch_factors(double* sG, const double* G, int64_t e0, int count, uint64_t* bar) {
-  constexpr int P = NP * NP * NP;
-  constexpr unsigned kElemBytes = 6u * P * sizeof(double);
+  constexpr int P = NP * NP * NP, GST = df_gst<NP>();
+  constexpr unsigned kElemBytes = GST * sizeof(double);
   fence_proxy_async();
   mbar_expect_tx(bar, kElemBytes * static_cast<unsigned>(count));
-  for (int q = 0; q < count; ++q) tma_load_1d(sG + q * 6 * P, G + (e0 + q) * 6 * P, kElemBytes, bar);
+  for (int q = 0; q < count; ++q) {
+    tma_load_1d(sG + q * GST, G + (e0 + q) * 6 * P, kElemBytes, bar);
+    if constexpr (GST != 6 * P) l2_prefetch(G + (e0 + q) * 6 * P + GST, (6 * P - GST) * sizeof(double));
+  }
 }
 
 // Phases of a group, as in k_ax (barrier between phases; each thread owns one i-row, one
@@ -120,14 +130,15 @@ __device__ __forceinline__ void prefetch_factors(double* sG, const double* G, in
 //   2 j-lines of A -> us in place;  3 column: G (ur, us, ut);  4 D^T on rows, lines, column;
 //   5 column: w = sum of the three, converted to FP64 and stored.
 template <int NP, bool CG, bool PAIRS>
-__global__ void __launch_bounds__(NP * NP * ax_epb<NP>())
+__global__ void __launch_bounds__(NP * NP * ax_epb<NP>(), (CG && NP == 8) ? 4 : 1)
     k_ax_df(const __grid_constant__ DfTab<NP> tab, int64_t E, const double* __restrict__ u, double* __restrict__ w,
             const double* __restrict__ G, const double* __restrict__ z, double* __restrict__ p,
             CgScalars* __restrict__ st, double* __restrict__ partials, int* __restrict__ err) {
   constexpr int NP2 = NP * NP, P = NP2 * NP, EPB = ax_epb<NP>(), SZ = Stage<NP>::kSize;
   extern __shared__ __align__(128) unsigned char smem[];
+  constexpr int GST = df_gst<NP>();
   double* sG = reinterpret_cast<double*>(smem);
-  df2* sA0 = reinterpret_cast<df2*>(sG + EPB * 6 * P);
+  df2* sA0 = reinterpret_cast<df2*>(sG + EPB * GST);
   df2* sB0 = sA0 + EPB * SZ;
   // byte offset EPB*6*P*8 + 2*EPB*SZ*8: a multiple of 8, as the mbarrier needs
   uint64_t* bar = reinterpret_cast<uint64_t*>(sB0 + EPB * SZ);
@@ -209,7 +220,8 @@ __global__ void __launch_bounds__(NP * NP * ax_epb<NP>())
     }
     // phase 3
     {
-      const double* gE = sG + slot * 6 * P;
+      const double* gE = sG + slot * GST;
+      const double* gH = G + (valid ? e : int64_t(0)) * 6 * P;  // arrays 3..5 from L2 when not staged
       df2 rR[NP], rS[NP];
 #pragma unroll
       for (int k = 0; k < NP; ++k) {
@@ -222,11 +234,12 @@ __global__ void __launch_bounds__(NP * NP * ax_epb<NP>())
         df2 g[6];
 #pragma unroll
         for (int m = 0; m < 6; ++m) {
+          const double* src = (GST != 6 * P && m >= 3) ? gH : gE;
           if constexpr (PAIRS) {  // factors stored as float pairs: no split needed
-            const float2 v = reinterpret_cast<const float2*>(gE)[m * P + k * NP2 + tid];
+            const float2 v = reinterpret_cast<const float2*>(src)[m * P + k * NP2 + tid];
             g[m] = {v.x, v.y};
           } else {
-            g[m] = df_from_double(gE[m * P + k * NP2 + tid]);
+            g[m] = df_from_double(src[m * P + k * NP2 + tid]);
           }
         }
         const df2 ur = rR[k], us = rS[k], ut = rT[k];

@@ -37,6 +37,12 @@ __device__ __forceinline__ void tma_load_1d(void* dst, const void* src, unsigned
       : "memory");
 }
 
+// Bulk prefetch of [src, src + bytes) of global memory into L2 (src 16-byte aligned, bytes a
+// multiple of 16); a hint with no completion to wait for.
+__device__ __forceinline__ void l2_prefetch(const void* src, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
   uint32_t ok;
   asm volatile(
