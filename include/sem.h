@@ -134,7 +134,9 @@ sem_status sem_mesh_get_info(sem_mesh mesh, sem_mesh_info_t* info_host);
  * [n_local], 1 = zeroed) and the gather-scatter segments to host buffers.
  * Segments: global nodes on element boundaries in ascending global id;
  * seg_off [n_seg + 1] int32 offsets into seg_idx [n_gs] int32 local indices
- * (ascending within a segment); seg_mask [n_seg] uint8. Any pointer may be NULL. */
+ * (ascending within a segment); seg_mask [n_seg] uint8. They are rebuilt from the
+ * device's gather-scatter plan (segments grouped by copy count), so they show exactly
+ * what the gather-scatter kernels use. Any pointer may be NULL. */
 sem_status sem_mesh_get_glo_num(sem_mesh mesh, int64_t* glo_num_host);
 sem_status sem_mesh_get_mask(sem_mesh mesh, uint8_t* mask_host);
 sem_status sem_mesh_get_segments(sem_mesh mesh, int32_t* seg_off_host, int32_t* seg_idx_host,
