@@ -1143,7 +1143,7 @@ extern "C" sem_status sem_autotune(sem_mesh m, sem_prec prec, int reps, sem_tune
       a.w = w;
       a.E = m->E;
       a.err = m->dev_err;
-      a.shape = shape;
+      a.shape = shape == 0 ? 2 : shape;  // the tuner times each shape as it is
       a.coef = prec == SEM_F32 ? static_cast<const void*>(m->coef32) : static_cast<const void*>(m->coef64);
       a.G = stored_factors(m, prec, &a.g_pairs);
       a.scale = prec == SEM_F32 ? static_cast<const void*>(m->scale32) : static_cast<const void*>(m->scale64);

@@ -374,11 +374,25 @@ sem_status launch_ax_shape(int N, sem_ax_variant v, bool cg, const AxLaunch& a, 
 
 // Dispatch over the block shape, the variant and the mode for one order and precision
 // (the per-point-scale variant is compiled with the default block shape only).
+inline int device_sm_count() {
+  static const int n = [] {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 1;
+  }();
+  return n;
+}
+
+// A mesh with fewer element groups than SMs takes the shape with fewer elements per block
+// (if there is one), so that more SMs share its FP64 work.
 template <int NP, typename T>
 sem_status launch_ax_np(int N, sem_ax_variant v, bool cg, const AxLaunch& a, cudaStream_t s) {
   if (v == SEM_AX_OTF_SCALE)
     return cg ? launch_ax_t<NP, T, 2, true, ax_epb<NP>()>(N, a, s) : launch_ax_t<NP, T, 2, false, ax_epb<NP>()>(N, a, s);
-  if (a.shape == 1 && ax_epb_alt<NP>() != ax_epb<NP>()) return launch_ax_shape<NP, T, ax_epb_alt<NP>()>(N, v, cg, a, s);
+  const bool few_groups = a.shape == 0 && (a.E + ax_epb<NP>() - 1) / ax_epb<NP>() < device_sm_count();
+  if ((a.shape == 1 && ax_epb_alt<NP>() != ax_epb<NP>()) || (few_groups && ax_epb_alt<NP>() < ax_epb<NP>()))
+    return launch_ax_shape<NP, T, ax_epb_alt<NP>()>(N, v, cg, a, s);
   return launch_ax_shape<NP, T, ax_epb<NP>()>(N, v, cg, a, s);
 }
 

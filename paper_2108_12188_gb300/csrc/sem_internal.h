@@ -180,7 +180,8 @@ struct AxLaunch {
   double* partials;   // [gridDim.x] interior partial dots
   int* grid_out;      // receives gridDim.x used
   int* err;           // device error word (bounded waits that ran out write SEM_ERR_TIMEOUT)
-  int shape;          // block shape choice: 0 default elements per block, 1 the alternative
+  int shape;          // block shape: 0 default elements per block (the alternative if it is smaller and the
+                      // mesh has fewer element groups than SMs), 1 the alternative, 2 the default always
 };
 sem_status launch_ax_f64_lo(int N, sem_ax_variant v, bool cg_mode, const AxLaunch& a, cudaStream_t s);  // N+1 <= 7
 sem_status launch_ax_f64_hi(int N, sem_ax_variant v, bool cg_mode, const AxLaunch& a, cudaStream_t s);  // N+1 >= 8
