@@ -630,6 +630,8 @@ def run_solve(args):
     mj = torch.empty_like(b)
     sem.sem_jacobi(mesh.handle, sem.SEM_F64, mj)  # builds the Jacobi diagonal once (set-up)
     del mj
+    for prec in (sem.SEM_F64, sem.SEM_F32):  # block shapes of this order (set-up); used by every variant
+        sem.sem_autotune(mesh.handle, prec, reps=5)
     runs = {}
     configs = {
         "fp64_cg": sem.sem_cg_default_opts(rtol=1e-10, variant=sem.SEM_AX_STORED, check_every=50),
