@@ -237,346 +237,376 @@ using namespace sem;
 
 extern "C" sem_status sem_mesh_create(int N, int64_t nv, const double* vert_xyz, int64_t E, const int64_t* elem_verts,
                                       const uint8_t* dflags, unsigned flags, void* stream, sem_mesh* out) {
-  if (!out) return fail(SEM_ERR_ARG, "out is null");
-  *out = nullptr;
-  if (!vert_xyz || !elem_verts) return fail(SEM_ERR_ARG, "vert_xyz and elem_verts must be given");
-  if (flags & ~(SEM_MESH_F64_STORED | SEM_MESH_F32_STORED | SEM_MESH_OTF_SCALE | SEM_MESH_F64X_STORED))
-    return fail(SEM_ERR_ARG, "unknown mesh flags");
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  Topology T;
-  SEM_TRY(build_topology(N, nv, E, elem_verts, dflags, T));
-  for (int64_t v = 0; v < nv; ++v)
-    for (int c = 0; c < 3; ++c)
-      if (!std::isfinite(vert_xyz[3 * v + c])) return fail(SEM_ERR_MESH, "non-finite vertex coordinate");
+  return guarded([&]() -> sem_status {
+    if (!out) return fail(SEM_ERR_ARG, "out is null");
+    *out = nullptr;
+    if (!vert_xyz || !elem_verts) return fail(SEM_ERR_ARG, "vert_xyz and elem_verts must be given");
+    if (flags & ~(SEM_MESH_F64_STORED | SEM_MESH_F32_STORED | SEM_MESH_OTF_SCALE | SEM_MESH_F64X_STORED))
+      return fail(SEM_ERR_ARG, "unknown mesh flags");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Topology T;
+    SEM_TRY(build_topology(N, nv, E, elem_verts, dflags, T));
+    for (int64_t v = 0; v < nv; ++v)
+      for (int c = 0; c < 3; ++c)
+        if (!std::isfinite(vert_xyz[3 * v + c])) return fail(SEM_ERR_MESH, "non-finite vertex coordinate");
 
-  auto m = std::make_unique<sem_mesh_s>();
-  SEM_CUDA_TRY(cudaGetDevice(&m->device));
-  m->N = N;
-  m->Np = N + 1;
-  m->flags = flags;
-  m->E = E;
-  m->n = T.n;
-  m->n_glob = T.n_glob;
-  m->n_seg = static_cast<int64_t>(T.seg_mask.size());
-  m->n_gs = static_cast<int64_t>(T.seg_idx.size());
-  const int64_t P = static_cast<int64_t>(m->Np) * m->Np * m->Np;
+    auto m = std::make_unique<sem_mesh_s>();
+    SEM_CUDA_TRY(cudaGetDevice(&m->device));
+    m->N = N;
+    m->Np = N + 1;
+    m->flags = flags;
+    m->E = E;
+    m->n = T.n;
+    m->n_glob = T.n_glob;
+    m->n_seg = static_cast<int64_t>(T.seg_mask.size());
+    m->n_gs = static_cast<int64_t>(T.seg_idx.size());
+    const int64_t P = static_cast<int64_t>(m->Np) * m->Np * m->Np;
 
-  std::vector<double> X(static_cast<size_t>(E) * 24);
-  for (int64_t e = 0; e < E; ++e)
-    for (int v = 0; v < 8; ++v)
-      for (int c = 0; c < 3; ++c) X[e * 24 + v * 3 + c] = vert_xyz[3 * elem_verts[e * 8 + v] + c];
-  std::vector<double> ctab(256, 0.0);
-  for (int k = 1; k < 256; ++k) ctab[k] = 1.0 / k;
+    std::vector<double> X(static_cast<size_t>(E) * 24);
+    for (int64_t e = 0; e < E; ++e)
+      for (int v = 0; v < 8; ++v)
+        for (int c = 0; c < 3; ++c) X[e * 24 + v * 3 + c] = vert_xyz[3 * elem_verts[e * 8 + v] + c];
+    std::vector<double> ctab(256, 0.0);
+    for (int k = 1; k < 256; ++k) ctab[k] = 1.0 / k;
 
-  double* Xd = nullptr;
-  int* bad = nullptr;
-  SEM_CUDA_TRY(cudaStreamCreateWithFlags(&m->home, cudaStreamNonBlocking));
-  m->used.push_back(s);
-  auto cleanup = [&](sem_status st) {
-    dfree(Xd, s);
-    dfree(bad, s);
-    if (st != SEM_OK) free_mesh(m.get());
-    return st;
-  };
-  size_t& acc = m->device_bytes;
-  sem_status st = SEM_OK;
-#define SEM_STEP(expr)               \
-  do {                               \
-    st = (expr);                     \
-    if (st != SEM_OK) return cleanup(st); \
-  } while (0)
-#define SEM_CSTEP(expr)                                  \
-  do {                                                   \
-    cudaError_t _e = (expr);                             \
-    if (_e != cudaSuccess) return cleanup(cuda_fail(_e, #expr)); \
-  } while (0)
-  SEM_STEP(dmalloc(&Xd, X.size(), nullptr, s));
-  SEM_STEP(dmalloc(&bad, 1, nullptr, s));
-  SEM_STEP(dmalloc(&m->coef64, static_cast<size_t>(E) * 24, &acc, s));
-  SEM_STEP(dmalloc(&m->coef32, static_cast<size_t>(E) * 24, &acc, s));
-  if (flags & SEM_MESH_F64_STORED) SEM_STEP(dmalloc(&m->G64, static_cast<size_t>(E * 6 * P), &acc, s));
-  if (flags & SEM_MESH_F64X_STORED) SEM_STEP(dmalloc(&m->Gx, static_cast<size_t>(2 * E * 6 * P), &acc, s));
-  if (flags & SEM_MESH_F32_STORED)
-    SEM_STEP(dmalloc(&m->G32, static_cast<size_t>(E * factor_stride(m->Np, true)), &acc, s));
-  if (flags & SEM_MESH_OTF_SCALE) {
-    SEM_STEP(dmalloc(&m->scale64, static_cast<size_t>(E * P), &acc, s));
-    SEM_STEP(dmalloc(&m->scale32, static_cast<size_t>(E * P), &acc, s));
-  }
-  GsHost H;
-  build_gs_host(T, H);
-  for (int c = 0; c < kGsClasses; ++c) {
-    SEM_STEP(dmalloc(&m->gs_rec[c], H.rec[c].size(), &acc, s));
-    SEM_STEP(dmalloc(&m->gs_msk[c], H.msk[c].size(), &acc, s));
-  }
-  SEM_STEP(dmalloc(&m->gs_xoff, H.xoff.size(), &acc, s));
-  SEM_STEP(dmalloc(&m->gs_xidx, H.xidx.size(), &acc, s));
-  SEM_STEP(dmalloc(&m->gs_xmsk, H.xmsk.size(), &acc, s));
-  SEM_STEP(dmalloc(&m->mult, T.mult.size(), &acc, s));
-  SEM_STEP(dmalloc(&m->ctab, 256, &acc, s));
-  SEM_STEP(dmalloc(&m->partials, kRedMax, &acc, s));
-  SEM_STEP(dmalloc(&m->ticket, 1, &acc, s));
-  SEM_STEP(dmalloc(&m->dev_err, 1, &acc, s));
-  SEM_CSTEP(cudaMemsetAsync(m->dev_err, 0, sizeof(int), s));
-  SEM_CSTEP(cudaMemcpyAsync(Xd, X.data(), X.size() * sizeof(double), cudaMemcpyHostToDevice, s));
-  for (int c = 0; c < kGsClasses; ++c) {
-    m->gs.n[c] = static_cast<int64_t>(H.msk[c].size());
-    m->gs.rec[c] = m->gs_rec[c];
-    m->gs.msk[c] = m->gs_msk[c];
-    if (!H.msk[c].empty()) {
-      SEM_CSTEP(cudaMemcpyAsync(m->gs_rec[c], H.rec[c].data(), H.rec[c].size() * 4, cudaMemcpyHostToDevice, s));
-      SEM_CSTEP(cudaMemcpyAsync(m->gs_msk[c], H.msk[c].data(), H.msk[c].size(), cudaMemcpyHostToDevice, s));
+    double* Xd = nullptr;
+    int* bad = nullptr;
+    SEM_CUDA_TRY(cudaStreamCreateWithFlags(&m->home, cudaStreamNonBlocking));
+    m->used.push_back(s);
+    auto cleanup = [&](sem_status st) {
+      dfree(Xd, s);
+      dfree(bad, s);
+      if (st != SEM_OK) free_mesh(m.get());
+      return st;
+    };
+    size_t& acc = m->device_bytes;
+    sem_status st = SEM_OK;
+  #define SEM_STEP(expr)               \
+    do {                               \
+      st = (expr);                     \
+      if (st != SEM_OK) return cleanup(st); \
+    } while (0)
+  #define SEM_CSTEP(expr)                                  \
+    do {                                                   \
+      cudaError_t _e = (expr);                             \
+      if (_e != cudaSuccess) return cleanup(cuda_fail(_e, #expr)); \
+    } while (0)
+    SEM_STEP(dmalloc(&Xd, X.size(), nullptr, s));
+    SEM_STEP(dmalloc(&bad, 1, nullptr, s));
+    SEM_STEP(dmalloc(&m->coef64, static_cast<size_t>(E) * 24, &acc, s));
+    SEM_STEP(dmalloc(&m->coef32, static_cast<size_t>(E) * 24, &acc, s));
+    if (flags & SEM_MESH_F64_STORED) SEM_STEP(dmalloc(&m->G64, static_cast<size_t>(E * 6 * P), &acc, s));
+    if (flags & SEM_MESH_F64X_STORED) SEM_STEP(dmalloc(&m->Gx, static_cast<size_t>(2 * E * 6 * P), &acc, s));
+    if (flags & SEM_MESH_F32_STORED)
+      SEM_STEP(dmalloc(&m->G32, static_cast<size_t>(E * factor_stride(m->Np, true)), &acc, s));
+    if (flags & SEM_MESH_OTF_SCALE) {
+      SEM_STEP(dmalloc(&m->scale64, static_cast<size_t>(E * P), &acc, s));
+      SEM_STEP(dmalloc(&m->scale32, static_cast<size_t>(E * P), &acc, s));
     }
-  }
-  m->gs.nx = static_cast<int64_t>(H.xmsk.size());
-  m->gs.xoff = m->gs_xoff;
-  m->gs.xidx = m->gs_xidx;
-  m->gs.xmsk = m->gs_xmsk;
-  SEM_CSTEP(cudaMemcpyAsync(m->gs_xoff, H.xoff.data(), H.xoff.size() * 4, cudaMemcpyHostToDevice, s));
-  if (!H.xmsk.empty()) {
-    SEM_CSTEP(cudaMemcpyAsync(m->gs_xidx, H.xidx.data(), H.xidx.size() * 4, cudaMemcpyHostToDevice, s));
-    SEM_CSTEP(cudaMemcpyAsync(m->gs_xmsk, H.xmsk.data(), H.xmsk.size(), cudaMemcpyHostToDevice, s));
-  }
-  SEM_CSTEP(cudaMemcpyAsync(m->mult, T.mult.data(), T.mult.size(), cudaMemcpyHostToDevice, s));
-  SEM_CSTEP(cudaMemcpyAsync(m->ctab, ctab.data(), 256 * sizeof(double), cudaMemcpyHostToDevice, s));
-  SEM_CSTEP(cudaMemsetAsync(m->ticket, 0, sizeof(unsigned int), s));
-  SEM_CSTEP(cudaMemsetAsync(bad, 0, sizeof(int), s));
-  SEM_STEP(launch_coefficients(E, Xd, m->coef64, m->coef32, s));
-  // geometric factors (and the det J > 0 check at every GLL point)
-  SEM_STEP(launch_geometry(N, E, m->coef64, m->G64, m->G32, nullptr, nullptr, bad, factor_stride(m->Np, false),
-                           factor_stride(m->Np, true), s, m->scale64, m->scale32, m->Gx));
-  int bad_h = 0;
-  SEM_CSTEP(cudaMemcpyAsync(&bad_h, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
-  SEM_CSTEP(cudaStreamSynchronize(s));
-  if (bad_h) return cleanup(fail(SEM_ERR_MESH, "det J <= 0 (inverted or degenerate element)"));
-#undef SEM_STEP
-#undef SEM_CSTEP
-  cleanup(SEM_OK);
-  m->glo = std::move(T.glo);
-  m->mask = std::move(T.mask);
-  *out = m.release();
-  return SEM_OK;
+    GsHost H;
+    build_gs_host(T, H);
+    for (int c = 0; c < kGsClasses; ++c) {
+      SEM_STEP(dmalloc(&m->gs_rec[c], H.rec[c].size(), &acc, s));
+      SEM_STEP(dmalloc(&m->gs_msk[c], H.msk[c].size(), &acc, s));
+    }
+    SEM_STEP(dmalloc(&m->gs_xoff, H.xoff.size(), &acc, s));
+    SEM_STEP(dmalloc(&m->gs_xidx, H.xidx.size(), &acc, s));
+    SEM_STEP(dmalloc(&m->gs_xmsk, H.xmsk.size(), &acc, s));
+    SEM_STEP(dmalloc(&m->mult, T.mult.size(), &acc, s));
+    SEM_STEP(dmalloc(&m->ctab, 256, &acc, s));
+    SEM_STEP(dmalloc(&m->partials, kRedMax, &acc, s));
+    SEM_STEP(dmalloc(&m->ticket, 1, &acc, s));
+    SEM_STEP(dmalloc(&m->dev_err, 1, &acc, s));
+    SEM_CSTEP(cudaMemsetAsync(m->dev_err, 0, sizeof(int), s));
+    SEM_CSTEP(cudaMemcpyAsync(Xd, X.data(), X.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    for (int c = 0; c < kGsClasses; ++c) {
+      m->gs.n[c] = static_cast<int64_t>(H.msk[c].size());
+      m->gs.rec[c] = m->gs_rec[c];
+      m->gs.msk[c] = m->gs_msk[c];
+      if (!H.msk[c].empty()) {
+        SEM_CSTEP(cudaMemcpyAsync(m->gs_rec[c], H.rec[c].data(), H.rec[c].size() * 4, cudaMemcpyHostToDevice, s));
+        SEM_CSTEP(cudaMemcpyAsync(m->gs_msk[c], H.msk[c].data(), H.msk[c].size(), cudaMemcpyHostToDevice, s));
+      }
+    }
+    m->gs.nx = static_cast<int64_t>(H.xmsk.size());
+    m->gs.xoff = m->gs_xoff;
+    m->gs.xidx = m->gs_xidx;
+    m->gs.xmsk = m->gs_xmsk;
+    SEM_CSTEP(cudaMemcpyAsync(m->gs_xoff, H.xoff.data(), H.xoff.size() * 4, cudaMemcpyHostToDevice, s));
+    if (!H.xmsk.empty()) {
+      SEM_CSTEP(cudaMemcpyAsync(m->gs_xidx, H.xidx.data(), H.xidx.size() * 4, cudaMemcpyHostToDevice, s));
+      SEM_CSTEP(cudaMemcpyAsync(m->gs_xmsk, H.xmsk.data(), H.xmsk.size(), cudaMemcpyHostToDevice, s));
+    }
+    SEM_CSTEP(cudaMemcpyAsync(m->mult, T.mult.data(), T.mult.size(), cudaMemcpyHostToDevice, s));
+    SEM_CSTEP(cudaMemcpyAsync(m->ctab, ctab.data(), 256 * sizeof(double), cudaMemcpyHostToDevice, s));
+    SEM_CSTEP(cudaMemsetAsync(m->ticket, 0, sizeof(unsigned int), s));
+    SEM_CSTEP(cudaMemsetAsync(bad, 0, sizeof(int), s));
+    SEM_STEP(launch_coefficients(E, Xd, m->coef64, m->coef32, s));
+    // geometric factors (and the det J > 0 check at every GLL point)
+    SEM_STEP(launch_geometry(N, E, m->coef64, m->G64, m->G32, nullptr, nullptr, bad, factor_stride(m->Np, false),
+                             factor_stride(m->Np, true), s, m->scale64, m->scale32, m->Gx));
+    int bad_h = 0;
+    SEM_CSTEP(cudaMemcpyAsync(&bad_h, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+    SEM_CSTEP(cudaStreamSynchronize(s));
+    if (bad_h) return cleanup(fail(SEM_ERR_MESH, "det J <= 0 (inverted or degenerate element)"));
+  #undef SEM_STEP
+  #undef SEM_CSTEP
+    cleanup(SEM_OK);
+    m->glo = std::move(T.glo);
+    m->mask = std::move(T.mask);
+    *out = m.release();
+    return SEM_OK;
+  });
 }
 
 extern "C" sem_status sem_mesh_numbering(int N, int64_t nv, int64_t E, const int64_t* elem_verts,
                                          const uint8_t* dflags, int64_t* glo_out, uint8_t* mask_out,
                                          int64_t* n_glob_out) {
-  Topology T;
-  SEM_TRY(build_topology(N, nv, E, elem_verts, dflags, T));
-  if (glo_out)
-    for (size_t i = 0; i < T.glo.size(); ++i) glo_out[i] = T.glo[i];
-  if (mask_out) std::memcpy(mask_out, T.mask.data(), T.mask.size());
-  if (n_glob_out) *n_glob_out = T.n_glob;
-  return SEM_OK;
+  return guarded([&]() -> sem_status {
+    Topology T;
+    SEM_TRY(build_topology(N, nv, E, elem_verts, dflags, T));
+    if (glo_out)
+      for (size_t i = 0; i < T.glo.size(); ++i) glo_out[i] = T.glo[i];
+    if (mask_out) std::memcpy(mask_out, T.mask.data(), T.mask.size());
+    if (n_glob_out) *n_glob_out = T.n_glob;
+    return SEM_OK;
+  });
 }
 
 extern "C" sem_status sem_mesh_destroy(sem_mesh m) {
-  if (!m) return SEM_OK;
-  int cur = 0;
-  cudaGetDevice(&cur);
-  if (cur != m->device) cudaSetDevice(m->device);
-  free_mesh(m);
-  if (cur != m->device) cudaSetDevice(cur);
-  delete m;
-  return SEM_OK;
+  return guarded([&]() -> sem_status {
+    if (!m) return SEM_OK;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != m->device) cudaSetDevice(m->device);
+    free_mesh(m);
+    if (cur != m->device) cudaSetDevice(cur);
+    delete m;
+    return SEM_OK;
+  });
 }
 
 extern "C" sem_status sem_mesh_get_info(sem_mesh m, sem_mesh_info_t* info) {
-  if (!m || !info) return fail(SEM_ERR_ARG, "null argument");
-  info->N = m->N;
-  info->Np = m->Np;
-  info->E = m->E;
-  info->n_local = m->n;
-  info->n_glob = m->n_glob;
-  info->n_seg = m->n_seg;
-  info->n_gs = m->n_gs;
-  info->flags = m->flags;
-  info->device = m->device;
-  info->device_bytes = m->device_bytes;
-  return SEM_OK;
+  return guarded([&]() -> sem_status {
+    if (!m || !info) return fail(SEM_ERR_ARG, "null argument");
+    info->N = m->N;
+    info->Np = m->Np;
+    info->E = m->E;
+    info->n_local = m->n;
+    info->n_glob = m->n_glob;
+    info->n_seg = m->n_seg;
+    info->n_gs = m->n_gs;
+    info->flags = m->flags;
+    info->device = m->device;
+    info->device_bytes = m->device_bytes;
+    return SEM_OK;
+  });
 }
 
 extern "C" sem_status sem_mesh_get_glo_num(sem_mesh m, int64_t* out) {
-  if (!m || !out) return fail(SEM_ERR_ARG, "null argument");
-  for (size_t i = 0; i < m->glo.size(); ++i) out[i] = m->glo[i];
-  return SEM_OK;
+  return guarded([&]() -> sem_status {
+    if (!m || !out) return fail(SEM_ERR_ARG, "null argument");
+    for (size_t i = 0; i < m->glo.size(); ++i) out[i] = m->glo[i];
+    return SEM_OK;
+  });
 }
 
 extern "C" sem_status sem_mesh_get_mask(sem_mesh m, uint8_t* out) {
-  if (!m || !out) return fail(SEM_ERR_ARG, "null argument");
-  std::memcpy(out, m->mask.data(), m->mask.size());
-  return SEM_OK;
+  return guarded([&]() -> sem_status {
+    if (!m || !out) return fail(SEM_ERR_ARG, "null argument");
+    std::memcpy(out, m->mask.data(), m->mask.size());
+    return SEM_OK;
+  });
 }
 
 // Rebuilt from the device plan: every segment's copies (records without padding, CSR lists)
 // with its flag, segments in ascending order of their first copy (= ascending global id).
 extern "C" sem_status sem_mesh_get_segments(sem_mesh m, int32_t* off, int32_t* idx, uint8_t* smask) {
-  SEM_TRY(check_mesh(m));
-  static constexpr int kW[kGsClasses] = {1, 2, 4, 8};
-  struct Seg {
-    int32_t first;
-    int cls;
-    int64_t at;
-  };
-  std::vector<int32_t> rec[kGsClasses], xoff(m->gs.nx + 1), xidx;
-  std::vector<uint8_t> msk[kGsClasses], xmsk(m->gs.nx);
-  std::vector<Seg> segs;
-  segs.reserve(static_cast<size_t>(m->n_seg));
-  for (int c = 0; c < kGsClasses; ++c) {
-    rec[c].resize(m->gs.n[c] * kW[c]);
-    msk[c].resize(m->gs.n[c]);
-    if (m->gs.n[c] == 0) continue;
-    SEM_CUDA_TRY(cudaMemcpy(rec[c].data(), m->gs_rec[c], rec[c].size() * 4, cudaMemcpyDeviceToHost));
-    SEM_CUDA_TRY(cudaMemcpy(msk[c].data(), m->gs_msk[c], msk[c].size(), cudaMemcpyDeviceToHost));
-    for (int64_t q = 0; q < m->gs.n[c]; ++q) segs.push_back({rec[c][q * kW[c]], c, q});
-  }
-  SEM_CUDA_TRY(cudaMemcpy(xoff.data(), m->gs_xoff, xoff.size() * 4, cudaMemcpyDeviceToHost));
-  if (m->gs.nx > 0) {
-    xidx.resize(xoff.back());
-    SEM_CUDA_TRY(cudaMemcpy(xidx.data(), m->gs_xidx, xidx.size() * 4, cudaMemcpyDeviceToHost));
-    SEM_CUDA_TRY(cudaMemcpy(xmsk.data(), m->gs_xmsk, xmsk.size(), cudaMemcpyDeviceToHost));
-    for (int64_t q = 0; q < m->gs.nx; ++q) segs.push_back({xidx[xoff[q]], kGsClasses, q});
-  }
-  std::sort(segs.begin(), segs.end(), [](const Seg& a, const Seg& b) { return a.first < b.first; });
-  int64_t o = 0;
-  for (size_t k = 0; k < segs.size(); ++k) {
-    const Seg& g = segs[k];
-    if (off) off[k] = static_cast<int32_t>(o);
-    if (g.cls < kGsClasses) {
-      if (smask) smask[k] = msk[g.cls][g.at];
-      for (int q = 0; q < kW[g.cls]; ++q) {
-        const int32_t v = rec[g.cls][g.at * kW[g.cls] + q];
-        if (v < 0) break;
-        if (idx) idx[o] = v;
-        ++o;
-      }
-    } else {
-      if (smask) smask[k] = xmsk[g.at];
-      for (int32_t q = xoff[g.at]; q < xoff[g.at + 1]; ++q) {
-        if (idx) idx[o] = xidx[q];
-        ++o;
+  return guarded([&]() -> sem_status {
+    SEM_TRY(check_mesh(m));
+    static constexpr int kW[kGsClasses] = {1, 2, 4, 8};
+    struct Seg {
+      int32_t first;
+      int cls;
+      int64_t at;
+    };
+    std::vector<int32_t> rec[kGsClasses], xoff(m->gs.nx + 1), xidx;
+    std::vector<uint8_t> msk[kGsClasses], xmsk(m->gs.nx);
+    std::vector<Seg> segs;
+    segs.reserve(static_cast<size_t>(m->n_seg));
+    for (int c = 0; c < kGsClasses; ++c) {
+      rec[c].resize(m->gs.n[c] * kW[c]);
+      msk[c].resize(m->gs.n[c]);
+      if (m->gs.n[c] == 0) continue;
+      SEM_CUDA_TRY(cudaMemcpy(rec[c].data(), m->gs_rec[c], rec[c].size() * 4, cudaMemcpyDeviceToHost));
+      SEM_CUDA_TRY(cudaMemcpy(msk[c].data(), m->gs_msk[c], msk[c].size(), cudaMemcpyDeviceToHost));
+      for (int64_t q = 0; q < m->gs.n[c]; ++q) segs.push_back({rec[c][q * kW[c]], c, q});
+    }
+    SEM_CUDA_TRY(cudaMemcpy(xoff.data(), m->gs_xoff, xoff.size() * 4, cudaMemcpyDeviceToHost));
+    if (m->gs.nx > 0) {
+      xidx.resize(xoff.back());
+      SEM_CUDA_TRY(cudaMemcpy(xidx.data(), m->gs_xidx, xidx.size() * 4, cudaMemcpyDeviceToHost));
+      SEM_CUDA_TRY(cudaMemcpy(xmsk.data(), m->gs_xmsk, xmsk.size(), cudaMemcpyDeviceToHost));
+      for (int64_t q = 0; q < m->gs.nx; ++q) segs.push_back({xidx[xoff[q]], kGsClasses, q});
+    }
+    std::sort(segs.begin(), segs.end(), [](const Seg& a, const Seg& b) { return a.first < b.first; });
+    int64_t o = 0;
+    for (size_t k = 0; k < segs.size(); ++k) {
+      const Seg& g = segs[k];
+      if (off) off[k] = static_cast<int32_t>(o);
+      if (g.cls < kGsClasses) {
+        if (smask) smask[k] = msk[g.cls][g.at];
+        for (int q = 0; q < kW[g.cls]; ++q) {
+          const int32_t v = rec[g.cls][g.at * kW[g.cls] + q];
+          if (v < 0) break;
+          if (idx) idx[o] = v;
+          ++o;
+        }
+      } else {
+        if (smask) smask[k] = xmsk[g.at];
+        for (int32_t q = xoff[g.at]; q < xoff[g.at + 1]; ++q) {
+          if (idx) idx[o] = xidx[q];
+          ++o;
+        }
       }
     }
-  }
-  if (off) off[segs.size()] = static_cast<int32_t>(o);
-  return SEM_OK;
+    if (off) off[segs.size()] = static_cast<int32_t>(o);
+    return SEM_OK;
+  });
 }
 
 extern "C" sem_status sem_mesh_coords(sem_mesh m, double* xyz, void* stream) {
-  SEM_TRY(check_mesh(m));
-  SEM_TRY(check_ptr(xyz, "xyz_dev"));
-  note_stream(m, static_cast<cudaStream_t>(stream));
-  return launch_coords(m->N, m->E, m->coef64, xyz, m->n, static_cast<cudaStream_t>(stream));
+  return guarded([&]() -> sem_status {
+    SEM_TRY(check_mesh(m));
+    SEM_TRY(check_ptr(xyz, "xyz_dev"));
+    note_stream(m, static_cast<cudaStream_t>(stream));
+    return launch_coords(m->N, m->E, m->coef64, xyz, m->n, static_cast<cudaStream_t>(stream));
+  });
 }
 
 extern "C" sem_status sem_mesh_geometry(sem_mesh m, sem_prec prec, void* G, void* B, void* stream) {
-  SEM_TRY(check_mesh(m));
-  SEM_TRY(check_prec(prec));
-  if (G) SEM_TRY(check_ptr(G, "G_dev"));
-  if (B) SEM_TRY(check_ptr(B, "B_dev"));
-  if (!G && !B) return SEM_OK;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  note_stream(m, s);
-  int* bad = nullptr;
-  SEM_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&bad), sizeof(int), s));
-  const bool f64 = prec != SEM_F32;
-  sem_status st = launch_geometry(m->N, m->E, m->coef64, f64 ? static_cast<double*>(G) : nullptr,
-                                  prec == SEM_F32 ? static_cast<float*>(G) : nullptr,
-                                  f64 ? static_cast<double*>(B) : nullptr,
-                                  prec == SEM_F32 ? static_cast<float*>(B) : nullptr, bad, 6LL * m->Np * m->Np * m->Np,
-                                  6LL * m->Np * m->Np * m->Np, s);
-  cudaFreeAsync(bad, s);
-  return st;
+  return guarded([&]() -> sem_status {
+    SEM_TRY(check_mesh(m));
+    SEM_TRY(check_prec(prec));
+    if (G) SEM_TRY(check_ptr(G, "G_dev"));
+    if (B) SEM_TRY(check_ptr(B, "B_dev"));
+    if (!G && !B) return SEM_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    note_stream(m, s);
+    int* bad = nullptr;
+    SEM_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&bad), sizeof(int), s));
+    const bool f64 = prec != SEM_F32;
+    sem_status st = launch_geometry(m->N, m->E, m->coef64, f64 ? static_cast<double*>(G) : nullptr,
+                                    prec == SEM_F32 ? static_cast<float*>(G) : nullptr,
+                                    f64 ? static_cast<double*>(B) : nullptr,
+                                    prec == SEM_F32 ? static_cast<float*>(B) : nullptr, bad, 6LL * m->Np * m->Np * m->Np,
+                                    6LL * m->Np * m->Np * m->Np, s);
+    cudaFreeAsync(bad, s);
+    return st;
+  });
 }
 
 extern "C" sem_status sem_scatter(sem_mesh m, sem_prec prec, const void* ug, void* ul, void* stream) {
-  SEM_TRY(check_mesh(m));
-  SEM_TRY(check_prec(prec));
-  SEM_TRY(check_ptr(ug, "u_glob_dev"));
-  SEM_TRY(check_ptr(ul, "u_local_dev"));
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  note_stream(m, s);
-  const HostVec<int32_t>& g32 = m->glo;
-  int32_t* gd = nullptr;
-  SEM_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&gd), g32.size() * 4, s));
-  sem_status st = SEM_OK;
-  cudaError_t e = cudaMemcpyAsync(gd, g32.data(), g32.size() * 4, cudaMemcpyHostToDevice, s);
-  if (e != cudaSuccess) st = cuda_fail(e, "cudaMemcpyAsync (numbering)");
-  if (st == SEM_OK) st = launch_scatter(data_prec(prec), m->n, gd, ug, ul, s);
-  // the host copy must outlive the transfer
-  e = cudaStreamSynchronize(s);
-  if (st == SEM_OK && e != cudaSuccess) st = cuda_fail(e, "cudaStreamSynchronize");
-  cudaFreeAsync(gd, s);
-  return st;
+  return guarded([&]() -> sem_status {
+    SEM_TRY(check_mesh(m));
+    SEM_TRY(check_prec(prec));
+    SEM_TRY(check_ptr(ug, "u_glob_dev"));
+    SEM_TRY(check_ptr(ul, "u_local_dev"));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    note_stream(m, s);
+    const HostVec<int32_t>& g32 = m->glo;
+    int32_t* gd = nullptr;
+    SEM_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&gd), g32.size() * 4, s));
+    sem_status st = SEM_OK;
+    cudaError_t e = cudaMemcpyAsync(gd, g32.data(), g32.size() * 4, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) st = cuda_fail(e, "cudaMemcpyAsync (numbering)");
+    if (st == SEM_OK) st = launch_scatter(data_prec(prec), m->n, gd, ug, ul, s);
+    // the host copy must outlive the transfer
+    e = cudaStreamSynchronize(s);
+    if (st == SEM_OK && e != cudaSuccess) st = cuda_fail(e, "cudaStreamSynchronize");
+    cudaFreeAsync(gd, s);
+    return st;
+  });
 }
 
 extern "C" sem_status sem_ax(sem_mesh m, sem_ax_variant v, sem_prec prec, const void* u, void* w, int assemble,
                              void* stream) {
-  SEM_TRY(check_mesh(m));
-  SEM_TRY(check_prec(prec));
-  if (v < SEM_AX_STORED || v > SEM_AX_OTF_SCALE) return fail(SEM_ERR_ARG, "unknown Ax variant");
-  SEM_TRY(check_ptr(u, "u_dev"));
-  SEM_TRY(check_ptr(w, "w_dev"));
-  if (u == w) return fail(SEM_ERR_ARG, "u and w must not overlap");
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  note_stream(m, s);
-  AxLaunch a{};
-  a.u = u;
-  a.w = w;
-  SEM_TRY(launch_ax_any(m, prec, v, false, a, s));
-  if (assemble) SEM_TRY(launch_dssum(data_prec(prec), m->gs, w, 1, s));
-  return SEM_OK;
+  return guarded([&]() -> sem_status {
+    SEM_TRY(check_mesh(m));
+    SEM_TRY(check_prec(prec));
+    if (v < SEM_AX_STORED || v > SEM_AX_OTF_SCALE) return fail(SEM_ERR_ARG, "unknown Ax variant");
+    SEM_TRY(check_ptr(u, "u_dev"));
+    SEM_TRY(check_ptr(w, "w_dev"));
+    if (u == w) return fail(SEM_ERR_ARG, "u and w must not overlap");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    note_stream(m, s);
+    AxLaunch a{};
+    a.u = u;
+    a.w = w;
+    SEM_TRY(launch_ax_any(m, prec, v, false, a, s));
+    if (assemble) SEM_TRY(launch_dssum(data_prec(prec), m->gs, w, 1, s));
+    return SEM_OK;
+  });
 }
 
 extern "C" sem_status sem_dssum(sem_mesh m, sem_prec prec, void* u, int apply_mask, void* stream) {
-  SEM_TRY(check_mesh(m));
-  SEM_TRY(check_prec(prec));
-  SEM_TRY(check_ptr(u, "u_dev"));
-  note_stream(m, static_cast<cudaStream_t>(stream));
-  return launch_dssum(data_prec(prec), m->gs, u, apply_mask,
-                      static_cast<cudaStream_t>(stream));
+  return guarded([&]() -> sem_status {
+    SEM_TRY(check_mesh(m));
+    SEM_TRY(check_prec(prec));
+    SEM_TRY(check_ptr(u, "u_dev"));
+    note_stream(m, static_cast<cudaStream_t>(stream));
+    return launch_dssum(data_prec(prec), m->gs, u, apply_mask,
+                        static_cast<cudaStream_t>(stream));
+  });
 }
 
 extern "C" sem_status sem_glsc3(sem_mesh m, sem_prec prec, const void* a, const void* b, double* result,
                                 void* stream) {
-  SEM_TRY(check_mesh(m));
-  SEM_TRY(check_prec(prec));
-  SEM_TRY(check_ptr(a, "a_dev"));
-  SEM_TRY(check_ptr(b, "b_dev"));
-  if (!result) return fail(SEM_ERR_ARG, "result_dev is null");
-  note_stream(m, static_cast<cudaStream_t>(stream));
-  return launch_glsc3(data_prec(prec), m->n, a, b, m->mult, m->ctab, m->partials, m->ticket, result,
-                      static_cast<cudaStream_t>(stream));
+  return guarded([&]() -> sem_status {
+    SEM_TRY(check_mesh(m));
+    SEM_TRY(check_prec(prec));
+    SEM_TRY(check_ptr(a, "a_dev"));
+    SEM_TRY(check_ptr(b, "b_dev"));
+    if (!result) return fail(SEM_ERR_ARG, "result_dev is null");
+    note_stream(m, static_cast<cudaStream_t>(stream));
+    return launch_glsc3(data_prec(prec), m->n, a, b, m->mult, m->ctab, m->partials, m->ticket, result,
+                        static_cast<cudaStream_t>(stream));
+  });
 }
 
 extern "C" sem_status sem_jacobi(sem_mesh m, sem_prec prec, void* minv, void* stream) {
-  SEM_TRY(check_mesh(m));
-  SEM_TRY(check_prec(prec));
-  SEM_TRY(check_ptr(minv, "minv_dev"));
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  note_stream(m, s);
-  SEM_TRY(ensure_jacobi(m, s));
-  const bool f32 = prec == SEM_F32;
-  const size_t bytes = m->n * (f32 ? sizeof(float) : sizeof(double));
-  SEM_CUDA_TRY(cudaMemcpyAsync(minv, f32 ? static_cast<void*>(m->minv32) : static_cast<void*>(m->minv64),
-                               bytes, cudaMemcpyDeviceToDevice, s));
-  return SEM_OK;
+  return guarded([&]() -> sem_status {
+    SEM_TRY(check_mesh(m));
+    SEM_TRY(check_prec(prec));
+    SEM_TRY(check_ptr(minv, "minv_dev"));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    note_stream(m, s);
+    SEM_TRY(ensure_jacobi(m, s));
+    const bool f32 = prec == SEM_F32;
+    const size_t bytes = m->n * (f32 ? sizeof(float) : sizeof(double));
+    SEM_CUDA_TRY(cudaMemcpyAsync(minv, f32 ? static_cast<void*>(m->minv32) : static_cast<void*>(m->minv64),
+                                 bytes, cudaMemcpyDeviceToDevice, s));
+    return SEM_OK;
+  });
 }
 
 extern "C" sem_status sem_rhs_sine(sem_mesh m, int a, int b, int c, sem_prec prec, void* rhs, void* stream) {
-  SEM_TRY(check_mesh(m));
-  SEM_TRY(check_prec(prec));
-  SEM_TRY(check_ptr(rhs, "rhs_dev"));
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  note_stream(m, s);
-  double* tmp = static_cast<double*>(rhs);
-  if (prec == SEM_F32) SEM_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&tmp), m->n * sizeof(double), s));
-  sem_status st = launch_rhs_local(m->N, m->E, m->coef64, a, b, c, tmp, s);
-  if (st == SEM_OK) st = launch_dssum(SEM_F64, m->gs, tmp, 1, s);
-  if (prec == SEM_F32) {
-    if (st == SEM_OK) st = launch_cast(m->n, tmp, static_cast<float*>(rhs), s);
-    cudaFreeAsync(tmp, s);
-  }
-  return st;
+  return guarded([&]() -> sem_status {
+    SEM_TRY(check_mesh(m));
+    SEM_TRY(check_prec(prec));
+    SEM_TRY(check_ptr(rhs, "rhs_dev"));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    note_stream(m, s);
+    double* tmp = static_cast<double*>(rhs);
+    if (prec == SEM_F32) SEM_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&tmp), m->n * sizeof(double), s));
+    sem_status st = launch_rhs_local(m->N, m->E, m->coef64, a, b, c, tmp, s);
+    if (st == SEM_OK) st = launch_dssum(SEM_F64, m->gs, tmp, 1, s);
+    if (prec == SEM_F32) {
+      if (st == SEM_OK) st = launch_cast(m->n, tmp, static_cast<float*>(rhs), s);
+      cudaFreeAsync(tmp, s);
+    }
+    return st;
+  });
 }
 
 // ---------------------------------------------------------------------------
@@ -908,166 +938,182 @@ sem_status solve_mixed(sem_mesh m, const double* b, double* x, const sem_cg_opts
 }  // namespace sem
 
 extern "C" sem_status sem_cg_default_opts(sem_cg_opts* o) {
-  if (!o) return fail(SEM_ERR_ARG, "opts is null");
-  o->rtol = 1e-10;
-  o->max_iter = 100000;
-  o->precond = 1;
-  o->variant = SEM_AX_STORED;
-  o->mixed = 0;
-  o->inner_variant = SEM_AX_OTF;
-  o->inner_rtol = 1e-5;
-  o->max_outer = 50;
-  o->check_every = 50;
-  o->use_graph = 1;
-  o->f64_arith = 0;
-  return SEM_OK;
+  return guarded([&]() -> sem_status {
+    if (!o) return fail(SEM_ERR_ARG, "opts is null");
+    o->rtol = 1e-10;
+    o->max_iter = 100000;
+    o->precond = 1;
+    o->variant = SEM_AX_STORED;
+    o->mixed = 0;
+    o->inner_variant = SEM_AX_OTF;
+    o->inner_rtol = 1e-5;
+    o->max_outer = 50;
+    o->check_every = 50;
+    o->use_graph = 1;
+    o->f64_arith = 0;
+    return SEM_OK;
+  });
 }
 
 extern "C" sem_status sem_cg_create(sem_mesh m, const sem_cg_opts* o, sem_cg* out) {
-  if (!out) return fail(SEM_ERR_ARG, "out is null");
-  *out = nullptr;
-  SEM_TRY(check_mesh(m));
-  SEM_TRY(check_opts(o));
-  if (o->mixed) return fail(SEM_ERR_ARG, "the stateful CG handle runs FP64 CG only (mixed=0)");
-  return cg_alloc(m, o->f64_arith ? SEM_F64X : SEM_F64, static_cast<sem_ax_variant>(o->variant), o->precond, o->rtol,
-                  o->max_iter, o->use_graph, out);
+  return guarded([&]() -> sem_status {
+    if (!out) return fail(SEM_ERR_ARG, "out is null");
+    *out = nullptr;
+    SEM_TRY(check_mesh(m));
+    SEM_TRY(check_opts(o));
+    if (o->mixed) return fail(SEM_ERR_ARG, "the stateful CG handle runs FP64 CG only (mixed=0)");
+    return cg_alloc(m, o->f64_arith ? SEM_F64X : SEM_F64, static_cast<sem_ax_variant>(o->variant), o->precond, o->rtol,
+                    o->max_iter, o->use_graph, out);
+  });
 }
 
 extern "C" sem_status sem_cg_start(sem_cg c, const double* b, double* x, void* stream) {
-  if (!c) return fail(SEM_ERR_ARG, "null CG handle");
-  SEM_TRY(check_mesh(c->m));
-  SEM_TRY(check_ptr(b, "b_dev"));
-  SEM_TRY(check_ptr(x, "x_dev"));
-  return cg_start(c, b, x, false, static_cast<cudaStream_t>(stream));
+  return guarded([&]() -> sem_status {
+    if (!c) return fail(SEM_ERR_ARG, "null CG handle");
+    SEM_TRY(check_mesh(c->m));
+    SEM_TRY(check_ptr(b, "b_dev"));
+    SEM_TRY(check_ptr(x, "x_dev"));
+    return cg_start(c, b, x, false, static_cast<cudaStream_t>(stream));
+  });
 }
 
 extern "C" sem_status sem_cg_iterate(sem_cg c, int k, void* stream) {
-  if (!c) return fail(SEM_ERR_ARG, "null CG handle");
-  if (!c->x) return fail(SEM_ERR_ARG, "sem_cg_start has not been called");
-  return cg_iterate(c, k, static_cast<cudaStream_t>(stream));
+  return guarded([&]() -> sem_status {
+    if (!c) return fail(SEM_ERR_ARG, "null CG handle");
+    if (!c->x) return fail(SEM_ERR_ARG, "sem_cg_start has not been called");
+    return cg_iterate(c, k, static_cast<cudaStream_t>(stream));
+  });
 }
 
 extern "C" sem_status sem_cg_iterate_timed(sem_cg c, int k, double* total_ms, double* kernel_ms, void* stream) {
-  if (!c || !total_ms || !kernel_ms) return fail(SEM_ERR_ARG, "null argument");
-  if (!c->x) return fail(SEM_ERR_ARG, "sem_cg_start has not been called");
-  if (k < 1) return fail(SEM_ERR_ARG, "k must be >= 1");
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  sem_mesh m = c->m;
-  cg_note(c, s);
-  note_stream(m, s);
-  std::vector<cudaEvent_t> ev(3 * static_cast<size_t>(k) + 1, nullptr);
-  auto destroy = [&] {
-    for (cudaEvent_t e : ev)
-      if (e) cudaEventDestroy(e);
-  };
-  for (auto& e : ev) {
-    cudaError_t r = cudaEventCreate(&e);
-    if (r != cudaSuccess) {
-      destroy();
-      return cuda_fail(r, "cudaEventCreate");
-    }
-  }
-  sem_status st = SEM_OK;
-  cudaEventRecord(ev[0], s);
-  for (int q = 0; q < k && st == SEM_OK; ++q) {
-    AxLaunch a{};
-    a.w = c->w;
-    a.z = c->z;
-    a.p = c->p;
-    a.st = c->st;
-    a.partials = c->ax_part;
-    a.grid_out = &c->ax_blocks;
-    st = launch_ax_any(m, c->prec, c->variant, true, a, s);
-    cudaEventRecord(ev[3 * q + 1], s);
-    if (st == SEM_OK)
-      st = launch_dssum_cg(data_prec(c->prec), m->gs, c->w, c->p, c->st, c->ax_part,
-                           c->ax_blocks, c->gs_part, s);
-    cudaEventRecord(ev[3 * q + 2], s);
-    if (st == SEM_OK)
-      st = launch_cg_update(data_prec(c->prec), m->n, c->x, c->p, c->r, c->w, c->z, minv_of(c), m->mult, m->ctab, c->st,
-                            c->upd_part, s);
-    cudaEventRecord(ev[3 * q + 3], s);
-  }
-  cudaError_t r = cudaStreamSynchronize(s);
-  if (st == SEM_OK && r != cudaSuccess) st = cuda_fail(r, "cudaStreamSynchronize");
-  if (st == SEM_OK) {
-    float t = 0.f;
-    cudaEventElapsedTime(&t, ev[0], ev[3 * k]);
-    *total_ms = t;
-    for (int j = 0; j < 3; ++j) kernel_ms[j] = 0.0;
-    for (int q = 0; q < k; ++q)
-      for (int j = 0; j < 3; ++j) {
-        cudaEventElapsedTime(&t, ev[3 * q + j], ev[3 * q + j + 1]);
-        kernel_ms[j] += t / k;
+  return guarded([&]() -> sem_status {
+    if (!c || !total_ms || !kernel_ms) return fail(SEM_ERR_ARG, "null argument");
+    if (!c->x) return fail(SEM_ERR_ARG, "sem_cg_start has not been called");
+    if (k < 1) return fail(SEM_ERR_ARG, "k must be >= 1");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    sem_mesh m = c->m;
+    cg_note(c, s);
+    note_stream(m, s);
+    std::vector<cudaEvent_t> ev(3 * static_cast<size_t>(k) + 1, nullptr);
+    auto destroy = [&] {
+      for (cudaEvent_t e : ev)
+        if (e) cudaEventDestroy(e);
+    };
+    for (auto& e : ev) {
+      cudaError_t r = cudaEventCreate(&e);
+      if (r != cudaSuccess) {
+        destroy();
+        return cuda_fail(r, "cudaEventCreate");
       }
-  }
-  destroy();
-  return st;
+    }
+    sem_status st = SEM_OK;
+    cudaEventRecord(ev[0], s);
+    for (int q = 0; q < k && st == SEM_OK; ++q) {
+      AxLaunch a{};
+      a.w = c->w;
+      a.z = c->z;
+      a.p = c->p;
+      a.st = c->st;
+      a.partials = c->ax_part;
+      a.grid_out = &c->ax_blocks;
+      st = launch_ax_any(m, c->prec, c->variant, true, a, s);
+      cudaEventRecord(ev[3 * q + 1], s);
+      if (st == SEM_OK)
+        st = launch_dssum_cg(data_prec(c->prec), m->gs, c->w, c->p, c->st, c->ax_part,
+                             c->ax_blocks, c->gs_part, s);
+      cudaEventRecord(ev[3 * q + 2], s);
+      if (st == SEM_OK)
+        st = launch_cg_update(data_prec(c->prec), m->n, c->x, c->p, c->r, c->w, c->z, minv_of(c), m->mult, m->ctab, c->st,
+                              c->upd_part, s);
+      cudaEventRecord(ev[3 * q + 3], s);
+    }
+    cudaError_t r = cudaStreamSynchronize(s);
+    if (st == SEM_OK && r != cudaSuccess) st = cuda_fail(r, "cudaStreamSynchronize");
+    if (st == SEM_OK) {
+      float t = 0.f;
+      cudaEventElapsedTime(&t, ev[0], ev[3 * k]);
+      *total_ms = t;
+      for (int j = 0; j < 3; ++j) kernel_ms[j] = 0.0;
+      for (int q = 0; q < k; ++q)
+        for (int j = 0; j < 3; ++j) {
+          cudaEventElapsedTime(&t, ev[3 * q + j], ev[3 * q + j + 1]);
+          kernel_ms[j] += t / k;
+        }
+    }
+    destroy();
+    return st;
+  });
 }
 
 extern "C" sem_status sem_cg_query(sem_cg c, sem_cg_result* res, void* stream) {
-  if (!c || !res) return fail(SEM_ERR_ARG, "null argument");
-  res->time_ms = 0;
-  return cg_query(c, res, static_cast<cudaStream_t>(stream));
+  return guarded([&]() -> sem_status {
+    if (!c || !res) return fail(SEM_ERR_ARG, "null argument");
+    res->time_ms = 0;
+    return cg_query(c, res, static_cast<cudaStream_t>(stream));
+  });
 }
 
 extern "C" sem_status sem_cg_destroy(sem_cg c) {
-  if (!c) return SEM_OK;
-  cg_free(c);  // waits only for the streams this solver was used on
-  return SEM_OK;
+  return guarded([&]() -> sem_status {
+    if (!c) return SEM_OK;
+    cg_free(c);  // waits only for the streams this solver was used on
+    return SEM_OK;
+  });
 }
 
 extern "C" sem_status sem_cg_solve(sem_mesh m, const double* b, double* x, const sem_cg_opts* o, sem_cg_result* res,
                                    void* stream) {
-  SEM_TRY(check_mesh(m));
-  SEM_TRY(check_opts(o));
-  SEM_TRY(check_ptr(b, "b_dev"));
-  SEM_TRY(check_ptr(x, "x_dev"));
-  if (!res) return fail(SEM_ERR_ARG, "result is null");
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const double t0 = now_ms();
-  *res = sem_cg_result{};
-  sem_status st;
-  if (o->mixed) {
-    st = solve_mixed(m, b, x, o, res, s);
-  } else {
-    // Algorithm 1; when the recursively updated residual meets rtol, CG restarts from x:
-    // the restart recomputes r = b - A x, so the solve ends only when the true residual meets
-    // rtol (long runs let the recursive residual drift away from b - A x).
-    sem_cg c = nullptr;
-    SEM_TRY(cached_cg(m, o->f64_arith ? SEM_F64X : SEM_F64, static_cast<sem_ax_variant>(o->variant), o->precond,
-                      o->use_graph, o->rtol, o->max_iter, &c));
-    st = cg_start(c, b, x, false, s);
-    int total = 0;
-    for (int restart = 0; st == SEM_OK; ++restart) {
-      sem_cg_result r{};
-      st = cg_query(c, &r, s);
-      if (st != SEM_OK) break;
-      if (r.status != SEM_ERR_BUSY) {  // decided at the (re)start: true residual small, or limit
+  return guarded([&]() -> sem_status {
+    SEM_TRY(check_mesh(m));
+    SEM_TRY(check_opts(o));
+    SEM_TRY(check_ptr(b, "b_dev"));
+    SEM_TRY(check_ptr(x, "x_dev"));
+    if (!res) return fail(SEM_ERR_ARG, "result is null");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const double t0 = now_ms();
+    *res = sem_cg_result{};
+    sem_status st;
+    if (o->mixed) {
+      st = solve_mixed(m, b, x, o, res, s);
+    } else {
+      // Algorithm 1; when the recursively updated residual meets rtol, CG restarts from x:
+      // the restart recomputes r = b - A x, so the solve ends only when the true residual meets
+      // rtol (long runs let the recursive residual drift away from b - A x).
+      sem_cg c = nullptr;
+      SEM_TRY(cached_cg(m, o->f64_arith ? SEM_F64X : SEM_F64, static_cast<sem_ax_variant>(o->variant), o->precond,
+                        o->use_graph, o->rtol, o->max_iter, &c));
+      st = cg_start(c, b, x, false, s);
+      int total = 0;
+      for (int restart = 0; st == SEM_OK; ++restart) {
+        sem_cg_result r{};
+        st = cg_query(c, &r, s);
+        if (st != SEM_OK) break;
+        if (r.status != SEM_ERR_BUSY) {  // decided at the (re)start: true residual small, or limit
+          res->status = r.status;
+          res->rel_res = r.rel_res;
+          break;
+        }
+        st = cg_run(c, o->check_every, &r, s);
+        if (st != SEM_OK) break;
+        total += r.iters;
         res->status = r.status;
         res->rel_res = r.rel_res;
-        break;
+        if (r.status != SEM_OK || restart >= 20) break;
+        c->max_iter = o->max_iter - total;
+        st = cg_start(c, b, x, false, s);
       }
-      st = cg_run(c, o->check_every, &r, s);
-      if (st != SEM_OK) break;
-      total += r.iters;
-      res->status = r.status;
-      res->rel_res = r.rel_res;
-      if (r.status != SEM_OK || restart >= 20) break;
-      c->max_iter = o->max_iter - total;
-      st = cg_start(c, b, x, false, s);
+      res->iters = total;
+      cudaStreamSynchronize(s);
     }
-    res->iters = total;
-    cudaStreamSynchronize(s);
-  }
-  res->time_ms = now_ms() - t0;
-  if (st != SEM_OK) {
-    res->status = st;
-    return st;
-  }
-  if (res->status == SEM_ERR_NOT_CONVERGED) return fail(SEM_ERR_NOT_CONVERGED, "CG reached max_iter");
-  if (res->status == SEM_ERR_BREAKDOWN) return fail(SEM_ERR_BREAKDOWN, "CG breakdown (<p,Ap,c> <= 0 or non-finite)");
-  return static_cast<sem_status>(res->status);
+    res->time_ms = now_ms() - t0;
+    if (st != SEM_OK) {
+      res->status = st;
+      return st;
+    }
+    if (res->status == SEM_ERR_NOT_CONVERGED) return fail(SEM_ERR_NOT_CONVERGED, "CG reached max_iter");
+    if (res->status == SEM_ERR_BREAKDOWN) return fail(SEM_ERR_BREAKDOWN, "CG breakdown (<p,Ap,c> <= 0 or non-finite)");
+    return static_cast<sem_status>(res->status);
+  });
 }
 
 extern "C" uint64_t sem_launch_count(void) { return g_launches.load(); }
@@ -1108,135 +1154,141 @@ std::string device_name() {
 }  // namespace
 
 extern "C" sem_status sem_autotune(sem_mesh m, sem_prec prec, int reps, sem_tune_report* rep, void* stream) {
-  SEM_TRY(check_mesh(m));
-  SEM_TRY(check_prec(prec));
-  if (!rep || reps < 1) return fail(SEM_ERR_ARG, "need a report and reps >= 1");
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  note_stream(m, s);
-  const size_t es = prec == SEM_F32 ? sizeof(float) : sizeof(double);
-  void *u = nullptr, *w = nullptr;
-  SEM_CUDA_TRY(cudaMallocAsync(&u, m->n * es, s));
-  cudaError_t e = cudaMallocAsync(&w, m->n * es, s);
-  if (e != cudaSuccess) {
-    cudaFreeAsync(u, s);
-    return cuda_fail(e, "cudaMallocAsync");
-  }
-  cudaMemsetAsync(u, 0, m->n * es, s);
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
-  *rep = sem_tune_report{};
-  rep->N = m->N;
-  rep->prec = prec;
-  sem_status st = SEM_OK;
-  for (const sem_ax_variant v : {SEM_AX_STORED, SEM_AX_OTF, SEM_AX_OTF_SCALE}) {
-    if (st != SEM_OK) break;
-    if (v == SEM_AX_STORED && !has_factors(m, prec)) continue;
-    if (v != SEM_AX_STORED && prec == SEM_F64X) continue;
-    if (v == SEM_AX_OTF_SCALE && !has_scales(m)) continue;
-    for (int shape = 0; shape < 2 && st == SEM_OK; ++shape) {
-      if (shape == 1 && (prec == SEM_F64X || v == SEM_AX_OTF_SCALE ||
-                         ax_elements_per_block(m->N, 1) == ax_elements_per_block(m->N, 0)))
-        continue;
-      AxLaunch a{};
-      a.u = u;
-      a.w = w;
-      a.E = m->E;
-      a.err = m->dev_err;
-      a.shape = shape == 0 ? 2 : shape;  // the tuner times each shape as it is
-      a.coef = prec == SEM_F32 ? static_cast<const void*>(m->coef32) : static_cast<const void*>(m->coef64);
-      a.G = stored_factors(m, prec, &a.g_pairs);
-      a.scale = prec == SEM_F32 ? static_cast<const void*>(m->scale32) : static_cast<const void*>(m->scale64);
-      auto launch = [&] {
-        if (prec == SEM_F64X) return launch_ax_f64x(m->N, v, false, a, s);
-        return prec == SEM_F64 ? launch_ax_f64(m->N, v, false, a, s) : launch_ax_f32(m->N, v, false, a, s);
-      };
-      for (int q = 0; q < 2 && st == SEM_OK; ++q) st = launch();
-      cudaEventRecord(e0, s);
-      for (int q = 0; q < reps && st == SEM_OK; ++q) st = launch();
-      cudaEventRecord(e1, s);
+  return guarded([&]() -> sem_status {
+    SEM_TRY(check_mesh(m));
+    SEM_TRY(check_prec(prec));
+    if (!rep || reps < 1) return fail(SEM_ERR_ARG, "need a report and reps >= 1");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    note_stream(m, s);
+    const size_t es = prec == SEM_F32 ? sizeof(float) : sizeof(double);
+    void *u = nullptr, *w = nullptr;
+    SEM_CUDA_TRY(cudaMallocAsync(&u, m->n * es, s));
+    cudaError_t e = cudaMallocAsync(&w, m->n * es, s);
+    if (e != cudaSuccess) {
+      cudaFreeAsync(u, s);
+      return cuda_fail(e, "cudaMallocAsync");
+    }
+    cudaMemsetAsync(u, 0, m->n * es, s);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    *rep = sem_tune_report{};
+    rep->N = m->N;
+    rep->prec = prec;
+    sem_status st = SEM_OK;
+    for (const sem_ax_variant v : {SEM_AX_STORED, SEM_AX_OTF, SEM_AX_OTF_SCALE}) {
       if (st != SEM_OK) break;
-      cudaEventSynchronize(e1);
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      sem_tune_entry& c = rep->candidates[rep->n_candidates++];
-      c.variant = v;
-      c.shape = shape;
-      c.elements_per_block = prec == SEM_F64X ? 0 : ax_elements_per_block(m->N, shape);
-      c.ms = ms / reps;
+      if (v == SEM_AX_STORED && !has_factors(m, prec)) continue;
+      if (v != SEM_AX_STORED && prec == SEM_F64X) continue;
+      if (v == SEM_AX_OTF_SCALE && !has_scales(m)) continue;
+      for (int shape = 0; shape < 2 && st == SEM_OK; ++shape) {
+        if (shape == 1 && (prec == SEM_F64X || v == SEM_AX_OTF_SCALE ||
+                           ax_elements_per_block(m->N, 1) == ax_elements_per_block(m->N, 0)))
+          continue;
+        AxLaunch a{};
+        a.u = u;
+        a.w = w;
+        a.E = m->E;
+        a.err = m->dev_err;
+        a.shape = shape == 0 ? 2 : shape;  // the tuner times each shape as it is
+        a.coef = prec == SEM_F32 ? static_cast<const void*>(m->coef32) : static_cast<const void*>(m->coef64);
+        a.G = stored_factors(m, prec, &a.g_pairs);
+        a.scale = prec == SEM_F32 ? static_cast<const void*>(m->scale32) : static_cast<const void*>(m->scale64);
+        auto launch = [&] {
+          if (prec == SEM_F64X) return launch_ax_f64x(m->N, v, false, a, s);
+          return prec == SEM_F64 ? launch_ax_f64(m->N, v, false, a, s) : launch_ax_f32(m->N, v, false, a, s);
+        };
+        for (int q = 0; q < 2 && st == SEM_OK; ++q) st = launch();
+        cudaEventRecord(e0, s);
+        for (int q = 0; q < reps && st == SEM_OK; ++q) st = launch();
+        cudaEventRecord(e1, s);
+        if (st != SEM_OK) break;
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        sem_tune_entry& c = rep->candidates[rep->n_candidates++];
+        c.variant = v;
+        c.shape = shape;
+        c.elements_per_block = prec == SEM_F64X ? 0 : ax_elements_per_block(m->N, shape);
+        c.ms = ms / reps;
+      }
     }
-  }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  cudaFreeAsync(u, s);
-  cudaFreeAsync(w, s);
-  cudaStreamSynchronize(s);
-  if (st != SEM_OK) return st;
-  if (rep->n_candidates == 0) return fail(SEM_ERR_ARG, "no candidate implementation for this precision");
-  TuneSlot t;
-  t.valid = true;
-  double best = 1e300;
-  double best_v[3] = {1e300, 1e300, 1e300};
-  for (int q = 0; q < rep->n_candidates; ++q) {
-    const sem_tune_entry& c = rep->candidates[q];
-    const int slot = vslot(static_cast<sem_ax_variant>(c.variant));
-    if (c.ms < best_v[slot]) {
-      best_v[slot] = c.ms;
-      t.shape[slot] = c.shape;
-      t.ms[slot] = c.ms;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFreeAsync(u, s);
+    cudaFreeAsync(w, s);
+    cudaStreamSynchronize(s);
+    if (st != SEM_OK) return st;
+    if (rep->n_candidates == 0) return fail(SEM_ERR_ARG, "no candidate implementation for this precision");
+    TuneSlot t;
+    t.valid = true;
+    double best = 1e300;
+    double best_v[3] = {1e300, 1e300, 1e300};
+    for (int q = 0; q < rep->n_candidates; ++q) {
+      const sem_tune_entry& c = rep->candidates[q];
+      const int slot = vslot(static_cast<sem_ax_variant>(c.variant));
+      if (c.ms < best_v[slot]) {
+        best_v[slot] = c.ms;
+        t.shape[slot] = c.shape;
+        t.ms[slot] = c.ms;
+      }
+      if (c.ms < best) {
+        best = c.ms;
+        rep->best = q;
+        t.best = static_cast<sem_ax_variant>(c.variant);
+      }
     }
-    if (c.ms < best) {
-      best = c.ms;
-      rep->best = q;
-      t.best = static_cast<sem_ax_variant>(c.variant);
-    }
-  }
-  std::lock_guard<std::mutex> lock(g_tune_mu);
-  g_tune[prec][m->N] = t;
-  return SEM_OK;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune[prec][m->N] = t;
+    return SEM_OK;
+  });
 }
 
 extern "C" sem_status sem_autotune_save(const char* path) {
-  if (!path) return fail(SEM_ERR_ARG, "null path");
-  std::ofstream f(path);
-  if (!f) return fail(SEM_ERR_ARG, std::string("cannot write ") + path);
-  f << "sem-autotune 2 " << device_name() << "\n";
-  std::lock_guard<std::mutex> lock(g_tune_mu);
-  for (int p = 0; p < 3; ++p)
-    for (int N = 1; N <= SEM_MAX_N; ++N) {
-      const TuneSlot& t = g_tune[p][N];
-      if (t.valid)
-        f << p << " " << N << " " << t.best << " " << t.shape[0] << " " << t.shape[1] << " " << t.shape[2] << " "
-          << t.ms[0] << " " << t.ms[1] << " " << t.ms[2] << "\n";
-    }
-  return f ? SEM_OK : fail(SEM_ERR_ARG, "write failed");
+  return guarded([&]() -> sem_status {
+    if (!path) return fail(SEM_ERR_ARG, "null path");
+    std::ofstream f(path);
+    if (!f) return fail(SEM_ERR_ARG, std::string("cannot write ") + path);
+    f << "sem-autotune 2 " << device_name() << "\n";
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    for (int p = 0; p < 3; ++p)
+      for (int N = 1; N <= SEM_MAX_N; ++N) {
+        const TuneSlot& t = g_tune[p][N];
+        if (t.valid)
+          f << p << " " << N << " " << t.best << " " << t.shape[0] << " " << t.shape[1] << " " << t.shape[2] << " "
+            << t.ms[0] << " " << t.ms[1] << " " << t.ms[2] << "\n";
+      }
+    return f ? SEM_OK : fail(SEM_ERR_ARG, "write failed");
+  });
 }
 
 extern "C" sem_status sem_autotune_load(const char* path) {
-  if (!path) return fail(SEM_ERR_ARG, "null path");
-  std::ifstream f(path);
-  if (!f) return fail(SEM_ERR_ARG, std::string("cannot read ") + path);
-  std::string magic, gpu;
-  int version = 0;
-  f >> magic >> version >> gpu;
-  if (magic != "sem-autotune" || version != 2) return fail(SEM_ERR_ARG, "not a tuning table");
-  if (gpu != device_name()) return fail(SEM_ERR_ARG, "tuning table was made on " + gpu);
-  int p, N, best, s0, s1, s2;
-  double m0, m1, m2;
-  std::lock_guard<std::mutex> lock(g_tune_mu);
-  while (f >> p >> N >> best >> s0 >> s1 >> s2 >> m0 >> m1 >> m2) {
-    if (p < 0 || p > 2 || N < 1 || N > SEM_MAX_N || !(best == 0 || best == 1 || best == 3) || s0 < 0 || s0 > 1 ||
-        s1 < 0 || s1 > 1 || s2 != 0)
-      return fail(SEM_ERR_ARG, "corrupt tuning table");
-    TuneSlot& t = g_tune[p][N];
-    t.valid = true;
-    t.best = static_cast<sem_ax_variant>(best);
-    t.shape[0] = s0;
-    t.shape[1] = s1;
-    t.shape[2] = s2;
-    t.ms[0] = m0;
-    t.ms[1] = m1;
-    t.ms[2] = m2;
-  }
-  return SEM_OK;
+  return guarded([&]() -> sem_status {
+    if (!path) return fail(SEM_ERR_ARG, "null path");
+    std::ifstream f(path);
+    if (!f) return fail(SEM_ERR_ARG, std::string("cannot read ") + path);
+    std::string magic, gpu;
+    int version = 0;
+    f >> magic >> version >> gpu;
+    if (magic != "sem-autotune" || version != 2) return fail(SEM_ERR_ARG, "not a tuning table");
+    if (gpu != device_name()) return fail(SEM_ERR_ARG, "tuning table was made on " + gpu);
+    int p, N, best, s0, s1, s2;
+    double m0, m1, m2;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    while (f >> p >> N >> best >> s0 >> s1 >> s2 >> m0 >> m1 >> m2) {
+      if (p < 0 || p > 2 || N < 1 || N > SEM_MAX_N || !(best == 0 || best == 1 || best == 3) || s0 < 0 || s0 > 1 ||
+          s1 < 0 || s1 > 1 || s2 != 0)
+        return fail(SEM_ERR_ARG, "corrupt tuning table");
+      TuneSlot& t = g_tune[p][N];
+      t.valid = true;
+      t.best = static_cast<sem_ax_variant>(best);
+      t.shape[0] = s0;
+      t.shape[1] = s1;
+      t.shape[2] = s2;
+      t.ms[0] = m0;
+      t.ms[1] = m1;
+      t.ms[2] = m2;
+    }
+    return SEM_OK;
+  });
 }

@@ -4,7 +4,9 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <exception>
 #include <memory>
+#include <new>
 #include <string>
 #include <utility>
 #include <vector>
@@ -17,6 +19,21 @@ constexpr int kMaxNp = SEM_MAX_N + 1;  // 12 points per direction at most
 
 // Sets the thread-local error message and returns `s`.
 sem_status fail(sem_status s, const std::string& msg);
+
+// Runs the body of a C entry point; a C++ exception (a failed host allocation, a thread that
+// cannot be started) becomes a status instead of crossing the C boundary.
+template <typename F>
+sem_status guarded(F&& body) {
+  try {
+    return body();
+  } catch (const std::bad_alloc&) {
+    return fail(SEM_ERR_OOM, "host memory allocation failed");
+  } catch (const std::exception& e) {
+    return fail(SEM_ERR_CUDA, std::string("host error: ") + e.what());
+  } catch (...) {
+    return fail(SEM_ERR_CUDA, "unknown host error");
+  }
+}
 sem_status cuda_fail(cudaError_t e, const char* what);
 void count_launch(int k = 1);
 

@@ -111,11 +111,16 @@ void run_request(sem_server srv, Request* r) {
   }
   std::vector<double> xh;
   if (st == SEM_OK) {
-    xh.resize(static_cast<size_t>(info.n_local));
-    if (cudaMemcpyAsync(xh.data(), x, xh.size() * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess)
-      st = SEM_ERR_CUDA;
+    try {
+      xh.resize(static_cast<size_t>(info.n_local));
+    } catch (const std::bad_alloc&) {
+      st = SEM_ERR_OOM;
+    }
   }
+  if (st == SEM_OK && (cudaMemcpyAsync(xh.data(), x, xh.size() * sizeof(double), cudaMemcpyDeviceToHost, s) !=
+                           cudaSuccess ||
+                       cudaStreamSynchronize(s) != cudaSuccess))
+    st = SEM_ERR_CUDA;
   const double t2 = now_ms();
   if (b) cudaFreeAsync(b, s);
   if (x) cudaFreeAsync(x, s);
@@ -165,95 +170,116 @@ void worker_loop(sem_server srv) {
 }  // namespace
 
 using sem::fail;
+using sem::guarded;
 
 extern "C" sem_status sem_server_create(size_t hbm_budget_bytes, int max_slots, sem_server* out) {
-  if (!out) return fail(SEM_ERR_ARG, "out is null");
-  *out = nullptr;
-  if (max_slots < 1 || max_slots > 256 || hbm_budget_bytes == 0)
-    return fail(SEM_ERR_ARG, "need 1 <= max_slots <= 256 and a non-zero budget");
-  auto srv = std::make_unique<sem_server_s>();
-  SEM_CUDA_TRY(cudaGetDevice(&srv->device));
-  // keep freed stream-ordered memory in the pool between requests (this process only)
-  cudaMemPool_t pool;
-  if (cudaDeviceGetDefaultMemPool(&pool, srv->device) == cudaSuccess) {
-    uint64_t keep = hbm_budget_bytes;
-    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
-  }
-  srv->budget = hbm_budget_bytes;
-  srv->max_slots = max_slots;
-  for (int q = 0; q < max_slots; ++q) srv->workers.emplace_back(worker_loop, srv.get());
-  *out = srv.release();
-  return SEM_OK;
+  return guarded([&]() -> sem_status {
+    if (!out) return fail(SEM_ERR_ARG, "out is null");
+    *out = nullptr;
+    if (max_slots < 1 || max_slots > 256 || hbm_budget_bytes == 0)
+      return fail(SEM_ERR_ARG, "need 1 <= max_slots <= 256 and a non-zero budget");
+    auto srv = std::make_unique<sem_server_s>();
+    SEM_CUDA_TRY(cudaGetDevice(&srv->device));
+    // keep freed stream-ordered memory in the pool between requests (this process only)
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, srv->device) == cudaSuccess) {
+      uint64_t keep = hbm_budget_bytes;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    srv->budget = hbm_budget_bytes;
+    srv->max_slots = max_slots;
+    try {
+      for (int q = 0; q < max_slots; ++q) srv->workers.emplace_back(worker_loop, srv.get());
+    } catch (const std::exception&) {  // a worker could not be started: stop the ones that did
+      {
+        std::lock_guard<std::mutex> lock(srv->mu);
+        srv->stop = true;
+      }
+      srv->cv.notify_all();
+      for (auto& t : srv->workers) t.join();
+      return fail(SEM_ERR_OOM, "could not start the server's worker threads");
+    }
+    *out = srv.release();
+    return SEM_OK;
+  });
 }
 
 extern "C" sem_status sem_server_submit(sem_server srv, const sem_request* req, uint64_t* ticket) {
-  if (!srv || !req || !ticket) return fail(SEM_ERR_ARG, "null argument");
-  if (req->N < 1 || req->N > SEM_MAX_N) return fail(SEM_ERR_UNSUPPORTED, "polynomial order out of range");
-  if (req->E < 1 || req->num_vertices < 8 || !req->vert_xyz_host || !req->elem_verts_host)
-    return fail(SEM_ERR_ARG, "request needs vertices and elements");
-  auto r = std::make_unique<Request>();
-  r->N = req->N;
-  r->vxyz.assign(req->vert_xyz_host, req->vert_xyz_host + 3 * req->num_vertices);
-  r->ev.assign(req->elem_verts_host, req->elem_verts_host + 8 * req->E);
-  if (req->dirichlet_vertex_flags_host)
-    r->dflags.assign(req->dirichlet_vertex_flags_host, req->dirichlet_vertex_flags_host + req->num_vertices);
-  std::memcpy(r->sine, req->sine, sizeof(r->sine));
-  r->opts = req->opts;
-  const size_t Np = static_cast<size_t>(req->N) + 1;
-  r->n_local = static_cast<int64_t>(static_cast<size_t>(req->E) * Np * Np * Np);
-  r->est_bytes = estimate_bytes(req->E, req->N, req->opts);
-  std::lock_guard<std::mutex> lock(srv->mu);
-  if (r->est_bytes > srv->budget) return fail(SEM_ERR_ARG, "request needs more device memory than the budget");
-  r->t_submit = now_ms();
-  r->ticket = srv->next_ticket++;
-  r->res.status = SEM_ERR_BUSY;
-  *ticket = r->ticket;
-  srv->queue.push_back(r.get());
-  srv->all.emplace(r->ticket, std::move(r));
-  srv->cv.notify_all();
-  return SEM_OK;
+  return guarded([&]() -> sem_status {
+    if (!srv || !req || !ticket) return fail(SEM_ERR_ARG, "null argument");
+    if (req->N < 1 || req->N > SEM_MAX_N) return fail(SEM_ERR_UNSUPPORTED, "polynomial order out of range");
+    if (req->E < 1 || req->num_vertices < 8 || !req->vert_xyz_host || !req->elem_verts_host)
+      return fail(SEM_ERR_ARG, "request needs vertices and elements");
+    auto r = std::make_unique<Request>();
+    r->N = req->N;
+    r->vxyz.assign(req->vert_xyz_host, req->vert_xyz_host + 3 * req->num_vertices);
+    r->ev.assign(req->elem_verts_host, req->elem_verts_host + 8 * req->E);
+    if (req->dirichlet_vertex_flags_host)
+      r->dflags.assign(req->dirichlet_vertex_flags_host, req->dirichlet_vertex_flags_host + req->num_vertices);
+    std::memcpy(r->sine, req->sine, sizeof(r->sine));
+    r->opts = req->opts;
+    const size_t Np = static_cast<size_t>(req->N) + 1;
+    r->n_local = static_cast<int64_t>(static_cast<size_t>(req->E) * Np * Np * Np);
+    r->est_bytes = estimate_bytes(req->E, req->N, req->opts);
+    std::lock_guard<std::mutex> lock(srv->mu);
+    if (r->est_bytes > srv->budget) return fail(SEM_ERR_ARG, "request needs more device memory than the budget");
+    r->t_submit = now_ms();
+    r->ticket = srv->next_ticket++;
+    r->res.status = SEM_ERR_BUSY;
+    *ticket = r->ticket;
+    srv->queue.push_back(r.get());
+    srv->all.emplace(r->ticket, std::move(r));
+    srv->cv.notify_all();
+    return SEM_OK;
+  });
 }
 
 extern "C" sem_status sem_server_poll(sem_server srv, uint64_t ticket, double* x_host, int64_t x_capacity,
                                       sem_server_result* res) {
-  if (!srv || !res) return fail(SEM_ERR_ARG, "null argument");
-  std::lock_guard<std::mutex> lock(srv->mu);
-  auto it = srv->all.find(ticket);
-  if (it == srv->all.end()) return fail(SEM_ERR_ARG, "unknown or released ticket");
-  Request* r = it->second.get();
-  if (!r->done) {
-    *res = sem_server_result{};
-    res->status = SEM_ERR_BUSY;
-    res->n_local = r->n_local;
-    return SEM_ERR_BUSY;
-  }
-  *res = r->res;
-  if (x_host) {
-    if (x_capacity < static_cast<int64_t>(r->x.size())) return fail(SEM_ERR_ARG, "x_host is too small");
-    std::memcpy(x_host, r->x.data(), r->x.size() * sizeof(double));
-    srv->all.erase(it);  // released once its solution has been taken
-  }
-  return SEM_OK;
+  return guarded([&]() -> sem_status {
+    if (!srv || !res) return fail(SEM_ERR_ARG, "null argument");
+    std::lock_guard<std::mutex> lock(srv->mu);
+    auto it = srv->all.find(ticket);
+    if (it == srv->all.end()) return fail(SEM_ERR_ARG, "unknown or released ticket");
+    Request* r = it->second.get();
+    if (!r->done) {
+      *res = sem_server_result{};
+      res->status = SEM_ERR_BUSY;
+      res->n_local = r->n_local;
+      return SEM_ERR_BUSY;
+    }
+    *res = r->res;
+    if (x_host) {
+      if (x_capacity < static_cast<int64_t>(r->x.size())) return fail(SEM_ERR_ARG, "x_host is too small");
+      std::memcpy(x_host, r->x.data(), r->x.size() * sizeof(double));
+      srv->all.erase(it);  // released once its solution has been taken
+    }
+    return SEM_OK;
+  });
 }
 
 extern "C" sem_status sem_server_stats(sem_server srv, int* queued, int* active, size_t* bytes_in_use) {
-  if (!srv) return fail(SEM_ERR_ARG, "null server");
-  std::lock_guard<std::mutex> lock(srv->mu);
-  if (queued) *queued = static_cast<int>(srv->queue.size());
-  if (active) *active = srv->active;
-  if (bytes_in_use) *bytes_in_use = srv->in_use;
-  return SEM_OK;
+  return guarded([&]() -> sem_status {
+    if (!srv) return fail(SEM_ERR_ARG, "null server");
+    std::lock_guard<std::mutex> lock(srv->mu);
+    if (queued) *queued = static_cast<int>(srv->queue.size());
+    if (active) *active = srv->active;
+    if (bytes_in_use) *bytes_in_use = srv->in_use;
+    return SEM_OK;
+  });
 }
 
 extern "C" sem_status sem_server_destroy(sem_server srv) {
-  if (!srv) return SEM_OK;
-  {
-    std::lock_guard<std::mutex> lock(srv->mu);
-    srv->stop = true;
-    srv->queue.clear();  // queued requests are dropped; running ones finish
-  }
-  srv->cv.notify_all();
-  for (auto& t : srv->workers) t.join();
-  delete srv;
-  return SEM_OK;
+  return guarded([&]() -> sem_status {
+    if (!srv) return SEM_OK;
+    {
+      std::lock_guard<std::mutex> lock(srv->mu);
+      srv->stop = true;
+      srv->queue.clear();  // queued requests are dropped; running ones finish
+    }
+    srv->cv.notify_all();
+    for (auto& t : srv->workers) t.join();
+    delete srv;
+    return SEM_OK;
+  });
 }
