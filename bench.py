@@ -639,6 +639,8 @@ def run_solve(args):
         "mixed_otf": sem.sem_cg_default_opts(rtol=1e-10, mixed=1, variant=sem.SEM_AX_STORED,
                                              inner_variant=sem.SEM_AX_OTF, inner_rtol=args.inner_rtol,
                                              check_every=50),
+        "mixed_reliable": sem.sem_cg_default_opts(rtol=1e-10, mixed=2, variant=sem.SEM_AX_STORED,
+                                                  inner_variant=sem.SEM_AX_OTF, inner_rtol=0.1, check_every=50),
     }
     for name, opts in configs.items():
         x.zero_()

@@ -234,10 +234,14 @@ typedef struct {
   int max_iter;       /* FP64 CG: iteration limit; mixed: limit on inner iterations in total */
   int precond;        /* 0: none, 1: Jacobi */
   int variant;        /* sem_ax_variant of the FP64 operator (SEM_AX_AUTO allowed) */
-  int mixed;          /* 0: FP64 CG; 1: FP32 inner CG + FP64 iterative refinement */
+  int mixed;          /* 0: FP64 CG; 1: FP32 inner CG + FP64 iterative refinement (inner CG restarted at
+                       * each refinement step); 2: the same with reliable updates: the FP32 CG keeps its
+                       * search direction and its residual is replaced by the true FP64 residual each
+                       * time it has dropped by inner_rtol (0.1 is typical) */
   int inner_variant;  /* sem_ax_variant of the FP32 inner operator (mixed; SEM_AX_AUTO allowed) */
-  double inner_rtol;  /* relative tolerance of each inner solve (mixed) */
-  int max_outer;      /* refinement steps limit (mixed) */
+  double inner_rtol;  /* relative tolerance of each inner solve (mixed = 1) or reduction between
+                       * residual replacements (mixed = 2) */
+  int max_outer;      /* refinement steps (mixed = 1) or residual replacements (mixed = 2) limit */
   int check_every;    /* iterations between host reads of the device convergence flag (>= 1) */
   int use_graph;      /* 1: replay check_every iterations as one captured CUDA graph */
   int f64_arith;      /* FP64 operator arithmetic: 0 native FP64, 1 double-float (SEM_F64X; stored variant) */

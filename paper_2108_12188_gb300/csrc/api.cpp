@@ -837,6 +837,7 @@ sem_status check_opts(const sem_cg_opts* o) {
       (o->inner_variant < SEM_AX_STORED || o->inner_variant > SEM_AX_OTF_SCALE) ||
       (o->f64_arith != 0 && o->f64_arith != 1))
     return fail(SEM_ERR_ARG, "invalid CG options");
+  if (o->mixed < 0 || o->mixed > 2) return fail(SEM_ERR_ARG, "mixed must be 0, 1 or 2");
   if (o->mixed && (!(o->inner_rtol > 0 && o->inner_rtol < 1) || o->max_outer < 1))
     return fail(SEM_ERR_ARG, "mixed precision needs 0 < inner_rtol < 1 and max_outer >= 1");
   return SEM_OK;
@@ -858,6 +859,11 @@ sem_status cg_run(sem_cg c, int check_every, sem_cg_result* r, cudaStream_t s) {
 // FP32 inner CG (on-the-fly or stored factors) inside FP64 iterative refinement:
 //   r = b - A x (FP64 operator, FP64 dots); stop if ||r||_c / ||b||_c <= rtol;
 //   solve A d = r in FP32 to inner_rtol; x += d.
+// mixed = 1 restarts the FP32 CG from d = 0 after each refinement step. mixed = 2 keeps it
+// going (reliable updates, i.e. residual replacement as in van der Vorst and Ye, 2000): each
+// time its residual has dropped by inner_rtol, x += d (FP64), d = 0, the true residual
+// b - A x is formed in FP64 and replaces the FP32 residual, and the FP32 CG continues along
+// its current search direction, so the Krylov process is not restarted.
 sem_status solve_mixed(sem_mesh m, const double* b, double* x, const sem_cg_opts* o, sem_cg_result* res,
                        cudaStream_t s) {
   sem_cg inner = nullptr;
@@ -915,19 +921,32 @@ sem_status solve_mixed(sem_mesh m, const double* b, double* x, const sem_cg_opts
       res->status = SEM_ERR_NOT_CONVERGED;
       break;
     }
-    // FP32 inner solve from d = 0
-    inner->max_iter = o->max_iter - total_inner;
-    if ((e = cudaMemsetAsync(d32, 0, m->n * sizeof(float), s)) != cudaSuccess) { st = cuda_fail(e, "memset"); break; }
-    if ((st = cg_start(inner, r32, d32, true, s)) != SEM_OK) break;
+    const bool replace = o->mixed == 2 && outer > 0;
+    if (replace) {  // reliable update: the true residual replaces the FP32 one, p is kept
+      if ((st = launch_cg_replace(m->n, r32, static_cast<float*>(inner->r), static_cast<float*>(inner->z),
+                                  static_cast<const float*>(minv_of(inner)), m->mult, m->ctab, inner->st,
+                                  inner->init_part, s)) != SEM_OK)
+        break;
+    } else {  // FP32 inner solve from d = 0
+      inner->max_iter = o->max_iter - total_inner;
+      if ((e = cudaMemsetAsync(d32, 0, m->n * sizeof(float), s)) != cudaSuccess) { st = cuda_fail(e, "memset"); break; }
+      if ((st = cg_start(inner, r32, d32, true, s)) != SEM_OK) break;
+    }
+    const int before = o->mixed == 2 ? total_inner : 0;  // mixed = 2: the count continues across replacements
     sem_cg_result ir{};
     if ((st = cg_run(inner, o->check_every, &ir, s)) != SEM_OK) break;
-    total_inner += ir.iters;
+    const int steps = ir.iters - before;
+    total_inner = o->mixed == 2 ? ir.iters : total_inner + ir.iters;
     ++outer;
-    if (ir.status == SEM_ERR_BREAKDOWN && ir.iters == 0) {
+    if (ir.status == SEM_ERR_BREAKDOWN && steps == 0) {
       res->status = SEM_ERR_BREAKDOWN;
       break;
     }
     if ((st = launch_ir_correct(m->n, x, d32, s)) != SEM_OK) break;
+    if (o->mixed == 2 && (e = cudaMemsetAsync(d32, 0, m->n * sizeof(float), s)) != cudaSuccess) {
+      st = cuda_fail(e, "memset");
+      break;
+    }
   }
   res->iters = total_inner;
   res->outer_iters = outer;

@@ -324,6 +324,48 @@ __global__ void k_ir_residual(int64_t n, const double* __restrict__ b, const dou
   }
 }
 
+// Residual replacement in the FP32 CG of the reliable-update solver: r = rnew (the FP32 copy
+// of the true FP64 residual), z = M^-1 r, rho' = <r, z, c>. The search direction p is kept; the
+// next direction update uses beta = rho' / rho, rho being the last accepted <r, z, c> (the
+// update kernel leaves it in place when it stops), and <r, r, c> becomes the reference of the
+// relative stopping test. The iteration count continues.
+__global__ void k_cg_replace(int64_t n, const float* __restrict__ rnew, float* __restrict__ r, float* __restrict__ z,
+                             const float* __restrict__ minv, const uint8_t* __restrict__ mult,
+                             const double* __restrict__ ctab, CgScalars* st, double* __restrict__ partials) {
+  __shared__ double sRed[kThreads / 32];
+  DotAcc<float> rz, rr;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const float ri = rnew[i];
+    const float zi = minv ? minv[i] * ri : ri;
+    r[i] = ri;
+    z[i] = zi;
+    const float c = weight_t<float>(mult, ctab, i);
+    rz.add(ri, c * zi);
+    rr.add(ri, c * ri);
+  }
+  const double v[2] = {block_sum(rz.value(), sRed), block_sum(rr.value(), sRed)};
+  if (publish_partials<2>(v, partials, &st->ticket[2])) {
+    const double srz = sum_partials(partials, gridDim.x, 2, 0, sRed);
+    const double srr = sum_partials(partials, gridDim.x, 2, 1, sRed);
+    if (threadIdx.x == 0) {
+      if (!isfinite(srz) || !isfinite(srr) || !(st->rho > 0.0)) {
+        st->status = SEM_ERR_BREAKDOWN;
+        st->done = 1;
+      } else {
+        st->beta = srz / st->rho;
+        st->rho = srz;
+        st->rz = srz;
+        st->rr = srr;
+        st->bb = srr;
+        st->status = 0;
+        st->done = srr > 0.0 ? 0 : 1;
+        if (st->done) st->status = SEM_OK;
+      }
+    }
+  }
+}
+
 __global__ void k_ir_correct(int64_t n, double* __restrict__ x, const float* __restrict__ d) {
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x)
@@ -336,6 +378,14 @@ sem_status launch_ir_residual(int64_t n, const double* b, const double* w, doubl
                               const uint8_t* mult, const double* ctab, CgScalars* st, double* partials,
                               cudaStream_t s) {
   k_ir_residual<<<vec_grid(n), kThreads, 0, s>>>(n, b, w, r64, r32, mult, ctab, st, partials);
+  count_launch();
+  SEM_CUDA_TRY(cudaGetLastError());
+  return SEM_OK;
+}
+
+sem_status launch_cg_replace(int64_t n, const float* rnew, float* r, float* z, const float* minv, const uint8_t* mult,
+                             const double* ctab, CgScalars* st, double* partials, cudaStream_t s) {
+  k_cg_replace<<<vec_grid(n), kThreads, 0, s>>>(n, rnew, r, z, minv, mult, ctab, st, partials);
   count_launch();
   SEM_CUDA_TRY(cudaGetLastError());
   return SEM_OK;

@@ -255,5 +255,9 @@ sem_status launch_ir_residual(int64_t n, const double* b, const double* w, doubl
                               cudaStream_t s);
 // x64 += (double) d32
 sem_status launch_ir_correct(int64_t n, double* x, const float* d, cudaStream_t s);
+// Residual replacement of the FP32 CG (reliable updates): r = rnew, z = M^-1 r, new rho and
+// beta = rho_new / rho, p kept; partials needs 2 x gridDim doubles.
+sem_status launch_cg_replace(int64_t n, const float* rnew, float* r, float* z, const float* minv, const uint8_t* mult,
+                             const double* ctab, CgScalars* st, double* partials, cudaStream_t s);
 
 }  // namespace sem

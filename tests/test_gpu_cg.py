@@ -82,6 +82,23 @@ def test_cg_mixed_precision(sem, c1, inner_variant, f64_arith):
     assert abs(e_gpu - e_ref) <= 5e-4 * e_ref + 1e-11, (e_gpu, e_ref)
 
 
+@pytest.mark.parametrize("inner_variant,graph", [(1, 1), (0, 0)], ids=["inner-otf-graph", "inner-stored-eager"])
+def test_cg_mixed_reliable_updates(sem, c1, inner_variant, graph):
+    """mixed = 2: the FP32 CG keeps its direction across residual replacements, so it needs
+    about as many iterations as FP64 CG (restarted refinement needs far more)."""
+    m, prob, b, ref, mesh = c1
+    opts = sem.sem_cg_default_opts(rtol=1e-10, mixed=2, inner_variant=inner_variant, inner_rtol=0.1,
+                                   use_graph=graph, check_every=7)
+    res, x = _solve(sem, mesh, prob, opts)
+    assert res["status"] == sem.SEM_OK, res
+    assert res["outer_iters"] >= 5  # residual replacements
+    assert _true_rel(prob, b, x) <= 1e-10 * (1 + 1e-3)
+    assert res["iters"] <= 1.3 * ref.iterations, (res["iters"], ref.iterations)
+    e_gpu = np.abs(x - prob.exact_solution().ravel()).max()
+    e_ref = np.abs(ref.x - prob.exact_solution()).max()
+    assert abs(e_gpu - e_ref) <= 5e-4 * e_ref + 1e-11, (e_gpu, e_ref)
+
+
 def test_cg_stateful_and_limits(sem, c1):
     import torch
     m, prob, b, ref, mesh = c1
