@@ -241,8 +241,8 @@ def oracle_cg_sample(nel: int = 12, budget_s: float = 10.0) -> dict:
                       f"{iters} oracle Jacobi-PCG iterations"}
 
 
-def oracle_c1_solve() -> dict:
-    """The oracle's Jacobi-PCG solve of the small configuration (4^3 hexahedra, jitter 0.1h,
+def oracle_small_solve() -> dict:
+    """The oracle's Jacobi-PCG solve of the small workload (4^3 hexahedra, jitter 0.1h,
     seed 0, N = 7, sine right-hand side, rtol 1e-10), timed whole (set-up excluded)."""
     from oracle import sem_oracle as so
     from synthetic import BoxMesh
@@ -274,10 +274,10 @@ def _oracle_procs(count: int, budget_s: float) -> list:
 def run_cpu_baseline(budget_s: float = 10.0) -> dict:
     """The oracle on the host cores: one process alone, then one process per core at once
     (the oracle is single-threaded; each process times its own sample); and the oracle's
-    whole solve of the small configuration, single-threaded."""
+    whole solve of the small 4^3 workload, single-threaded."""
     single = _oracle_procs(1, budget_s)[0]
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    code = "import json, bench; print('RESULT ' + json.dumps(bench.oracle_c1_solve()))"
+    code = "import json, bench; print('RESULT ' + json.dumps(bench.oracle_small_solve()))"
     pr = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
     c1 = [json.loads(ln[7:]) for ln in pr.stdout.splitlines() if ln.startswith("RESULT ")]
     cores = max(1, min(os.cpu_count() or 1, 72))
@@ -286,7 +286,7 @@ def run_cpu_baseline(budget_s: float = 10.0) -> dict:
     return {"value": total, "unit": "GDOF/s", "cores": cores, "kind": "oracle",
             "sample": f"{single['sample']}; one such sample per core, {cores} single-threaded processes at once",
             "single_core_value": single["gdof_s"], "s_per_iter_single_core": single["s_per_iter"],
-            "config1_solve": c1[0] if c1 else None}
+            "solve_4cube_n7": c1[0] if c1 else None}
 
 
 # ---------------------------------------------------------------------------
@@ -547,7 +547,7 @@ def run_gpu(args):
                    "(work-vector allocation, r0 = b - A x0 and CUDA-graph capture included)",
            "ms_per_step": e2e_ms}
 
-    # ---- config 1: 4^3 mesh (+-0.1h, seed 0), N = 7, sine RHS, Jacobi-CG from zero to 1e-10
+    # ---- small solve: 4^3 mesh (+-0.1h, seed 0), N = 7, sine RHS, Jacobi-CG from zero to 1e-10
     m1 = BoxMesh(4, 4, 4, jitter=0.1, seed=0)
     mesh1 = sem.Mesh(NORD, m1.vert_xyz, m1.elem_verts, flags=sem.SEM_MESH_F64_STORED)
     b1 = torch.empty(mesh1.n, dtype=torch.float64, device="cuda")
@@ -581,7 +581,7 @@ def run_gpu(args):
                        "l2": "inputs larger than L2 (about 1.1 GB of algorithmic traffic per step)",
                        "gflop_s_eq11": flops_eq11(NORD) * n / (ms_step * 1e-3) / 1e9},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "clocks": clk.summary(), "ax": ax, "cg_config1": cg_c1, "step_f64x": step_f64x,
+            "clocks": clk.summary(), "ax": ax, "cg_4cube_n7": cg_c1, "step_f64x": step_f64x,
         }
         print(json.dumps(out))
     mesh.close()
