@@ -25,9 +25,9 @@ REQS = [((3, 3, 3), 5, (1, 1, 1)), ((4, 3, 2), 7, (2, 1, 3)), ((2, 2, 2), 9, (1,
         ((3, 2, 4), 7, (1, 3, 2)), ((2, 3, 2), 5, (2, 2, 2))]
 
 
-def _opts(sem):
-    return sem.sem_cg_default_opts(rtol=1e-8, mixed=1, variant=sem.SEM_AX_OTF, inner_variant=sem.SEM_AX_OTF,
-                                   inner_rtol=1e-5, check_every=20)
+def _opts(sem, mixed=1):
+    return sem.sem_cg_default_opts(rtol=1e-8, mixed=mixed, variant=sem.SEM_AX_OTF, inner_variant=sem.SEM_AX_OTF,
+                                   inner_rtol=1e-5 if mixed == 1 else 0.1, check_every=20)
 
 
 def _solo(sem, m, N, sine, opts):
@@ -57,8 +57,9 @@ def _drain(sem, srv, tickets):
     return results
 
 
-def test_results_alone_equal_results_in_the_mix(sem):
-    opts = _opts(sem)
+@pytest.mark.parametrize("mixed", [1, 2], ids=["restarted", "reliable-updates"])
+def test_results_alone_equal_results_in_the_mix(sem, mixed):
+    opts = _opts(sem, mixed)
     meshes = [BoxMesh(*d, jitter=0.1, seed=40 + q) for q, (d, _, _) in enumerate(REQS)]
     srv = sem.sem_server_create(8 << 30, 4)
     tickets = [sem.sem_server_submit(srv, N, m.vert_xyz, m.elem_verts, sine, opts)
