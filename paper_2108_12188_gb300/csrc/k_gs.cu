@@ -67,7 +67,8 @@ __device__ __forceinline__ void seg_store(T* __restrict__ u, const int (&ix)[W],
 // Visits the segments of fixed-width class c (records of width W): f(ix, masked).
 template <int W, typename F>
 __device__ __forceinline__ void for_class(const GsPlan& g, int c, int64_t t0, int64_t stride, F&& f) {
-  for (int64_t s = t0; s < g.n[c]; s += stride) {
+  for (int64_t t = t0; t < g.n[c]; t += stride) {
+    const int64_t s = g.n[c] - 1 - t;  // last segments first: their copies were written last
     int ix[W];
     load_rec<W>(g.rec[c], s, ix);
     f(ix, g.msk[c][s] != 0);
