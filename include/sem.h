@@ -129,6 +129,10 @@ sem_status sem_mesh_numbering(int N, int64_t num_vertices, int64_t E, const int6
                               int64_t* n_glob_host);
 
 sem_status sem_mesh_get_info(sem_mesh mesh, sem_mesh_info_t* info_host);
+/* The three sizes of the mesh: local points E (N+1)^3, distinct global nodes, and
+ * gather-scatter segments (global nodes with copies on element boundaries). Any pointer may
+ * be NULL. */
+sem_status sem_mesh_info(sem_mesh mesh, int64_t* n_local, int64_t* n_glob, int64_t* n_shared_seg);
 
 /* Test hooks: copy the numbering (int64 [n_local]), the Dirichlet mask (uint8
  * [n_local], 1 = zeroed) and the gather-scatter segments to host buffers.
@@ -330,6 +334,13 @@ sem_status sem_server_create(size_t hbm_budget_bytes, int max_slots, sem_server*
 /* Copies the request and queues it; never waits for the GPU. SEM_ERR_ARG if the request alone
  * needs more than the budget. */
 sem_status sem_server_submit(sem_server server, const sem_request* request, uint64_t* ticket);
+/* Queues a solve of A x = b on a mesh the caller has built (sem_mesh_create on the server's
+ * device), from x = 0, with the options `opts`. b_host: [n_local] FP64 right-hand side
+ * (assembled and masked), copied at submit. On SEM_OK the mesh belongs to the server, which
+ * destroys it after the solve; the streams the mesh was used on are synchronised here, so the
+ * caller may release them afterwards. On any other status the caller keeps the mesh. */
+sem_status sem_server_submit_mesh(sem_server server, sem_mesh mesh, const double* b_host, const sem_cg_opts* opts,
+                                  uint64_t* ticket);
 /* SEM_ERR_BUSY (res->status too) while the request is queued or running. When done: SEM_OK and
  * res filled; if x_host is not NULL and x_capacity >= res->n_local, x is copied into it and the
  * ticket is released (later polls of it return SEM_ERR_ARG). */

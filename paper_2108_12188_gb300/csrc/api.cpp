@@ -386,6 +386,16 @@ extern "C" sem_status sem_mesh_destroy(sem_mesh m) {
   });
 }
 
+extern "C" sem_status sem_mesh_info(sem_mesh m, int64_t* n_local, int64_t* n_glob, int64_t* n_shared_seg) {
+  return guarded([&]() -> sem_status {
+    if (!m) return fail(SEM_ERR_ARG, "null mesh");
+    if (n_local) *n_local = m->n;
+    if (n_glob) *n_glob = m->n_glob;
+    if (n_shared_seg) *n_shared_seg = m->n_seg;
+    return SEM_OK;
+  });
+}
+
 extern "C" sem_status sem_mesh_get_info(sem_mesh m, sem_mesh_info_t* info) {
   return guarded([&]() -> sem_status {
     if (!m || !info) return fail(SEM_ERR_ARG, "null argument");

@@ -5,7 +5,8 @@
 //
 // A request carries its mesh (vertices, connectivity, order), the wave numbers of the
 // manufactured right-hand side and CG options; the worker that takes it builds the mesh,
-// the right-hand side, solves, copies x to host memory and releases everything. Every
+// the right-hand side, solves, copies x to host memory and releases everything. A request
+// may instead hand over a mesh the caller built and a host right-hand side. Every
 // device allocation is stream-ordered, so one request's set-up or teardown never waits for
 // the others' kernels. A request that fails (bad mesh, non-convergence) fails alone.
 //
@@ -30,6 +31,8 @@ double now_ms() {
 
 struct Request {
   uint64_t ticket = 0;
+  sem_mesh mesh = nullptr;       // prebuilt mesh (sem_server_submit_mesh), owned by the server
+  std::vector<double> b_host;    // its right-hand side
   int N = 0;
   std::vector<double> vxyz;
   std::vector<int64_t> ev;
@@ -43,6 +46,9 @@ struct Request {
   sem_server_result res{};
   std::vector<double> x;
   double t_submit = 0, t_start = 0;
+  ~Request() {  // a prebuilt mesh still queued when the server is destroyed
+    if (mesh) sem_mesh_destroy(mesh);
+  }
 };
 
 }  // namespace
@@ -90,17 +96,28 @@ void run_request(sem_server srv, Request* r) {
   unsigned flags = 0;
   if (r->opts.variant == SEM_AX_STORED) flags |= r->opts.f64_arith ? SEM_MESH_F64X_STORED : SEM_MESH_F64_STORED;
   if (r->opts.mixed && r->opts.inner_variant == SEM_AX_STORED) flags |= SEM_MESH_F32_STORED;
-  if (st == SEM_OK)
+  if (r->mesh) {  // prebuilt mesh: now the server's
+    mesh = r->mesh;
+    r->mesh = nullptr;
+  } else if (st == SEM_OK) {
     st = sem_mesh_create(r->N, static_cast<int64_t>(r->vxyz.size() / 3), r->vxyz.data(),
                          static_cast<int64_t>(r->ev.size() / 8), r->ev.data(),
                          r->dflags.empty() ? nullptr : r->dflags.data(), flags, s, &mesh);
+  }
   sem_mesh_info_t info{};
   if (st == SEM_OK) st = sem_mesh_get_info(mesh, &info);
   if (st == SEM_OK && cudaMallocAsync(reinterpret_cast<void**>(&b), info.n_local * sizeof(double), s) != cudaSuccess)
     st = SEM_ERR_OOM;
   if (st == SEM_OK && cudaMallocAsync(reinterpret_cast<void**>(&x), info.n_local * sizeof(double), s) != cudaSuccess)
     st = SEM_ERR_OOM;
-  if (st == SEM_OK) st = sem_rhs_sine(mesh, r->sine[0], r->sine[1], r->sine[2], SEM_F64, b, s);
+  if (st == SEM_OK) {
+    if (r->b_host.empty()) {
+      st = sem_rhs_sine(mesh, r->sine[0], r->sine[1], r->sine[2], SEM_F64, b, s);
+    } else if (cudaMemcpyAsync(b, r->b_host.data(), r->b_host.size() * sizeof(double), cudaMemcpyHostToDevice, s) !=
+               cudaSuccess) {
+      st = SEM_ERR_CUDA;
+    }
+  }
   if (st == SEM_OK && cudaMemsetAsync(x, 0, info.n_local * sizeof(double), s) != cudaSuccess) st = SEM_ERR_CUDA;
   const double t1 = now_ms();
   sem_cg_result cg{};
@@ -223,6 +240,37 @@ extern "C" sem_status sem_server_submit(sem_server srv, const sem_request* req, 
     r->est_bytes = estimate_bytes(req->E, req->N, req->opts);
     std::lock_guard<std::mutex> lock(srv->mu);
     if (r->est_bytes > srv->budget) return fail(SEM_ERR_ARG, "request needs more device memory than the budget");
+    r->t_submit = now_ms();
+    r->ticket = srv->next_ticket++;
+    r->res.status = SEM_ERR_BUSY;
+    *ticket = r->ticket;
+    srv->queue.push_back(r.get());
+    srv->all.emplace(r->ticket, std::move(r));
+    srv->cv.notify_all();
+    return SEM_OK;
+  });
+}
+
+extern "C" sem_status sem_server_submit_mesh(sem_server srv, sem_mesh mesh, const double* b_host,
+                                              const sem_cg_opts* opts, uint64_t* ticket) {
+  return guarded([&]() -> sem_status {
+    if (!srv || !mesh || !b_host || !opts || !ticket) return fail(SEM_ERR_ARG, "null argument");
+    if (mesh->device != srv->device) return fail(SEM_ERR_ARG, "the mesh lives on another device than the server");
+    auto r = std::make_unique<Request>();
+    r->N = mesh->N;
+    r->n_local = mesh->n;
+    r->b_host.assign(b_host, b_host + mesh->n);
+    r->opts = *opts;
+    // the mesh's memory plus the solver's: b, x, the Jacobi inverse (FP64 and FP32) and the
+    // CG work vectors (FP64 CG, or FP32 CG with the FP64 refinement buffers)
+    const size_t n = static_cast<size_t>(mesh->n);
+    r->est_bytes = mesh->device_bytes + 16 * n + 12 * n + (opts->mixed ? 40 * n : 32 * n) + (8u << 20);
+    std::lock_guard<std::mutex> lock(srv->mu);
+    if (r->est_bytes > srv->budget) return fail(SEM_ERR_ARG, "request needs more device memory than the budget");
+    // the caller's streams may go away: finish their work on the mesh now
+    for (cudaStream_t u : mesh->used) SEM_CUDA_TRY(cudaStreamSynchronize(u));
+    mesh->used.clear();
+    r->mesh = mesh;
     r->t_submit = now_ms();
     r->ticket = srv->next_ticket++;
     r->res.status = SEM_ERR_BUSY;

@@ -29,7 +29,8 @@ EXPORTS = [
     "sem_glsc3", "sem_glsc3_noalloc", "sem_jacobi", "sem_rhs_sine", "sem_cg_default_opts", "sem_cg_solve", "sem_cg_create",
     "sem_cg_start", "sem_cg_iterate", "sem_cg_iterate_timed", "sem_cg_query", "sem_cg_destroy", "sem_launch_count", "sem_last_error",
     "sem_status_string", "sem_server_create", "sem_server_submit", "sem_server_poll", "sem_server_stats",
-    "sem_server_destroy", "sem_autotune", "sem_autotune_save", "sem_autotune_load",
+    "sem_server_destroy", "sem_autotune", "sem_autotune_save", "sem_autotune_load", "sem_mesh_info",
+    "sem_server_submit_mesh",
 ]
 
 
@@ -106,6 +107,7 @@ def load_library(path: str | None = None):
         "sem_mesh_destroy": [_VP],
         "sem_mesh_numbering": [_I, _I64, _I64, _VP, _VP, _VP, _VP, C.POINTER(_I64)],
         "sem_mesh_get_info": [_VP, C.POINTER(MeshInfo)],
+        "sem_mesh_info": [_VP, C.POINTER(_I64), C.POINTER(_I64), C.POINTER(_I64)],
         "sem_mesh_get_glo_num": [_VP, _VP],
         "sem_mesh_get_mask": [_VP, _VP],
         "sem_mesh_get_segments": [_VP, _VP, _VP, _VP],
@@ -128,6 +130,7 @@ def load_library(path: str | None = None):
         "sem_cg_destroy": [_VP],
         "sem_server_create": [C.c_size_t, _I, C.POINTER(_VP)],
         "sem_server_submit": [_VP, C.POINTER(Request), C.POINTER(C.c_uint64)],
+        "sem_server_submit_mesh": [_VP, _VP, _VP, C.POINTER(CgOpts), C.POINTER(C.c_uint64)],
         "sem_server_poll": [_VP, C.c_uint64, _VP, _I64, C.POINTER(ServerResult)],
         "sem_server_stats": [_VP, C.POINTER(_I), C.POINTER(_I), C.POINTER(C.c_size_t)],
         "sem_server_destroy": [_VP],
@@ -226,6 +229,13 @@ def sem_mesh_get_info(mesh) -> dict:
     info = MeshInfo()
     _check(load_library().sem_mesh_get_info(mesh, C.byref(info)))
     return {f: getattr(info, f) for f, _ in MeshInfo._fields_}
+
+
+def sem_mesh_info(mesh) -> tuple:
+    """(n_local, n_glob, n_shared_seg) of a mesh."""
+    a, b, c = _I64(), _I64(), _I64()
+    _check(load_library().sem_mesh_info(mesh, C.byref(a), C.byref(b), C.byref(c)))
+    return int(a.value), int(b.value), int(c.value)
 
 
 def sem_mesh_get_glo_num(mesh) -> np.ndarray:
@@ -393,6 +403,22 @@ def sem_server_submit(server, N, vert_xyz, elem_verts, sine=(1, 1, 1), opts=None
                   None if df is None else df.ctypes.data, (C.c_int * 3)(*sine), opts or sem_cg_default_opts())
     ticket = C.c_uint64()
     _check(load_library().sem_server_submit(server, C.byref(req), C.byref(ticket)))  # copies the arrays
+    return int(ticket.value)
+
+
+def sem_server_submit_mesh(server, mesh, b_host, opts=None):
+    """Queues a solve from x = 0 on a prebuilt mesh (a Mesh, which gives up its handle, or a
+    raw handle) with the FP64 host right-hand side b_host (copied). The server destroys the mesh."""
+    handle = mesh.handle if isinstance(mesh, Mesh) else mesh
+    b = np.ascontiguousarray(b_host, dtype=np.float64)
+    n, _, _ = sem_mesh_info(handle)
+    if b.size != n:
+        raise SemError(SEM_ERR_ARG, f"b has {b.size} values, the mesh {n} points")
+    o = opts or sem_cg_default_opts()
+    ticket = C.c_uint64()
+    _check(load_library().sem_server_submit_mesh(server, handle, b.ctypes.data, C.byref(o), C.byref(ticket)))
+    if isinstance(mesh, Mesh):
+        mesh.handle = None  # now the server's
     return int(ticket.value)
 
 

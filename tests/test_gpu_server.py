@@ -100,3 +100,55 @@ def test_bad_request_fails_alone_and_budget(sem):
     assert e.value.status == sem.SEM_ERR_ARG
     assert sem.sem_server_stats(srv)["active"] == 0
     sem.sem_server_destroy(srv)
+
+
+def test_prebuilt_mesh_requests(sem):
+    """sem_server_submit_mesh: a mesh built by the caller (with stored factors) and a host
+    right-hand side from the oracle give, in the mix with ordinary requests, the same x as
+    sem_cg_solve on an identical mesh; the server takes the mesh over, and prebuilt meshes
+    still queued when the server is destroyed are released with it."""
+    import torch
+    cases = [((3, 3, 2), 7, 0, sem.SEM_MESH_F64_STORED), ((2, 3, 3), 5, 2, sem.SEM_MESH_F32_STORED),
+             ((4, 2, 2), 9, 0, sem.SEM_MESH_F64X_STORED)]
+    srv = sem.sem_server_create(8 << 30, 3)
+    tickets, want = [], []
+    for q, (d, N, mixed, flags) in enumerate(cases):
+        m = BoxMesh(*d, jitter=0.1, seed=70 + q)
+        opts = sem.sem_cg_default_opts(rtol=1e-9, mixed=mixed, variant=sem.SEM_AX_STORED if mixed == 0 else sem.SEM_AX_OTF,
+                                       inner_variant=sem.SEM_AX_STORED, inner_rtol=0.1, check_every=10,
+                                       f64_arith=int(flags == sem.SEM_MESH_F64X_STORED))
+        b = so.SemProblem(N, m.vert_xyz, m.elem_verts).rhs(1 + q, 2, 1).ravel()
+        solo_mesh = sem.Mesh(N, m.vert_xyz, m.elem_verts, flags=flags)
+        bd = torch.tensor(b, device="cuda")
+        x = torch.zeros_like(bd)
+        res = sem.sem_cg_solve(solo_mesh.handle, bd, x, opts)
+        assert res["status"] == sem.SEM_OK, res
+        want.append((res, x.cpu().numpy(), N, m, b))
+        solo_mesh.close()
+        mesh = sem.Mesh(N, m.vert_xyz, m.elem_verts, flags=flags)
+        assert sem.sem_mesh_info(mesh.handle) == (mesh.n, mesh.info["n_glob"], mesh.info["n_seg"])
+        with pytest.raises(sem.SemError):
+            sem.sem_server_submit_mesh(srv, mesh, b[:-1], opts)  # wrong size: the caller keeps the mesh
+        assert mesh.handle is not None
+        tickets.append(sem.sem_server_submit_mesh(srv, mesh, b, opts))
+        assert mesh.handle is None
+        tickets.append(sem.sem_server_submit(srv, 5, m.vert_xyz, m.elem_verts, (1, 1, 1), _opts(sem, 2)))
+    results = _drain(sem, srv, tickets)
+    sem.sem_server_destroy(srv)
+    for (res, x_solo, N, m, b), t in zip(want, tickets[0::2]):
+        got, x = results[t]
+        assert got["status"] == sem.SEM_OK and got["cg"]["iters"] == res["iters"], (got, res)
+        np.testing.assert_array_equal(x, x_solo)
+    res, x_solo, N, m, b = want[0]
+    prob = so.SemProblem(N, m.vert_xyz, m.elem_verts)
+    bb = b.reshape(prob.shape())
+    r = bb - prob.ax(x_solo.reshape(prob.shape()))
+    assert np.sqrt(so.glsc3(r, r, prob.c) / so.glsc3(bb, bb, prob.c)) <= 1e-9 * (1 + 1e-3)
+    # a server destroyed with prebuilt meshes still queued releases them
+    srv = sem.sem_server_create(8 << 30, 1)
+    m = BoxMesh(3, 3, 3, jitter=0.1, seed=80)
+    b = so.SemProblem(5, m.vert_xyz, m.elem_verts).rhs(1, 1, 1).ravel()
+    for _ in range(4):
+        sem.sem_server_submit_mesh(srv, sem.Mesh(5, m.vert_xyz, m.elem_verts, flags=0), b, _opts(sem, 2))
+    sem.sem_server_destroy(srv)
+    torch.cuda.synchronize()
