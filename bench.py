@@ -656,12 +656,13 @@ def run_solve(args):
                       "iterations": res["iters"], "outer_iterations": res["outer_iters"],
                       "status": sem.sem_status_string(res["status"]), "solver_rel_res": res["rel_res"],
                       "true_rel_res": rel, "max_err_vs_sine": err}
-    out = {"metric": "CG time to 1e-10 (s)", "value": runs["mixed_otf"]["seconds"], "unit": "s",
+    out = {"metric": "CG time to 1e-10 (s)", "value": runs["mixed_reliable"]["seconds"], "unit": "s",
            "higher_is_better": False, "n_gpus": 1, "dtype": "f64 (outer) / f32 (inner)", "data": "synthetic",
            "config": {"workload": f"{nel}^3 hexahedra on [0,1]^3, jitter +-0.15h (seed 2), N={NORD}, "
                                   f"{n} local points, sine right-hand side, rtol 1e-10",
                       "inner_rtol": args.inner_rtol, "mesh_setup_s": setup_s},
-           **runs, "speedup_mixed_vs_fp64": runs["fp64_cg"]["seconds"] / runs["mixed_otf"]["seconds"]}
+           **runs, "speedup_mixed_vs_fp64": runs["fp64_cg"]["seconds"] / runs["mixed_reliable"]["seconds"],
+           "speedup_restarted_vs_fp64": runs["fp64_cg"]["seconds"] / runs["mixed_otf"]["seconds"]}
     print(json.dumps(out))
     mesh.close()
 

@@ -279,7 +279,10 @@ sem_status sem_cg_solve(sem_mesh mesh, const double* b_dev, double* x_dev, const
  *  sem_cg_create   allocates work vectors and device scalars (FP64, non-mixed opts only);
  *  sem_cg_start    r = b - A x0, z, rho; async;
  *  sem_cg_iterate  enqueues k iterations (a captured graph when opts.use_graph);
- *                  iterations after convergence are no-ops; async;
+ *                  iterations after convergence are no-ops; async; when they have run,
+ *                  x_dev holds the iterate of the last one (with opts.f64_arith the
+ *                  operator makes each x update one iteration late, and the call ends
+ *                  with the pending one);
  *  sem_cg_query    synchronises `stream` and reports iterations, residual, status;
  *  sem_cg_destroy  frees the handle. x_dev passed to sem_cg_start is updated in place
  *  and must stay valid until the last sem_cg_iterate has completed. */

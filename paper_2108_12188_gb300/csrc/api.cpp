@@ -768,23 +768,46 @@ sem_status cg_start(sem_cg c, const void* b, void* x, bool x0_is_zero, cudaStrea
   return SEM_OK;
 }
 
-// One iteration of Algorithm 1: [p = z + beta p; w = A_L p; interior <p,w>] -> [QQ^T, mask,
-// boundary <p,w>, alpha] -> [x, r, z updates, <r,z,c>, <r,r,c>, beta, stop test].
-sem_status cg_enqueue_iteration(sem_cg c, cudaStream_t s) {
-  sem_mesh m = c->m;
+// The operator's CG-mode launch: p = z + beta p (fused_cg: also the deferred x += alpha p,
+// with z = M^-1 r formed from r), w = A_L p, partials of <p, w>.
+AxLaunch cg_ax_launch(sem_cg c) {
   AxLaunch a{};
   a.w = c->w;
   a.z = c->z;
   a.p = c->p;
+  if (fused_cg(c->prec)) {
+    a.r = c->r;
+    a.minv = minv_of(c);
+    a.x = c->x;
+  }
   a.st = c->st;
   a.partials = c->ax_part;
   a.grid_out = &c->ax_blocks;
-  SEM_TRY(launch_ax_any(m, c->prec, c->variant, true, a, s));
-  SEM_TRY(launch_dssum_cg(data_prec(c->prec), m->gs, c->w, c->p, c->st, c->ax_part,
-                          c->ax_blocks, c->gs_part, s));
-  SEM_TRY(launch_cg_update(data_prec(c->prec), m->n, c->x, c->p, c->r, c->w, c->z, minv_of(c), m->mult, m->ctab, c->st,
-                           c->upd_part, s));
-  return SEM_OK;
+  return a;
+}
+
+sem_status cg_enqueue_gs(sem_cg c, cudaStream_t s) {
+  return launch_dssum_cg(data_prec(c->prec), c->m->gs, c->w, whole_dot(c->prec) ? nullptr : c->p, c->st, c->ax_part,
+                         c->ax_blocks, c->gs_part, s);
+}
+
+sem_status cg_enqueue_update(sem_cg c, cudaStream_t s) {
+  return launch_cg_update(data_prec(c->prec), fused_cg(c->prec), c->m->n, c->x, c->p, c->r, c->w, c->z, minv_of(c),
+                          c->m->mult, c->m->ctab, c->st, c->upd_part, s);
+}
+
+// fused_cg: the x update of the last iteration run (a no-op if there is none)
+sem_status cg_enqueue_flush(sem_cg c, cudaStream_t s) {
+  if (!fused_cg(c->prec)) return SEM_OK;
+  return launch_cg_flush(data_prec(c->prec), c->m->n, c->x, c->p, c->st, s);
+}
+
+// One iteration of Algorithm 1: [p = z + beta p; w = A_L p; <p,w> partials] -> [QQ^T, mask,
+// (boundary <p,w>), alpha] -> [r, z (and x) updates, <r,z,c>, <r,r,c>, beta, stop test].
+sem_status cg_enqueue_iteration(sem_cg c, cudaStream_t s) {
+  SEM_TRY(launch_ax_any(c->m, c->prec, c->variant, true, cg_ax_launch(c), s));
+  SEM_TRY(cg_enqueue_gs(c, s));
+  return cg_enqueue_update(c, s);
 }
 
 sem_status cg_iterate(sem_cg c, int k, cudaStream_t s) {
@@ -793,7 +816,7 @@ sem_status cg_iterate(sem_cg c, int k, cudaStream_t s) {
   note_stream(c->m, s);
   if (!c->use_graph) {
     for (int q = 0; q < k; ++q) SEM_TRY(cg_enqueue_iteration(c, s));
-    return SEM_OK;
+    return cg_enqueue_flush(c, s);
   }
   if (!c->exec || c->exec_k != k || c->exec_x != c->x) {
     if (c->exec) {
@@ -804,6 +827,7 @@ sem_status cg_iterate(sem_cg c, int k, cudaStream_t s) {
     t_capturing = true;
     sem_status st = SEM_OK;
     for (int q = 0; q < k && st == SEM_OK; ++q) st = cg_enqueue_iteration(c, c->cap);
+    if (st == SEM_OK) st = cg_enqueue_flush(c, c->cap);
     t_capturing = false;
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(c->cap, &g);
@@ -822,7 +846,7 @@ sem_status cg_iterate(sem_cg c, int k, cudaStream_t s) {
     c->exec_x = c->x;
   }
   SEM_CUDA_TRY(cudaGraphLaunch(c->exec, s));
-  count_launch(3 * k);
+  count_launch(3 * k + (fused_cg(c->prec) ? 1 : 0));
   return SEM_OK;
 }
 
@@ -1038,22 +1062,12 @@ extern "C" sem_status sem_cg_iterate_timed(sem_cg c, int k, double* total_ms, do
     sem_status st = SEM_OK;
     cudaEventRecord(ev[0], s);
     for (int q = 0; q < k && st == SEM_OK; ++q) {
-      AxLaunch a{};
-      a.w = c->w;
-      a.z = c->z;
-      a.p = c->p;
-      a.st = c->st;
-      a.partials = c->ax_part;
-      a.grid_out = &c->ax_blocks;
-      st = launch_ax_any(m, c->prec, c->variant, true, a, s);
+      st = launch_ax_any(m, c->prec, c->variant, true, cg_ax_launch(c), s);
       cudaEventRecord(ev[3 * q + 1], s);
-      if (st == SEM_OK)
-        st = launch_dssum_cg(data_prec(c->prec), m->gs, c->w, c->p, c->st, c->ax_part,
-                             c->ax_blocks, c->gs_part, s);
+      if (st == SEM_OK) st = cg_enqueue_gs(c, s);
       cudaEventRecord(ev[3 * q + 2], s);
-      if (st == SEM_OK)
-        st = launch_cg_update(data_prec(c->prec), m->n, c->x, c->p, c->r, c->w, c->z, minv_of(c), m->mult, m->ctab, c->st,
-                              c->upd_part, s);
+      if (st == SEM_OK) st = cg_enqueue_update(c, s);
+      if (st == SEM_OK && q == k - 1) st = cg_enqueue_flush(c, s);  // inside the timed region
       cudaEventRecord(ev[3 * q + 3], s);
     }
     cudaError_t r = cudaStreamSynchronize(s);

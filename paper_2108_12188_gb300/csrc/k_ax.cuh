@@ -101,20 +101,30 @@ __host__ __device__ constexpr size_t ax_smem_bytes() {
 // Work of a group of EPB elements; thread t of an element takes i-row (j, k) = (t % NP, t / NP),
 // j-line (i, k) = (t % NP, t / NP) and k-column (i, j) = (t % NP, t / NP), each a line of NP
 // values that it contracts with D or D^T in registers (even/odd split, see EoMat):
-//   0  column of u (or of p = z + beta p) -> registers and buffer A
+//   0  column of u (or of p = z + beta p) -> registers and buffer A. FP32 CG mode also makes
+//      the previous iteration's x update here, x += alpha p (alpha is 0 when none is
+//      pending), and forms z = M^-1 r from r and M^-1 instead of reading a stored z: the
+//      update kernel then neither reads nor writes x and writes no z (12 of its 33 bytes
+//      per point), and this kernel, bound by instruction issue, absorbs the extra loads
 //   1  i-rows of A -> ur into B;               column -> ut (registers)
 //   2  j-lines of A -> us, in place in A
 //   3  column: (vr, vs, vt) = G (ur, us, ut); vr, vs in place in B, A; vt in registers
 //   4  i-rows of B -> D^T vr in place;  j-lines of A -> D^T vs in place;  column -> D^T vt
-//   5  column: w = the three sums; stored (CG mode: p.w added over interior points)
+//   5  column: w = the three sums; stored (CG mode: p.w added, see kWholeDot)
 // with a block barrier between phases. Every thread reads and writes only its own line in
 // the in-place phases.
 template <int NP, typename T, int GEO, bool CG, int EPB>
 __global__ void __launch_bounds__(NP * NP * EPB)
     k_ax(const __grid_constant__ GllParam<NP, T> tab, int64_t E, const T* __restrict__ u, T* __restrict__ w,
          const T* __restrict__ G, const T* __restrict__ coef, const T* __restrict__ scale, const T* __restrict__ z,
-         T* __restrict__ p, CgScalars* __restrict__ st, double* __restrict__ partials, int* __restrict__ err) {
+         T* __restrict__ p, const T* __restrict__ r, const T* __restrict__ minv, T* __restrict__ x,
+         CgScalars* __restrict__ st, double* __restrict__ partials, int* __restrict__ err) {
   constexpr bool OTF = GEO != 0;
+  // CG mode: FP32 adds p.w over every point (the gather-scatter then reads no p); FP64 over
+  // the element interior only (the boundary part is added in the gather-scatter, one copy
+  // per shared node), which keeps the FP64 pipe to one FMA per interior point
+  constexpr bool kWholeDot = sizeof(T) == 4;
+  constexpr bool kFused = sizeof(T) == 4;  // the fused CG prologue of phase 0
   constexpr int NP2 = NP * NP, P = NP2 * NP, GS = ax_gstride<NP, T>(), SZ = Stage<NP>::kSize;
   constexpr size_t kG = OTF ? 0 : static_cast<size_t>(EPB) * GS;
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -126,10 +136,11 @@ __global__ void __launch_bounds__(NP * NP * EPB)
                   ~uintptr_t(7)));
   __shared__ double sRed[32];
 
-  T beta = T(0);
+  T beta = T(0), alpha = T(0);
   if constexpr (CG) {
     if (st->done) return;  // uniform over the grid: set by an earlier launch
     beta = static_cast<T>(st->beta);
+    alpha = static_cast<T>(st->alpha);
   }
   const int64_t n_groups = (E + EPB - 1) / EPB;
   constexpr unsigned kElemBytes = static_cast<unsigned>(GS * sizeof(T));
@@ -158,19 +169,44 @@ __global__ void __launch_bounds__(NP * NP * EPB)
     const int64_t base = e * P + tid;
     // phase 0: the column of the input
     T rU[NP];
+    if constexpr (CG && kFused) {
+      // every load of the column first, so that they are all in flight together
+      T po[NP], rq[NP], xq[NP], mq[NP];
 #pragma unroll
-    for (int k = 0; k < NP; ++k) {
-      T val = T(0);
-      if (valid) {
-        if constexpr (CG) {
-          val = z[base + k * NP2] + beta * p[base + k * NP2];
-          p[base + k * NP2] = val;
-        } else {
-          val = u[base + k * NP2];
-        }
+      for (int k = 0; k < NP; ++k) {
+        const int64_t q = base + k * NP2;
+        po[k] = valid ? p[q] : T(0);
+        rq[k] = valid ? r[q] : T(0);
+        xq[k] = valid ? x[q] : T(0);
+        mq[k] = valid && minv ? minv[q] : T(1);
       }
-      rU[k] = val;
-      sA[Stage<NP>::at(i, j, k)] = val;
+#pragma unroll
+      for (int k = 0; k < NP; ++k) {
+        const int64_t q = base + k * NP2;
+        const T zq = minv ? mq[k] * rq[k] : rq[k];
+        const T val = zq + beta * po[k];
+        if (valid) {
+          x[q] = xq[k] + alpha * po[k];
+          p[q] = val;
+        }
+        rU[k] = val;
+        sA[Stage<NP>::at(i, j, k)] = val;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < NP; ++k) {
+        T val = T(0);
+        if (valid) {
+          if constexpr (CG) {
+            val = z[base + k * NP2] + beta * p[base + k * NP2];
+            p[base + k * NP2] = val;
+          } else {
+            val = u[base + k * NP2];
+          }
+        }
+        rU[k] = val;
+        sA[Stage<NP>::at(i, j, k)] = val;
+      }
     }
     __syncthreads();
 
@@ -321,7 +357,7 @@ __global__ void __launch_bounds__(NP * NP * EPB)
       if (valid) w[base + k * NP2] = acc;
       if constexpr (CG) {
         const bool interior = i > 0 && i < NP - 1 && j > 0 && j < NP - 1 && k > 0 && k < NP - 1;
-        if (valid && interior) dot.add(rU[k], acc);
+        if (valid && (kWholeDot || interior)) dot.add(rU[k], acc);
       }
     }
     __syncthreads();  // the staging buffers are free for the next group
@@ -359,7 +395,8 @@ sem_status launch_ax_t(int N, const AxLaunch& a, cudaStream_t s) {
   k_ax<NP, T, GEO, CG, EPB><<<grid, NP * NP * EPB, ax_smem_bytes<NP, T, GEO, EPB>(), s>>>(
       tab, a.E, static_cast<const T*>(a.u), static_cast<T*>(a.w), static_cast<const T*>(a.G),
       static_cast<const T*>(a.coef), static_cast<const T*>(a.scale), static_cast<const T*>(a.z),
-      static_cast<T*>(a.p), a.st, a.partials, a.err);
+      static_cast<T*>(a.p), static_cast<const T*>(a.r), static_cast<const T*>(a.minv), static_cast<T*>(a.x), a.st,
+      a.partials, a.err);
   count_launch();
   SEM_CUDA_TRY(cudaGetLastError());
   return SEM_OK;

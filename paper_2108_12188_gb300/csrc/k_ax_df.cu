@@ -18,8 +18,10 @@
 // do not wait on factor loads (bounded mbarrier waits; a timeout sets SEM_ERR_TIMEOUT). The factors are FP64 values, split into float pairs by
 // integer operations, or (SEM_MESH_F64X_STORED) float pairs already, in the same 8 bytes.
 //
-// CG mode (Algorithm 1 steps 5-6): p = z + beta p in FP64 (one FMA per point), stored, and
-// the element-interior part of <p, w> accumulated in double-float.
+// CG mode (Algorithm 1 steps 5-6, fused_cg): the previous iteration's x += alpha p, z = M^-1 r
+// and p = z + beta p in FP64 (on the FP64 pipe, which this kernel otherwise leaves idle), and
+// <p, w> accumulated in double-float over every local point of the unassembled w (equal to
+// <p, QQ^T w, c> because p has one value per global node; the gather-scatter reads no p).
 #include "k_ax.cuh"
 #include "k_df.cuh"
 #include "k_tma.cuh"
@@ -126,14 +128,15 @@ __device__ __forceinline__ void prefetch_factors(double* sG, const double* G, in
 
 // Phases of a group, as in k_ax (barrier between phases; each thread owns one i-row, one
 // j-line and one k-column of its element in the in-place phases):
-//   0 column of u (or p = z + beta p) -> registers and A;  1 i-rows of A -> ur into B, column -> ut;
+//   0 column of u (or x += alpha p, p = M^-1 r + beta p) -> registers and A;  1 i-rows of A -> ur into B, column -> ut;
 //   2 j-lines of A -> us in place;  3 column: G (ur, us, ut);  4 D^T on rows, lines, column;
 //   5 column: w = sum of the three, converted to FP64 and stored.
 template <int NP, bool CG, bool PAIRS>
 __global__ void __launch_bounds__(NP * NP * ax_epb<NP>(), (CG && NP == 8) ? 4 : 1)
     k_ax_df(const __grid_constant__ DfTab<NP> tab, int64_t E, const double* __restrict__ u, double* __restrict__ w,
-            const double* __restrict__ G, const double* __restrict__ z, double* __restrict__ p,
-            CgScalars* __restrict__ st, double* __restrict__ partials, int* __restrict__ err) {
+            const double* __restrict__ G, const double* __restrict__ r, double* __restrict__ p,
+            const double* __restrict__ minv, double* __restrict__ x, CgScalars* __restrict__ st,
+            double* __restrict__ partials, int* __restrict__ err) {
   constexpr int NP2 = NP * NP, P = NP2 * NP, EPB = ax_epb<NP>(), SZ = Stage<NP>::kSize;
   extern __shared__ __align__(128) unsigned char smem[];
   constexpr int GST = df_gst<NP>();
@@ -144,10 +147,11 @@ __global__ void __launch_bounds__(NP * NP * ax_epb<NP>(), (CG && NP == 8) ? 4 : 
   uint64_t* bar = reinterpret_cast<uint64_t*>(sB0 + EPB * SZ);
   __shared__ double sRed[32];
 
-  double beta = 0.0;
+  double beta = 0.0, alpha = 0.0;
   if constexpr (CG) {
     if (st->done) return;
     beta = st->beta;
+    alpha = st->alpha;
   }
   const int64_t n_groups = (E + EPB - 1) / EPB;
   if (threadIdx.x == 0) {
@@ -174,8 +178,12 @@ __global__ void __launch_bounds__(NP * NP * ax_epb<NP>(), (CG && NP == 8) ? 4 : 
       double val = 0.0;
       if (valid) {
         if constexpr (CG) {
-          val = fma(beta, p[base + k * NP2], z[base + k * NP2]);
-          p[base + k * NP2] = val;
+          const int64_t q = base + k * NP2;
+          const double po = p[q], xo = x[q], rr = r[q], mm = minv ? minv[q] : 1.0;
+          const double zq = minv ? mm * rr : rr;
+          val = fma(beta, po, zq);
+          x[q] = fma(alpha, po, xo);
+          p[q] = val;
         } else {
           val = u[base + k * NP2];
         }
@@ -295,8 +303,7 @@ __global__ void __launch_bounds__(NP * NP * ax_epb<NP>(), (CG && NP == 8) ? 4 : 
       const df2 acc = df_norm(df_add_nr(df_add_nr(sB[at], sA[at]), rW[k]));
       if (valid) w[base + k * NP2] = df_to_double(acc);
       if constexpr (CG) {
-        const bool interior = i > 0 && i < NP - 1 && j > 0 && j < NP - 1 && k > 0 && k < NP - 1;
-        if (valid && interior) df_fma_acc(dot, rU[k].h, rU[k].l, acc.h, acc.l);
+        if (valid) df_fma_acc(dot, rU[k].h, rU[k].l, acc.h, acc.l);
       }
     }
     __syncthreads();  // the staging buffers are free for the next group
@@ -326,7 +333,8 @@ sem_status launch_df_t(int N, const AxLaunch& a, cudaStream_t s) {
   if (a.grid_out) *a.grid_out = grid;
   k_ax_df<NP, CG, PAIRS><<<grid, NP * NP * EPB, smem, s>>>(make_df_tab<NP>(N), a.E, static_cast<const double*>(a.u),
                                                      static_cast<double*>(a.w), static_cast<const double*>(a.G),
-                                                     static_cast<const double*>(a.z), static_cast<double*>(a.p),
+                                                     static_cast<const double*>(a.r), static_cast<double*>(a.p),
+                                                     static_cast<const double*>(a.minv), static_cast<double*>(a.x),
                                                      a.st, a.partials, a.err);
   count_launch();
   SEM_CUDA_TRY(cudaGetLastError());

@@ -123,7 +123,9 @@ struct Vec16<float> {
 
 // Algorithm 1 steps 9-13 with z = M^-1 r. Each thread takes 16 bytes of every vector per
 // step (vector loads and stores); the last n mod (16 / sizeof(T)) points are done singly.
-template <typename T>
+// FUSED: the operator's CG prologue makes x += alpha p (one iteration later) and recomputes
+// z = M^-1 r, so this kernel leaves x alone and stores no z (z is formed for the dots only).
+template <typename T, bool FUSED>
 __global__ void k_cg_update(int64_t n, T* __restrict__ x, const T* __restrict__ p, T* __restrict__ r,
                             const T* __restrict__ w, T* __restrict__ z, const T* __restrict__ minv,
                             const uint8_t* __restrict__ mult, const double* __restrict__ ctab, CgScalars* st,
@@ -147,7 +149,7 @@ __global__ void k_cg_update(int64_t n, T* __restrict__ x, const T* __restrict__ 
     __syncthreads();
     df2 rz{0.f, 0.f}, rr{0.f, 0.f};
     auto point = [&](T& xi, T pi, T& ri, T wi, T& zi, T mi, unsigned m) {
-      xi += alpha * pi;
+      if constexpr (!FUSED) xi += alpha * pi;
       ri = ri - alpha * wi;
       zi = minv ? mi * ri : ri;
       const df2 r2 = df_from_double(ri), z2 = df_from_double(zi), c2 = sC[m];
@@ -157,29 +159,37 @@ __global__ void k_cg_update(int64_t n, T* __restrict__ x, const T* __restrict__ 
       df_fma_acc(rr, ch, cl, r2.h, r2.l);
     };
     for (int64_t q = t0; q < nv; q += stride) {
-      VT xv = reinterpret_cast<const VT*>(x)[q], rv = reinterpret_cast<const VT*>(r)[q], zv;
-      const VT pv = reinterpret_cast<const VT*>(p)[q], wv = reinterpret_cast<const VT*>(w)[q];
+      VT xv{}, rv = reinterpret_cast<const VT*>(r)[q], zv, pv{};
+      if constexpr (!FUSED) {
+        xv = reinterpret_cast<const VT*>(x)[q];
+        pv = reinterpret_cast<const VT*>(p)[q];
+      }
+      const VT wv = reinterpret_cast<const VT*>(w)[q];
       const VT mv = minv ? reinterpret_cast<const VT*>(minv)[q] : VT{};
       const MT cv = reinterpret_cast<const MT*>(mult)[q];
       point(xv.x, pv.x, rv.x, wv.x, zv.x, mv.x, cv.x);
       point(xv.y, pv.y, rv.y, wv.y, zv.y, mv.y, cv.y);
-      reinterpret_cast<VT*>(x)[q] = xv;
       reinterpret_cast<VT*>(r)[q] = rv;
-      reinterpret_cast<VT*>(z)[q] = zv;
+      if constexpr (!FUSED) {
+        reinterpret_cast<VT*>(x)[q] = xv;
+        reinterpret_cast<VT*>(z)[q] = zv;
+      }
     }
     for (int64_t i = nv * V + t0; i < n; i += stride) {
-      T xi = x[i], ri = r[i], zi;
-      point(xi, p[i], ri, w[i], zi, minv ? minv[i] : T(0), mult[i]);
-      x[i] = xi;
+      T xi = FUSED ? T(0) : x[i], ri = r[i], zi;
+      point(xi, FUSED ? T(0) : p[i], ri, w[i], zi, minv ? minv[i] : T(0), mult[i]);
       r[i] = ri;
-      z[i] = zi;
+      if constexpr (!FUSED) {
+        x[i] = xi;
+        z[i] = zi;
+      }
     }
     v[0] = block_sum(static_cast<double>(rz.h) + static_cast<double>(rz.l), sRed);
     v[1] = block_sum(static_cast<double>(rr.h) + static_cast<double>(rr.l), sRed);
   } else {
     DotAcc<T> rz, rr;
     auto point = [&](T& xi, T pi, T& ri, T wi, T& zi, T mi, unsigned m) {
-      xi += alpha * pi;
+      if constexpr (!FUSED) xi += alpha * pi;
       ri = ri - alpha * wi;
       zi = minv ? mi * ri : ri;
       const T c = m == 1u ? T(1) : static_cast<T>(__ldg(ctab + m));
@@ -187,24 +197,32 @@ __global__ void k_cg_update(int64_t n, T* __restrict__ x, const T* __restrict__ 
       rr.add(ri, c * ri);
     };
     for (int64_t q = t0; q < nv; q += stride) {
-      VT xv = reinterpret_cast<const VT*>(x)[q], rv = reinterpret_cast<const VT*>(r)[q], zv;
-      const VT pv = reinterpret_cast<const VT*>(p)[q], wv = reinterpret_cast<const VT*>(w)[q];
+      VT xv{}, rv = reinterpret_cast<const VT*>(r)[q], zv, pv{};
+      if constexpr (!FUSED) {
+        xv = reinterpret_cast<const VT*>(x)[q];
+        pv = reinterpret_cast<const VT*>(p)[q];
+      }
+      const VT wv = reinterpret_cast<const VT*>(w)[q];
       const VT mv = minv ? reinterpret_cast<const VT*>(minv)[q] : VT{};
       const MT cv = reinterpret_cast<const MT*>(mult)[q];
       point(xv.x, pv.x, rv.x, wv.x, zv.x, mv.x, cv.x);
       point(xv.y, pv.y, rv.y, wv.y, zv.y, mv.y, cv.y);
       point(xv.z, pv.z, rv.z, wv.z, zv.z, mv.z, cv.z);
       point(xv.w, pv.w, rv.w, wv.w, zv.w, mv.w, cv.w);
-      reinterpret_cast<VT*>(x)[q] = xv;
       reinterpret_cast<VT*>(r)[q] = rv;
-      reinterpret_cast<VT*>(z)[q] = zv;
+      if constexpr (!FUSED) {
+        reinterpret_cast<VT*>(x)[q] = xv;
+        reinterpret_cast<VT*>(z)[q] = zv;
+      }
     }
     for (int64_t i = nv * V + t0; i < n; i += stride) {
-      T xi = x[i], ri = r[i], zi;
-      point(xi, p[i], ri, w[i], zi, minv ? minv[i] : T(0), mult[i]);
-      x[i] = xi;
+      T xi = FUSED ? T(0) : x[i], ri = r[i], zi;
+      point(xi, FUSED ? T(0) : p[i], ri, w[i], zi, minv ? minv[i] : T(0), mult[i]);
       r[i] = ri;
-      z[i] = zi;
+      if constexpr (!FUSED) {
+        x[i] = xi;
+        z[i] = zi;
+      }
     }
     v[0] = block_sum(rz.value(), sRed);
     v[1] = block_sum(rr.value(), sRed);
@@ -268,20 +286,67 @@ sem_status launch_cg_init(sem_prec prec, int64_t n, const void* b, const void* a
   return SEM_OK;
 }
 
-sem_status launch_cg_update(sem_prec prec, int64_t n, void* x, const void* p, void* r, const void* w, void* z,
-                            const void* minv, const uint8_t* mult, const double* ctab, CgScalars* st,
+sem_status launch_cg_update(sem_prec prec, bool fused, int64_t n, void* x, const void* p, void* r, const void* w,
+                            void* z, const void* minv, const uint8_t* mult, const double* ctab, CgScalars* st,
                             double* partials, cudaStream_t s) {
   const int grid = vec_grid(n);
+  if (prec == SEM_F64) {
+    auto* xd = static_cast<double*>(x);
+    auto* pd = static_cast<const double*>(p);
+    auto* rd = static_cast<double*>(r);
+    auto* wd = static_cast<const double*>(w);
+    auto* zd = static_cast<double*>(z);
+    auto* md = static_cast<const double*>(minv);
+    if (fused)
+      k_cg_update<double, true><<<grid, kThreads, 0, s>>>(n, xd, pd, rd, wd, zd, md, mult, ctab, st, partials);
+    else
+      k_cg_update<double, false><<<grid, kThreads, 0, s>>>(n, xd, pd, rd, wd, zd, md, mult, ctab, st, partials);
+  } else {
+    if (!fused) return fail(SEM_ERR_UNSUPPORTED, "the FP32 CG update runs with the fused operator prologue only");
+    k_cg_update<float, true><<<grid, kThreads, 0, s>>>(n, static_cast<float*>(x), static_cast<const float*>(p),
+                                                       static_cast<float*>(r), static_cast<const float*>(w),
+                                                       static_cast<float*>(z), static_cast<const float*>(minv), mult,
+                                                       ctab, st, partials);
+  }
+  count_launch();
+  SEM_CUDA_TRY(cudaGetLastError());
+  return SEM_OK;
+}
+
+namespace {
+
+// x += alpha p: the update that the fused CG prologue defers to the next iteration, made
+// when the iterations stop. The last block sets alpha to 0, so that a later prologue (more
+// iterations on the same state) adds nothing twice; alpha == 0 means nothing is pending.
+template <typename T>
+__global__ void k_cg_flush(int64_t n, T* __restrict__ x, const T* __restrict__ p, CgScalars* st) {
+  const double a64 = st->alpha;  // every block reads alpha before the last one clears it
+  if (a64 == 0.0) return;
+  const T a = static_cast<T>(a64);
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    x[i] += a * p[i];
+  __shared__ bool last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned int t = atomicAdd(&st->ticket[4], 1u);
+    last = (t == gridDim.x - 1);
+    if (last) {
+      st->ticket[4] = 0u;
+      st->alpha = 0.0;
+    }
+  }
+}
+
+}  // namespace
+
+sem_status launch_cg_flush(sem_prec prec, int64_t n, void* x, const void* p, CgScalars* st, cudaStream_t s) {
+  const int grid = vec_grid(n);
   if (prec == SEM_F64)
-    k_cg_update<double><<<grid, kThreads, 0, s>>>(n, static_cast<double*>(x), static_cast<const double*>(p),
-                                                  static_cast<double*>(r), static_cast<const double*>(w),
-                                                  static_cast<double*>(z), static_cast<const double*>(minv), mult,
-                                                  ctab, st, partials);
+    k_cg_flush<double><<<grid, kThreads, 0, s>>>(n, static_cast<double*>(x), static_cast<const double*>(p), st);
   else
-    k_cg_update<float><<<grid, kThreads, 0, s>>>(n, static_cast<float*>(x), static_cast<const float*>(p),
-                                                 static_cast<float*>(r), static_cast<const float*>(w),
-                                                 static_cast<float*>(z), static_cast<const float*>(minv), mult, ctab,
-                                                 st, partials);
+    k_cg_flush<float><<<grid, kThreads, 0, s>>>(n, static_cast<float*>(x), static_cast<const float*>(p), st);
   count_launch();
   SEM_CUDA_TRY(cudaGetLastError());
   return SEM_OK;

@@ -97,11 +97,14 @@ __global__ void k_dssum(const GsPlan g, T* __restrict__ u, int apply_mask) {
   }
 }
 
-// CG step 7 + the boundary part of <p, w, c>: after the sum, all copies of a segment hold
-// the same w and the same p, and their weights c = 1/multiplicity add up to one, so the
-// segment contributes p * w once. The last block adds the Ax kernel's element-interior
-// partials, forms <p, w, c> and alpha = rho / <p, w, c> (Algorithm 1 step 8).
-template <typename T>
+// CG step 7. DOT: also the boundary part of <p, w, c>: after the sum, all copies of a
+// segment hold the same w and the same p, and their weights c = 1/multiplicity add up to
+// one, so the segment contributes p * w once. Without DOT the operator has already formed
+// the whole product over the unassembled w (sum over local points of p_i (A_L p)_i equals
+// <p, QQ^T A_L p, c> because p has one value per global node and is 0 on Dirichlet nodes).
+// The last block adds the operator's partials (and its own), forms <p, w, c> and
+// alpha = rho / <p, w, c> (Algorithm 1 step 8).
+template <typename T, bool DOT>
 __global__ void k_dssum_cg(const GsPlan g, T* __restrict__ w, const T* __restrict__ p, CgScalars* __restrict__ st,
                            const double* __restrict__ ax_partials, int ax_blocks, double* __restrict__ partials) {
   __shared__ double sRed[kThreads / 32];
@@ -111,11 +114,12 @@ __global__ void k_dssum_cg(const GsPlan g, T* __restrict__ w, const T* __restric
   DotAcc<T> dot;
   auto body = [&](const auto& ix, bool masked) {
     constexpr int W = std::extent<std::remove_reference_t<decltype(ix)>>::value;
-    const T pf = p[ix[0]];
+    T pf = T(0);
+    if constexpr (DOT) pf = p[ix[0]];
     T s = seg_sum<W>(w, ix);
     if (masked) s = T(0);
     seg_store<W>(w, ix, s);
-    dot.add(pf, s);
+    if constexpr (DOT) dot.add(pf, s);
   };
   for_class<2>(g, 1, t0, stride, body);
   for_class<4>(g, 2, t0, stride, body);
@@ -128,7 +132,7 @@ __global__ void k_dssum_cg(const GsPlan g, T* __restrict__ w, const T* __restric
     for (int o = o0 + 1; o < o1; ++o) s += w[g.xidx[o]];
     if (g.xmsk[x]) s = T(0);
     for (int o = o0; o < o1; ++o) w[g.xidx[o]] = s;
-    dot.add(p[first], s);
+    if constexpr (DOT) dot.add(p[first], s);
   }
   const double v[1] = {block_sum(dot.value(), sRed)};
   if (publish_partials<1>(v, partials, &st->ticket[0])) {
@@ -140,6 +144,7 @@ __global__ void k_dssum_cg(const GsPlan g, T* __restrict__ w, const T* __restric
       if (!(pw > 0.0) || !isfinite(pw)) {
         st->status = SEM_ERR_BREAKDOWN;
         st->done = 1;
+        st->alpha = 0.0;  // x is not advanced along this p (fused CG: nothing left to flush)
       } else {
         st->alpha = st->rho / pw;
       }
@@ -191,12 +196,21 @@ sem_status launch_dssum(sem_prec prec, const GsPlan& g, void* u, int apply_mask,
 sem_status launch_dssum_cg(sem_prec prec, const GsPlan& g, void* w, const void* p, CgScalars* st,
                            const double* ax_partials, int ax_blocks, double* partials, cudaStream_t s) {
   const int grid = seg_grid(g.total());
-  if (prec == SEM_F64)
-    k_dssum_cg<double><<<grid, kThreads, 0, s>>>(g, static_cast<double*>(w), static_cast<const double*>(p), st,
-                                                 ax_partials, ax_blocks, partials);
-  else
-    k_dssum_cg<float><<<grid, kThreads, 0, s>>>(g, static_cast<float*>(w), static_cast<const float*>(p), st,
-                                                ax_partials, ax_blocks, partials);
+  if (prec == SEM_F64) {
+    if (p)
+      k_dssum_cg<double, true><<<grid, kThreads, 0, s>>>(g, static_cast<double*>(w), static_cast<const double*>(p),
+                                                         st, ax_partials, ax_blocks, partials);
+    else
+      k_dssum_cg<double, false><<<grid, kThreads, 0, s>>>(g, static_cast<double*>(w), nullptr, st, ax_partials,
+                                                          ax_blocks, partials);
+  } else {
+    if (p)
+      k_dssum_cg<float, true><<<grid, kThreads, 0, s>>>(g, static_cast<float*>(w), static_cast<const float*>(p), st,
+                                                        ax_partials, ax_blocks, partials);
+    else
+      k_dssum_cg<float, false><<<grid, kThreads, 0, s>>>(g, static_cast<float*>(w), nullptr, st, ax_partials,
+                                                         ax_blocks, partials);
+  }
   count_launch();
   SEM_CUDA_TRY(cudaGetLastError());
   return SEM_OK;

@@ -100,7 +100,7 @@ void build_gs_host(const Topology& T, GsHost& out);
 struct CgScalars {
   double rho, alpha, beta, pw, rz, rr, bb, rtol2;
   int iter, max_iter, done, status;  // status: 0 running, SEM_OK converged, else sem_status
-  unsigned int ticket[4];            // last-block-done counters (reset by the last block)
+  unsigned int ticket[5];            // last-block-done counters (reset by the last block)
 };
 
 // Element stride (in elements of the factor type) of the mesh's stored-factor arrays: the six
@@ -190,9 +190,14 @@ struct AxLaunch {
   bool g_pairs;       // SEM_F64X: G holds float pairs (high, low) instead of FP64 values
   const void* coef;   // trilinear coefficients (otf)
   const void* scale;  // per-point w/det J (otf with stored scale)
-  // CG mode (p = z + beta p prologue, interior part of <p, w> in the epilogue)
+  // CG mode (p = z + beta p prologue, <p, w> partials in the epilogue)
   const void* z;
   void* p;
+  // fused CG prologue (FP32 and double-float operators, fused_cg): x += alpha p, the update
+  // deferred from the previous iteration, and z = M^-1 r (minv null: no preconditioner)
+  const void* r;
+  const void* minv;
+  void* x;
   CgScalars* st;
   double* partials;   // [gridDim.x] interior partial dots
   int* grid_out;      // receives gridDim.x used
@@ -232,8 +237,13 @@ sem_status launch_cast(int64_t n, const double* in, float* out, cudaStream_t s);
 
 // gather-scatter (k_gs.cu)
 sem_status launch_dssum(sem_prec prec, const GsPlan& g, void* u, int apply_mask, cudaStream_t s);
-// CG variant: also the boundary part of <p, w, c>; the last block combines it with
-// the Ax kernel's interior partials and sets alpha (or a breakdown status).
+// CG variant: with p, also the boundary part of <p, w, c> (the operator added the interior
+// part); with p == nullptr the operator's partials hold the whole product (whole_dot). The
+// last block combines the partials and sets alpha (or a breakdown status).
+inline bool whole_dot(sem_prec prec) { return prec != SEM_F64; }  // FP32 and double-float operators
+// The same operators take the fused CG prologue (AxLaunch::r, minv, x): the update kernel
+// then skips x and z, and after the last iteration launch_cg_flush adds the pending alpha p.
+inline bool fused_cg(sem_prec prec) { return prec != SEM_F64; }
 sem_status launch_dssum_cg(sem_prec prec, const GsPlan& g, void* w, const void* p, CgScalars* st,
                            const double* ax_partials, int ax_blocks, double* partials, cudaStream_t s);
 // Jacobi: assembled diagonal inverted (0 on Dirichlet nodes) on every element-boundary copy.
@@ -245,9 +255,13 @@ sem_status launch_glsc3(sem_prec prec, int64_t n, const void* a, const void* b, 
 sem_status launch_cg_init(sem_prec prec, int64_t n, const void* b, const void* ax0, void* r, void* z, void* p,
                           const void* minv, const uint8_t* mult, const double* ctab, CgScalars* st, double* partials,
                           cudaStream_t s);
-sem_status launch_cg_update(sem_prec prec, int64_t n, void* x, const void* p, void* r, const void* w, void* z,
-                            const void* minv, const uint8_t* mult, const double* ctab, CgScalars* st,
+// fused (fused_cg): x and z are left to the operator's CG prologue (see AxLaunch::r)
+sem_status launch_cg_update(sem_prec prec, bool fused, int64_t n, void* x, const void* p, void* r, const void* w,
+                            void* z, const void* minv, const uint8_t* mult, const double* ctab, CgScalars* st,
                             double* partials, cudaStream_t s);
+// x += alpha p if an update is pending (alpha != 0), then alpha = 0 (fused CG, at the end of
+// a run of iterations)
+sem_status launch_cg_flush(sem_prec prec, int64_t n, void* x, const void* p, CgScalars* st, cudaStream_t s);
 // Iterative refinement (FP64 outer loop around an FP32 inner solve):
 // r64 = b - w64, r32 = (float) r64, <r,r,c> and <b,b,c> into st (done when converged).
 sem_status launch_ir_residual(int64_t n, const double* b, const double* w, double* r64, float* r32,
