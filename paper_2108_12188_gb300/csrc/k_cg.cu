@@ -122,7 +122,8 @@ struct Vec16<float> {
 };
 
 // Algorithm 1 steps 9-13 with z = M^-1 r. Each thread takes 16 bytes of every vector per
-// step (vector loads and stores); the last n mod (16 / sizeof(T)) points are done singly.
+// step (vector loads and stores; FUSED: two steps at a time with all their loads issued
+// first); the last n mod (16 / sizeof(T)) points are done singly.
 // FUSED: the operator's CG prologue makes x += alpha p (one iteration later) and recomputes
 // z = M^-1 r, so this kernel leaves x alone and stores no z (z is formed for the dots only).
 template <typename T, bool FUSED>
@@ -139,6 +140,66 @@ __global__ void k_cg_update(int64_t n, T* __restrict__ x, const T* __restrict__ 
   const int64_t t0 = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   const int64_t nv = n / V;
+  struct Pack {
+    VT x, r, p, w, m;
+    MT c;
+  };
+  auto load = [&](int64_t q, Pack& k) {
+    k.r = reinterpret_cast<const VT*>(r)[q];
+    k.w = reinterpret_cast<const VT*>(w)[q];
+    k.m = minv ? reinterpret_cast<const VT*>(minv)[q] : VT{};
+    k.c = reinterpret_cast<const MT*>(mult)[q];
+    if constexpr (!FUSED) {
+      k.x = reinterpret_cast<const VT*>(x)[q];
+      k.p = reinterpret_cast<const VT*>(p)[q];
+    } else {
+      k.x = VT{};
+      k.p = VT{};
+    }
+  };
+  // point(x, p, r, w, z, minv, multiplicity) on every lane of step q, then the stores
+  auto finish = [&](int64_t q, Pack& k, auto&& point) {
+    VT zv;
+    T* xs = reinterpret_cast<T*>(&k.x);
+    T* rs = reinterpret_cast<T*>(&k.r);
+    T* zs = reinterpret_cast<T*>(&zv);
+    const T* ps = reinterpret_cast<const T*>(&k.p);
+    const T* ws = reinterpret_cast<const T*>(&k.w);
+    const T* ms = reinterpret_cast<const T*>(&k.m);
+    const unsigned char* cs = reinterpret_cast<const unsigned char*>(&k.c);
+#pragma unroll
+    for (int l = 0; l < V; ++l) point(xs[l], ps[l], rs[l], ws[l], zs[l], ms[l], cs[l]);
+    reinterpret_cast<VT*>(r)[q] = k.r;
+    if constexpr (!FUSED) {
+      reinterpret_cast<VT*>(x)[q] = k.x;
+      reinterpret_cast<VT*>(z)[q] = zv;
+    }
+  };
+  auto sweep = [&](auto&& point) {
+    int64_t q = t0;
+    // two steps at a time where the fewer vectors leave the registers for it (fused)
+    for (; FUSED && q + stride < nv; q += 2 * stride) {
+      Pack a, b;
+      load(q, a);
+      load(q + stride, b);
+      finish(q, a, point);
+      finish(q + stride, b, point);
+    }
+    for (; q < nv; q += stride) {
+      Pack a;
+      load(q, a);
+      finish(q, a, point);
+    }
+    for (int64_t i = nv * V + t0; i < n; i += stride) {
+      T xi = FUSED ? T(0) : x[i], ri = r[i], zi;
+      point(xi, FUSED ? T(0) : p[i], ri, w[i], zi, minv ? minv[i] : T(0), mult[i]);
+      r[i] = ri;
+      if constexpr (!FUSED) {
+        x[i] = xi;
+        z[i] = zi;
+      }
+    }
+  };
   double v[2];
   if constexpr (sizeof(T) == 8) {
     // x, r, z: three FP64 operations per point. <r, z, c> and <r, r, c>: r and z as float
@@ -148,7 +209,7 @@ __global__ void k_cg_update(int64_t n, T* __restrict__ x, const T* __restrict__ 
     for (int m = threadIdx.x; m < 256; m += blockDim.x) sC[m] = m == 1 ? df2{1.f, 0.f} : df_from_double(ctab[m]);
     __syncthreads();
     df2 rz{0.f, 0.f}, rr{0.f, 0.f};
-    auto point = [&](T& xi, T pi, T& ri, T wi, T& zi, T mi, unsigned m) {
+    sweep([&](T& xi, T pi, T& ri, T wi, T& zi, T mi, unsigned m) {
       if constexpr (!FUSED) xi += alpha * pi;
       ri = ri - alpha * wi;
       zi = minv ? mi * ri : ri;
@@ -157,73 +218,19 @@ __global__ void k_cg_update(int64_t n, T* __restrict__ x, const T* __restrict__ 
       df_prod(c2.h, c2.l, r2.h, r2.l, ch, cl);
       df_fma_acc(rz, ch, cl, z2.h, z2.l);
       df_fma_acc(rr, ch, cl, r2.h, r2.l);
-    };
-    for (int64_t q = t0; q < nv; q += stride) {
-      VT xv{}, rv = reinterpret_cast<const VT*>(r)[q], zv, pv{};
-      if constexpr (!FUSED) {
-        xv = reinterpret_cast<const VT*>(x)[q];
-        pv = reinterpret_cast<const VT*>(p)[q];
-      }
-      const VT wv = reinterpret_cast<const VT*>(w)[q];
-      const VT mv = minv ? reinterpret_cast<const VT*>(minv)[q] : VT{};
-      const MT cv = reinterpret_cast<const MT*>(mult)[q];
-      point(xv.x, pv.x, rv.x, wv.x, zv.x, mv.x, cv.x);
-      point(xv.y, pv.y, rv.y, wv.y, zv.y, mv.y, cv.y);
-      reinterpret_cast<VT*>(r)[q] = rv;
-      if constexpr (!FUSED) {
-        reinterpret_cast<VT*>(x)[q] = xv;
-        reinterpret_cast<VT*>(z)[q] = zv;
-      }
-    }
-    for (int64_t i = nv * V + t0; i < n; i += stride) {
-      T xi = FUSED ? T(0) : x[i], ri = r[i], zi;
-      point(xi, FUSED ? T(0) : p[i], ri, w[i], zi, minv ? minv[i] : T(0), mult[i]);
-      r[i] = ri;
-      if constexpr (!FUSED) {
-        x[i] = xi;
-        z[i] = zi;
-      }
-    }
+    });
     v[0] = block_sum(static_cast<double>(rz.h) + static_cast<double>(rz.l), sRed);
     v[1] = block_sum(static_cast<double>(rr.h) + static_cast<double>(rr.l), sRed);
   } else {
     DotAcc<T> rz, rr;
-    auto point = [&](T& xi, T pi, T& ri, T wi, T& zi, T mi, unsigned m) {
+    sweep([&](T& xi, T pi, T& ri, T wi, T& zi, T mi, unsigned m) {
       if constexpr (!FUSED) xi += alpha * pi;
       ri = ri - alpha * wi;
       zi = minv ? mi * ri : ri;
       const T c = m == 1u ? T(1) : static_cast<T>(__ldg(ctab + m));
       rz.add(ri, c * zi);
       rr.add(ri, c * ri);
-    };
-    for (int64_t q = t0; q < nv; q += stride) {
-      VT xv{}, rv = reinterpret_cast<const VT*>(r)[q], zv, pv{};
-      if constexpr (!FUSED) {
-        xv = reinterpret_cast<const VT*>(x)[q];
-        pv = reinterpret_cast<const VT*>(p)[q];
-      }
-      const VT wv = reinterpret_cast<const VT*>(w)[q];
-      const VT mv = minv ? reinterpret_cast<const VT*>(minv)[q] : VT{};
-      const MT cv = reinterpret_cast<const MT*>(mult)[q];
-      point(xv.x, pv.x, rv.x, wv.x, zv.x, mv.x, cv.x);
-      point(xv.y, pv.y, rv.y, wv.y, zv.y, mv.y, cv.y);
-      point(xv.z, pv.z, rv.z, wv.z, zv.z, mv.z, cv.z);
-      point(xv.w, pv.w, rv.w, wv.w, zv.w, mv.w, cv.w);
-      reinterpret_cast<VT*>(r)[q] = rv;
-      if constexpr (!FUSED) {
-        reinterpret_cast<VT*>(x)[q] = xv;
-        reinterpret_cast<VT*>(z)[q] = zv;
-      }
-    }
-    for (int64_t i = nv * V + t0; i < n; i += stride) {
-      T xi = FUSED ? T(0) : x[i], ri = r[i], zi;
-      point(xi, FUSED ? T(0) : p[i], ri, w[i], zi, minv ? minv[i] : T(0), mult[i]);
-      r[i] = ri;
-      if constexpr (!FUSED) {
-        x[i] = xi;
-        z[i] = zi;
-      }
-    }
+    });
     v[0] = block_sum(rz.value(), sRed);
     v[1] = block_sum(rr.value(), sRed);
   }

@@ -75,19 +75,66 @@ __device__ __forceinline__ void for_class(const GsPlan& g, int c, int64_t t0, in
   }
 }
 
+// Copies of a segment in record order (padding entries read as 0, never added).
+template <int W, typename T>
+__device__ __forceinline__ void seg_load(const T* __restrict__ u, const int (&ix)[W], T (&v)[W]) {
+#pragma unroll
+  for (int q = 0; q < W; ++q) v[q] = (q == 0 || ix[q] >= 0) ? u[ix[q]] : T(0);
+}
+
+template <int W, typename T>
+__device__ __forceinline__ T seg_add(const int (&ix)[W], const T (&v)[W]) {
+  T s = v[0];
+#pragma unroll
+  for (int q = 1; q < W; ++q)
+    if (ix[q] >= 0) s += v[q];
+  return s;
+}
+
+// In-place gather-scatter of class c, two segments per thread at a time (both records, then
+// the copies of both, are loaded before anything is added or stored: segments never share
+// copies). value(masked, sum, pf) gives what is written to the copies; pf is pv at the
+// segment's first copy, loaded with the copies (0 if pv is null).
+template <int W, typename T, typename F>
+__device__ __forceinline__ void gs_class(const GsPlan& g, int c, int64_t t0, int64_t stride, T* __restrict__ u,
+                                         const T* __restrict__ pv, F&& value) {
+  const int64_t n = g.n[c];
+  int64_t t = t0;
+  for (; t + stride < n; t += 2 * stride) {
+    const int64_t s0 = n - 1 - t, s1 = s0 - stride;  // last segments first: their copies were written last
+    int a[W], b[W];
+    load_rec<W>(g.rec[c], s0, a);
+    load_rec<W>(g.rec[c], s1, b);
+    const bool ma = g.msk[c][s0] != 0, mb = g.msk[c][s1] != 0;
+    T va[W], vb[W];
+    seg_load<W>(u, a, va);
+    seg_load<W>(u, b, vb);
+    const T pa = pv ? pv[a[0]] : T(0), pb = pv ? pv[b[0]] : T(0);
+    const T ra = value(ma, seg_add<W>(a, va), pa);
+    const T rb = value(mb, seg_add<W>(b, vb), pb);
+    seg_store<W>(u, a, ra);
+    seg_store<W>(u, b, rb);
+  }
+  if (t < n) {
+    const int64_t s0 = n - 1 - t;
+    int a[W];
+    load_rec<W>(g.rec[c], s0, a);
+    T va[W];
+    seg_load<W>(u, a, va);
+    const T pa = pv ? pv[a[0]] : T(0);
+    seg_store<W>(u, a, value(g.msk[c][s0] != 0, seg_add<W>(a, va), pa));
+  }
+}
+
 template <typename T>
 __global__ void k_dssum(const GsPlan g, T* __restrict__ u, int apply_mask) {
   const int64_t t0 = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-  auto body = [&](const auto& ix, bool masked) {
-    constexpr int W = std::extent<std::remove_reference_t<decltype(ix)>>::value;
-    const T s = (apply_mask && masked) ? T(0) : seg_sum<W>(u, ix);
-    seg_store<W>(u, ix, s);
-  };
-  for_class<2>(g, 1, t0, stride, body);
-  for_class<4>(g, 2, t0, stride, body);
-  for_class<8>(g, 3, t0, stride, body);
-  for_class<1>(g, 0, t0, stride, body);
+  auto value = [&](bool masked, T sum, T) { return (apply_mask && masked) ? T(0) : sum; };
+  gs_class<2>(g, 1, t0, stride, u, static_cast<const T*>(nullptr), value);
+  gs_class<4>(g, 2, t0, stride, u, static_cast<const T*>(nullptr), value);
+  gs_class<8>(g, 3, t0, stride, u, static_cast<const T*>(nullptr), value);
+  gs_class<1>(g, 0, t0, stride, u, static_cast<const T*>(nullptr), value);
   for (int64_t x = t0; x < g.nx; x += stride) {
     const int o0 = g.xoff[x], o1 = g.xoff[x + 1];
     T s = u[g.xidx[o0]];
@@ -112,19 +159,16 @@ __global__ void k_dssum_cg(const GsPlan g, T* __restrict__ w, const T* __restric
   const int64_t t0 = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   DotAcc<T> dot;
-  auto body = [&](const auto& ix, bool masked) {
-    constexpr int W = std::extent<std::remove_reference_t<decltype(ix)>>::value;
-    T pf = T(0);
-    if constexpr (DOT) pf = p[ix[0]];
-    T s = seg_sum<W>(w, ix);
-    if (masked) s = T(0);
-    seg_store<W>(w, ix, s);
+  const T* pv = DOT ? p : nullptr;
+  auto value = [&](bool masked, T sum, T pf) {
+    const T s = masked ? T(0) : sum;
     if constexpr (DOT) dot.add(pf, s);
+    return s;
   };
-  for_class<2>(g, 1, t0, stride, body);
-  for_class<4>(g, 2, t0, stride, body);
-  for_class<8>(g, 3, t0, stride, body);
-  for_class<1>(g, 0, t0, stride, body);
+  gs_class<2>(g, 1, t0, stride, w, pv, value);
+  gs_class<4>(g, 2, t0, stride, w, pv, value);
+  gs_class<8>(g, 3, t0, stride, w, pv, value);
+  gs_class<1>(g, 0, t0, stride, w, pv, value);
   for (int64_t x = t0; x < g.nx; x += stride) {
     const int o0 = g.xoff[x], o1 = g.xoff[x + 1];
     const int first = g.xidx[o0];
