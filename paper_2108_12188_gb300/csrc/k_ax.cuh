@@ -86,12 +86,21 @@ struct Stage {
   }
 };
 
+// FP32 CG mode with the fused prologue takes the group's p, r, M^-1 and x by TMA bulk copies
+// (one per element and array: P floats, a multiple of 16 bytes when NP is even).
+template <int NP, typename T, bool CG>
+__host__ __device__ constexpr bool ax_tma_in() {
+  return CG && sizeof(T) == 4 && (NP * NP * NP) % 4 == 0;
+}
+
 // Dynamic shared memory of k_ax: [factors of the element group (STORED only, TMA target)]
-// [staging buffers A, B] [mbarrier].
-template <int NP, typename T, int GEO, int EPB>
+// [staging buffers A, B] [p, r, M^-1, x of the group (ax_tma_in only, TMA target)]
+// [two mbarriers].
+template <int NP, typename T, int GEO, bool CG, int EPB>
 __host__ __device__ constexpr size_t ax_smem_bytes() {
   return (GEO != 0 ? 0 : static_cast<size_t>(EPB) * ax_gstride<NP, T>() * sizeof(T)) +
-         2 * static_cast<size_t>(EPB) * Stage<NP>::kSize * sizeof(T) + 16;
+         2 * static_cast<size_t>(EPB) * Stage<NP>::kSize * sizeof(T) +
+         (ax_tma_in<NP, T, CG>() ? 4 * static_cast<size_t>(EPB) * NP * NP * NP * sizeof(T) : 0) + 32;
 }
 
 // GEO: 0 stored factors, 1 factors recomputed from the element coefficients, 2 recomputed
@@ -128,12 +137,16 @@ __global__ void __launch_bounds__(NP * NP * EPB)
   constexpr int NP2 = NP * NP, P = NP2 * NP, GS = ax_gstride<NP, T>(), SZ = Stage<NP>::kSize;
   constexpr size_t kG = OTF ? 0 : static_cast<size_t>(EPB) * GS;
   extern __shared__ __align__(128) unsigned char smem_raw[];
+  constexpr bool kTmaIn = ax_tma_in<NP, T, CG>();
+  constexpr size_t kIn = kTmaIn ? 4 * static_cast<size_t>(EPB) * P : 0;
   T* sG = reinterpret_cast<T*>(smem_raw);
   T* sA0 = sG + kG;
   T* sB0 = sA0 + EPB * SZ;
+  T* sIn = sB0 + EPB * SZ;  // [4][EPB][P]: p, r, M^-1, x (kTmaIn)
   uint64_t* bar = reinterpret_cast<uint64_t*>(
-      smem_raw + ((reinterpret_cast<uintptr_t>(sB0 + EPB * SZ) - reinterpret_cast<uintptr_t>(smem_raw) + 7) &
+      smem_raw + ((reinterpret_cast<uintptr_t>(sIn + kIn) - reinterpret_cast<uintptr_t>(smem_raw) + 7) &
                   ~uintptr_t(7)));
+  uint64_t* bar_in = bar + 1;
   __shared__ double sRed[32];
 
   T beta = T(0), alpha = T(0);
@@ -155,12 +168,36 @@ __global__ void __launch_bounds__(NP * NP * EPB)
       for (int q = 0; q < cnt; ++q) tma_load_1d(sG + q * GS, G + (e0 + q) * GS, kElemBytes, bar);
     }
   }
+  // kTmaIn: the copies need 16-byte aligned vectors (the library's own are); else plain loads
+  const bool tma_in =
+      kTmaIn && ((reinterpret_cast<uintptr_t>(p) | reinterpret_cast<uintptr_t>(r) | reinterpret_cast<uintptr_t>(x) |
+                  reinterpret_cast<uintptr_t>(minv)) & 15u) == 0;
+  constexpr unsigned kInBytes = static_cast<unsigned>(P * sizeof(T));
+  auto issue_in = [&](int64_t e0, int cnt) {  // thread 0: the group's p, r, M^-1, x
+    fence_proxy_async();
+    mbar_expect_tx(bar_in, kInBytes * static_cast<unsigned>(cnt) * (minv ? 4u : 3u));
+    for (int q = 0; q < cnt; ++q) {
+      const int64_t off = (e0 + q) * P;
+      tma_load_1d(sIn + (0 * EPB + q) * P, p + off, kInBytes, bar_in);
+      tma_load_1d(sIn + (1 * EPB + q) * P, r + off, kInBytes, bar_in);
+      if (minv) tma_load_1d(sIn + (2 * EPB + q) * P, minv + off, kInBytes, bar_in);
+      tma_load_1d(sIn + (3 * EPB + q) * P, x + off, kInBytes, bar_in);
+    }
+  };
+  if constexpr (kTmaIn) {
+    if (tma_in && threadIdx.x == 0) {  // inputs of the first group
+      mbar_init(bar_in, 1);
+      const int64_t e0 = static_cast<int64_t>(blockIdx.x) * EPB;
+      issue_in(e0, static_cast<int>(E - e0 < EPB ? E - e0 : EPB));
+    }
+  }
   const int slot = threadIdx.x / NP2, tid = threadIdx.x % NP2;
   const int i = tid % NP, j = tid / NP;  // column (i, j); i-row (j, k) = (i, j); j-line (i, k) = (i, j)
   T* sA = sA0 + slot * SZ;
   T* sB = sB0 + slot * SZ;
   DotAcc<T> dot;
-  unsigned parity = 0;
+  unsigned parity = 0, parity_in = 0;
+  bool in_pend = tma_in;  // an input copy is in flight (uniform over the block)
   __syncthreads();
 
   for (int64_t grp = blockIdx.x; grp < n_groups; grp += gridDim.x) {
@@ -170,15 +207,46 @@ __global__ void __launch_bounds__(NP * NP * EPB)
     // phase 0: the column of the input
     T rU[NP];
     if constexpr (CG && kFused) {
-      // every load of the column first, so that they are all in flight together
+      // every load of the column first, so that they are all in flight together (kTmaIn: the
+      // group's copies in shared memory)
       T po[NP], rq[NP], xq[NP], mq[NP];
+      bool from_smem = false;
+      if constexpr (kTmaIn) {
+        if (tma_in) {
+          const bool ok = mbar_wait_bounded(bar_in, parity_in);
+          parity_in ^= 1u;
+          in_pend = false;
+          if (__syncthreads_or(!ok)) {  // the copies did not arrive: report and leave together
+            if (threadIdx.x == 0) {  // first let this block's copies in flight land (bounded)
+              mbar_wait_bounded(bar_in, parity_in ^ 1u);
+              if constexpr (!OTF) mbar_wait_bounded(bar, parity);  // this group's factors
+              atomicExch(err, static_cast<int>(SEM_ERR_TIMEOUT));
+              st->status = SEM_ERR_TIMEOUT;
+              st->done = 1;
+            }
+            return;
+          }
+          from_smem = true;
+        }
+      }
+      if (from_smem) {
+        const T* sp = sIn + slot * P + tid;
 #pragma unroll
-      for (int k = 0; k < NP; ++k) {
-        const int64_t q = base + k * NP2;
-        po[k] = valid ? p[q] : T(0);
-        rq[k] = valid ? r[q] : T(0);
-        xq[k] = valid ? x[q] : T(0);
-        mq[k] = valid && minv ? minv[q] : T(1);
+        for (int k = 0; k < NP; ++k) {
+          po[k] = valid ? sp[0 * EPB * P + k * NP2] : T(0);
+          rq[k] = valid ? sp[1 * EPB * P + k * NP2] : T(0);
+          mq[k] = valid && minv ? sp[2 * EPB * P + k * NP2] : T(1);
+          xq[k] = valid ? sp[3 * EPB * P + k * NP2] : T(0);
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+          const int64_t q = base + k * NP2;
+          po[k] = valid ? p[q] : T(0);
+          rq[k] = valid ? r[q] : T(0);
+          xq[k] = valid ? x[q] : T(0);
+          mq[k] = valid && minv ? minv[q] : T(1);
+        }
       }
 #pragma unroll
       for (int k = 0; k < NP; ++k) {
@@ -191,6 +259,14 @@ __global__ void __launch_bounds__(NP * NP * EPB)
         }
         rU[k] = val;
         sA[Stage<NP>::at(i, j, k)] = val;
+      }
+      if constexpr (kTmaIn) {
+        __syncthreads();  // the input copies are consumed
+        in_pend = tma_in && grp + gridDim.x < n_groups;
+        if (in_pend && threadIdx.x == 0) {  // next group's, during phases 1-5
+          const int64_t e0 = (grp + gridDim.x) * EPB;
+          issue_in(e0, static_cast<int>(E - e0 < EPB ? E - e0 : EPB));
+        }
       }
     } else {
 #pragma unroll
@@ -235,8 +311,9 @@ __global__ void __launch_bounds__(NP * NP * EPB)
       const bool ok = mbar_wait_bounded(bar, parity);  // this group's factors
       parity ^= 1u;
       if (__syncthreads_or(!ok)) {  // the factor copy did not arrive: report and leave together
-        if (threadIdx.x == 0) {
+        if (threadIdx.x == 0) {  // first let this block's copies in flight land (bounded)
           mbar_wait_bounded(bar, parity ^ 1u);
+          if (in_pend) mbar_wait_bounded(bar_in, parity_in);
           atomicExch(err, static_cast<int>(SEM_ERR_TIMEOUT));
           if constexpr (CG) {
             st->status = SEM_ERR_TIMEOUT;
@@ -372,7 +449,7 @@ template <int NP, typename T, int GEO, bool CG, int EPB>
 int ax_max_blocks() {
   // resident blocks per SM x SMs; computed once (thread-safe static initialisation)
   static const int cached = [] {
-    constexpr size_t smem = ax_smem_bytes<NP, T, GEO, EPB>();
+    constexpr size_t smem = ax_smem_bytes<NP, T, GEO, CG, EPB>();
     cudaFuncSetAttribute(k_ax<NP, T, GEO, CG, EPB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          static_cast<int>(smem));
     int dev = 0, sms = 0, per_sm = 0;
@@ -392,7 +469,7 @@ sem_status launch_ax_t(int N, const AxLaunch& a, cudaStream_t s) {
   if (groups < grid) grid = static_cast<int>(groups);
   if (a.grid_out) *a.grid_out = grid;
   const GllParam<NP, T> tab = make_gll_param<NP, T>(N);
-  k_ax<NP, T, GEO, CG, EPB><<<grid, NP * NP * EPB, ax_smem_bytes<NP, T, GEO, EPB>(), s>>>(
+  k_ax<NP, T, GEO, CG, EPB><<<grid, NP * NP * EPB, ax_smem_bytes<NP, T, GEO, CG, EPB>(), s>>>(
       tab, a.E, static_cast<const T*>(a.u), static_cast<T*>(a.w), static_cast<const T*>(a.G),
       static_cast<const T*>(a.coef), static_cast<const T*>(a.scale), static_cast<const T*>(a.z),
       static_cast<T*>(a.p), static_cast<const T*>(a.r), static_cast<const T*>(a.minv), static_cast<T*>(a.x), a.st,
