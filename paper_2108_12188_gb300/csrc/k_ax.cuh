@@ -18,8 +18,9 @@
 // which costs 21 multiply-adds instead of building six factors and applying them.
 //
 // CG mode (Algorithm 1, steps 5-6 fused, Section 5.1): the prologue forms p = z + beta p
-// and stores it, and the epilogue adds p.w over element-interior points (those points are
-// untouched by the gather-scatter) into a per-block partial of <p, w, c>.
+// and stores it, and the epilogue adds p.w into a per-block partial of <p, w, c>: FP64 over
+// element-interior points (untouched by the gather-scatter), FP32 over every point. The
+// FP32 prologue also takes the previous iteration's x update and z = M^-1 r (phase 0 below).
 #pragma once
 
 #include "k_common.cuh"
@@ -114,7 +115,9 @@ __host__ __device__ constexpr size_t ax_smem_bytes() {
 //      the previous iteration's x update here, x += alpha p (alpha is 0 when none is
 //      pending), and forms z = M^-1 r from r and M^-1 instead of reading a stored z: the
 //      update kernel then neither reads nor writes x and writes no z (12 of its 33 bytes
-//      per point), and this kernel, bound by instruction issue, absorbs the extra loads
+//      per point), and this kernel, bound by instruction issue, absorbs the extra loads;
+//      for even NP they arrive by TMA bulk copies of the group's p, r, M^-1 and x, issued
+//      during the previous group's phases 1-5 (ax_tma_in)
 //   1  i-rows of A -> ur into B;               column -> ut (registers)
 //   2  j-lines of A -> us, in place in A
 //   3  column: (vr, vs, vt) = G (ur, us, ut); vr, vs in place in B, A; vt in registers
