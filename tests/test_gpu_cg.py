@@ -152,3 +152,48 @@ def test_cg_single_element(sem, mixed):
     assert _true_rel(prob, b, x) <= 1e-10 * (1 + 1e-3)
     if not mixed:
         assert abs(res["iters"] - ref.iterations) <= max(1, 0.02 * ref.iterations), (res["iters"], ref.iterations)
+
+
+@pytest.mark.parametrize("graph", [1, 0], ids=["graph", "eager"])
+def test_cg_deferred_update_split_runs(sem, c1, graph):
+    """The double-float CG makes each x update one iteration late, in the operator's prologue,
+    and adds the pending one when a run of iterations ends. Runs of 4 + 3 + 5 iterations give
+    the x of one run of 12 bit for bit, the residual follows the oracle's history, and runs
+    after convergence change nothing."""
+    import torch
+    m, prob, b, ref, mesh = c1
+    bd = torch.empty(prob.n, dtype=torch.float64, device="cuda")
+    sem.sem_rhs_sine(mesh.handle, 1, 1, 1, sem.SEM_F64, bd)
+    opts = sem.sem_cg_default_opts(rtol=1e-10, f64_arith=1, use_graph=graph, check_every=5)
+
+    def run(chunks):
+        x = torch.zeros_like(bd)
+        cg = sem.sem_cg_create(mesh.handle, opts)
+        sem.sem_cg_start(cg, bd, x)
+        for k in chunks:
+            sem.sem_cg_iterate(cg, k)
+        q = sem.sem_cg_query(cg)
+        return cg, x, q
+
+    cg_a, xa, qa = run([12])
+    cg_b, xb, qb = run([4, 3, 5])
+    assert qa["iters"] == qb["iters"] == 12
+    np.testing.assert_array_equal(xa.cpu().numpy(), xb.cpu().numpy())
+    assert abs(qa["rel_res"] - ref.history[12]) <= 1e-8 * ref.history[12]
+    # the returned x is the 12th iterate: its true residual is the recurrence's
+    assert abs(_true_rel(prob, b, xa.cpu().numpy()) - qa["rel_res"]) <= 1e-6 * qa["rel_res"]
+    sem.sem_cg_destroy(cg_b)
+    for _ in range(100):
+        sem.sem_cg_iterate(cg_a, 25)
+        q = sem.sem_cg_query(cg_a)
+        if q["status"] != sem.SEM_ERR_BUSY:
+            break
+    assert q["status"] == sem.SEM_OK and q["rel_res"] <= 1e-10
+    # the flushed x carries the last update: its true residual is the recurrence's (the
+    # double-float operator's own error, about 1e-14 of |A||x|, is far below 1e-12 here)
+    assert abs(_true_rel(prob, b, xa.cpu().numpy()) - q["rel_res"]) <= 1e-12
+    done = xa.cpu().numpy()
+    sem.sem_cg_iterate(cg_a, 7)
+    assert sem.sem_cg_query(cg_a)["iters"] == q["iters"]
+    np.testing.assert_array_equal(xa.cpu().numpy(), done)
+    sem.sem_cg_destroy(cg_a)
