@@ -136,3 +136,17 @@ def test_host_numbering_full_size_hash(sem, n, N):
     assert ng == n_glob
     assert hashlib.sha256(glo.astype("<i8").tobytes()).hexdigest() == hg
     assert hashlib.sha256(mask.tobytes()).hexdigest() == hm
+
+
+def test_null_handles_are_argument_errors(sem):
+    """Calls with a null handle or output pointer return SEM_ERR_ARG (and touch no device)."""
+    lib = sem.load_library()
+    a = sem.C.c_int64()
+    assert lib.sem_mesh_info(None, sem.C.byref(a), None, None) == sem.SEM_ERR_ARG
+    opts = sem.sem_cg_default_opts()
+    t = sem.C.c_uint64()
+    b = np.zeros(4)
+    assert lib.sem_server_submit_mesh(None, None, b.ctypes.data, sem.C.byref(opts), sem.C.byref(t)) == sem.SEM_ERR_ARG
+    assert lib.sem_mesh_destroy(None) == sem.SEM_OK
+    assert lib.sem_server_destroy(None) == sem.SEM_OK
+    assert "null" in lib.sem_last_error().decode()

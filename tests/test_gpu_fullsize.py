@@ -148,3 +148,27 @@ def test_cg_mode_iterates(full, f64x):
     sem.sem_glsc3(mesh.handle, 0, b, b, dot)
     true_rel = float(np.sqrt(rr / float(dot.item())))
     assert abs(true_rel - q["rel_res"]) <= 1e-6 * q["rel_res"], (true_rel, q["rel_res"])
+
+
+@pytest.mark.parametrize("mixed", [1, 2], ids=["restarted", "reliable-updates"])
+def test_mixed_solve_full_size(full, mixed):
+    """FP32 on-the-fly CG (fused prologue, TMA-staged inputs, deferred x updates) inside FP64
+    refinement on the full-size mesh: the solution's true residual b - A x, formed with the
+    FP64 operator and the FP64 weighted dot, meets rtol."""
+    import torch
+    sem, m, mesh = full
+    b = torch.empty(mesh.n, dtype=torch.float64, device="cuda")
+    sem.sem_rhs_sine(mesh.handle, 1, 1, 1, 0, b)
+    x = torch.zeros_like(b)
+    opts = sem.sem_cg_default_opts(rtol=1e-10, mixed=mixed, variant=sem.SEM_AX_STORED, inner_variant=sem.SEM_AX_OTF,
+                                   inner_rtol=0.1 if mixed == 2 else 1e-5)
+    res = sem.sem_cg_solve(mesh.handle, b, x, opts)
+    assert res["status"] == sem.SEM_OK, res
+    w = torch.empty_like(b)
+    sem.sem_ax(mesh.handle, 0, 0, x, w, assemble=True)
+    r = b - w
+    dot = torch.empty(1, dtype=torch.float64, device="cuda")
+    sem.sem_glsc3(mesh.handle, 0, r, r, dot)
+    rr = float(dot.item())
+    sem.sem_glsc3(mesh.handle, 0, b, b, dot)
+    assert np.sqrt(rr / float(dot.item())) <= 1e-10 * (1 + 1e-3)
