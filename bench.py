@@ -458,7 +458,8 @@ def run_gpu(args):
     del x_df
     step_f64x = {"ms_per_step": df_total / args.steps, "gdof_s": n / (df_total / args.steps * 1e-3) / 1e9,
                  "per_kernel_ms": {"ax": df_kernels[0], "gather_scatter": df_kernels[1], "update": df_kernels[2]},
-                 "ax_hbm_frac": (ax_bytes_per_point("stored", "f64", NORD) * n + 16 * n) / (df_kernels[0] * 1e-3)
+                 # fused CG prologue: p, r, M^-1, x in and x, p out besides the plain operator's u/w/G
+                 "ax_hbm_frac": (ax_bytes_per_point("stored", "f64", NORD) * n + 40 * n) / (df_kernels[0] * 1e-3)
                  / 1e9 / hbm_gbs}
 
     # roofline of the dominant kernel (the local operator, FP64 stored, CG mode)
