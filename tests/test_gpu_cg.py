@@ -197,3 +197,22 @@ def test_cg_deferred_update_split_runs(sem, c1, graph):
     assert sem.sem_cg_query(cg_a)["iters"] == q["iters"]
     np.testing.assert_array_equal(xa.cpu().numpy(), done)
     sem.sem_cg_destroy(cg_a)
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 6, 8, 10, 11])
+def test_cg_fused_prologue_every_order(sem, N):
+    """The FP32 CG (reliable updates; TMA-staged prologue inputs for even N + 1, plain loads for
+    odd) and the double-float CG (fused prologue for every order) on a ragged jittered mesh:
+    the oracle's true residual of each solution meets rtol."""
+    m = BoxMesh(3, 2, 2, jitter=0.1, seed=N)
+    prob = so.SemProblem(N, m.vert_xyz, m.elem_verts)
+    b = prob.rhs()
+    mesh = sem.Mesh(N, m.vert_xyz, m.elem_verts, flags=sem.SEM_MESH_F64_STORED | sem.SEM_MESH_F32_STORED)
+    for opts in (sem.sem_cg_default_opts(rtol=1e-10, mixed=2, inner_variant=sem.SEM_AX_OTF, inner_rtol=0.1),
+                 sem.sem_cg_default_opts(rtol=1e-10, mixed=2, inner_variant=sem.SEM_AX_STORED, inner_rtol=0.1,
+                                         use_graph=0),
+                 sem.sem_cg_default_opts(rtol=1e-9, f64_arith=1)):
+        res, x = _solve(sem, mesh, prob, opts)
+        assert res["status"] == sem.SEM_OK, (N, res)
+        assert _true_rel(prob, b, x) <= opts.rtol * (1 + 1e-3), N
+    mesh.close()
