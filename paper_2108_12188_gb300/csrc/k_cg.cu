@@ -18,9 +18,10 @@ namespace {
 
 constexpr int kThreads = 256;
 
-int vec_grid(int64_t n) {
+// One thread per kThreads-th of the points at most, and no more blocks than are resident at
+// once (cap = resident_blocks of the kernel): grid-stride beyond.
+int vec_grid(int64_t n, int cap) {
   const int64_t b = (n + kThreads - 1) / kThreads;
-  const int64_t cap = 152 * 8;
   return static_cast<int>(b < cap ? (b > 0 ? b : 1) : cap);
 }
 
@@ -263,7 +264,8 @@ __global__ void k_cg_update(int64_t n, T* __restrict__ x, const T* __restrict__ 
 
 sem_status launch_glsc3(sem_prec prec, int64_t n, const void* a, const void* b, const uint8_t* mult,
                         const double* ctab, double* partials, unsigned int* ticket, double* result, cudaStream_t s) {
-  const int grid = vec_grid(n);
+  const int grid = vec_grid(n, prec == SEM_F64 ? resident_blocks<k_glsc3<double>>(kThreads)
+                                               : resident_blocks<k_glsc3<float>>(kThreads));
   if (prec == SEM_F64)
     k_glsc3<double><<<grid, kThreads, 0, s>>>(n, static_cast<const double*>(a), static_cast<const double*>(b), mult,
                                               ctab, partials, ticket, result);
@@ -278,7 +280,8 @@ sem_status launch_glsc3(sem_prec prec, int64_t n, const void* a, const void* b, 
 sem_status launch_cg_init(sem_prec prec, int64_t n, const void* b, const void* ax0, void* r, void* z, void* p,
                           const void* minv, const uint8_t* mult, const double* ctab, CgScalars* st, double* partials,
                           cudaStream_t s) {
-  const int grid = vec_grid(n);
+  const int grid = vec_grid(n, prec == SEM_F64 ? resident_blocks<k_cg_init<double>>(kThreads)
+                                               : resident_blocks<k_cg_init<float>>(kThreads));
   if (prec == SEM_F64)
     k_cg_init<double><<<grid, kThreads, 0, s>>>(n, static_cast<const double*>(b), static_cast<const double*>(ax0),
                                                 static_cast<double*>(r), static_cast<double*>(z),
@@ -296,7 +299,9 @@ sem_status launch_cg_init(sem_prec prec, int64_t n, const void* b, const void* a
 sem_status launch_cg_update(sem_prec prec, bool fused, int64_t n, void* x, const void* p, void* r, const void* w,
                             void* z, const void* minv, const uint8_t* mult, const double* ctab, CgScalars* st,
                             double* partials, cudaStream_t s) {
-  const int grid = vec_grid(n);
+  const int grid = vec_grid(n, prec != SEM_F64 ? resident_blocks<k_cg_update<float, true>>(kThreads)
+                               : fused         ? resident_blocks<k_cg_update<double, true>>(kThreads)
+                                               : resident_blocks<k_cg_update<double, false>>(kThreads));
   if (prec == SEM_F64) {
     auto* xd = static_cast<double*>(x);
     auto* pd = static_cast<const double*>(p);
@@ -349,7 +354,8 @@ __global__ void k_cg_flush(int64_t n, T* __restrict__ x, const T* __restrict__ p
 }  // namespace
 
 sem_status launch_cg_flush(sem_prec prec, int64_t n, void* x, const void* p, CgScalars* st, cudaStream_t s) {
-  const int grid = vec_grid(n);
+  const int grid = vec_grid(n, prec == SEM_F64 ? resident_blocks<k_cg_flush<double>>(kThreads)
+                                               : resident_blocks<k_cg_flush<float>>(kThreads));
   if (prec == SEM_F64)
     k_cg_flush<double><<<grid, kThreads, 0, s>>>(n, static_cast<double*>(x), static_cast<const double*>(p), st);
   else
@@ -449,7 +455,7 @@ __global__ void k_ir_correct(int64_t n, double* __restrict__ x, const float* __r
 sem_status launch_ir_residual(int64_t n, const double* b, const double* w, double* r64, float* r32,
                               const uint8_t* mult, const double* ctab, CgScalars* st, double* partials,
                               cudaStream_t s) {
-  k_ir_residual<<<vec_grid(n), kThreads, 0, s>>>(n, b, w, r64, r32, mult, ctab, st, partials);
+  k_ir_residual<<<vec_grid(n, resident_blocks<k_ir_residual>(kThreads)), kThreads, 0, s>>>(n, b, w, r64, r32, mult, ctab, st, partials);
   count_launch();
   SEM_CUDA_TRY(cudaGetLastError());
   return SEM_OK;
@@ -457,14 +463,14 @@ sem_status launch_ir_residual(int64_t n, const double* b, const double* w, doubl
 
 sem_status launch_cg_replace(int64_t n, const float* rnew, float* r, float* z, const float* minv, const uint8_t* mult,
                              const double* ctab, CgScalars* st, double* partials, cudaStream_t s) {
-  k_cg_replace<<<vec_grid(n), kThreads, 0, s>>>(n, rnew, r, z, minv, mult, ctab, st, partials);
+  k_cg_replace<<<vec_grid(n, resident_blocks<k_cg_replace>(kThreads)), kThreads, 0, s>>>(n, rnew, r, z, minv, mult, ctab, st, partials);
   count_launch();
   SEM_CUDA_TRY(cudaGetLastError());
   return SEM_OK;
 }
 
 sem_status launch_ir_correct(int64_t n, double* x, const float* d, cudaStream_t s) {
-  k_ir_correct<<<vec_grid(n), kThreads, 0, s>>>(n, x, d);
+  k_ir_correct<<<vec_grid(n, resident_blocks<k_ir_correct>(kThreads)), kThreads, 0, s>>>(n, x, d);
   count_launch();
   SEM_CUDA_TRY(cudaGetLastError());
   return SEM_OK;

@@ -137,6 +137,21 @@ __device__ __forceinline__ double sum_partials(const double* partials, int count
   return block_sum(s, sh);
 }
 
+// Blocks of kernel K (with `threads` threads and no dynamic shared memory) that are resident
+// on the device at once: SMs x blocks per SM, computed on first use. Grid-stride kernels are
+// launched with at most this many blocks, so that all of them run in one wave.
+template <auto K>
+int resident_blocks(int threads) {
+  static const int cap = [threads] {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, K, threads, 0);
+    return (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+  }();
+  return cap;
+}
+
 __host__ __device__ constexpr int ceil_div(long long a, long long b) { return static_cast<int>((a + b - 1) / b); }
 
 }  // namespace sem
