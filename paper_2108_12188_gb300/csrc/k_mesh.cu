@@ -215,9 +215,16 @@ __global__ void k_cast(int64_t n, const double* __restrict__ in, float* __restri
     out[i] = static_cast<float>(in[i]);
 }
 
+// One thread per item, at most 32 blocks per SM (grid-stride beyond).
 int grid_for(int64_t n) {
+  static const int cap = [] {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return 32 * (sms > 0 ? sms : 1);
+  }();
   const int64_t b = (n + kThreads - 1) / kThreads;
-  return static_cast<int>(b < 152 * 32 ? (b > 0 ? b : 1) : 152 * 32);
+  return static_cast<int>(b < cap ? (b > 0 ? b : 1) : cap);
 }
 
 }  // namespace
