@@ -303,7 +303,7 @@ def run_reference(args):
     m = BoxMesh(nel, nel, nel, jitter=JITTER, seed=SEED)
     prob = so.SemProblem(NORD, m.vert_xyz, m.elem_verts)
     b = prob.rhs()
-    # one step = one oracle Jacobi-PCG iteration on the 8^3 sample of the workload
+    # one step = one oracle Jacobi-PCG iteration on the 12^3 sample of the workload
     shape = prob.shape()
     c = prob.c.reshape(shape)
     Minv = prob.jacobi_inverse()
@@ -739,6 +739,27 @@ def run_serve(args):
         "p99_ms": main["p99_ms"], "rates": out_rates}))
 
 
+def oracle_ax_rate(N: int, nel: int = 8, reps: int = 3) -> dict:
+    """The oracle's local operator A_L (FP64, stored factors, element by element) on one host
+    core, on a bounded sample: nel^3 elements of the sweep's jittered box at order N."""
+    import numpy as np
+    from oracle import sem_oracle as so
+    from synthetic import BoxMesh
+    m = BoxMesh(nel, nel, nel, jitter=0.1, seed=100 + N)
+    xi, wq = so.gll_nodes_weights(N)
+    D = so.lagrange_derivative_matrix(xi)
+    G, _ = so.geometric_factors(so.element_vertices(m.vert_xyz, m.elem_verts), xi, wq)
+    u = np.random.default_rng(N).uniform(-1.0, 1.0, (nel ** 3, N + 1, N + 1, N + 1))
+    so.ax_local(u, G, D)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        so.ax_local(u, G, D)
+    dt = (time.perf_counter() - t0) / reps
+    pts = nel ** 3 * (N + 1) ** 3
+    return {"gdof_s": pts / dt / 1e9, "cores": 1, "kind": "oracle",
+            "sample": f"{nel}^3 elements at N={N} ({pts} local points), A_L only, {reps} repetitions"}
+
+
 def run_sweep(args):
     """Polynomial-order sweep: N in {3,5,7,9,11}, E = n^3 with n = round(cbrt(16.8M / (N+1)^3)),
     interior jitter +-0.1h; per N the autotuner picks block shape and stored versus on-the-fly
@@ -786,6 +807,7 @@ def run_sweep(args):
             row[name] = {"ms": ms, "iterations": res["iters"], "outer": res["outer_iters"],
                          "ms_per_iteration": ms / max(res["iters"], 1), "rel_res": res["rel_res"],
                          "status": sem.sem_status_string(res["status"])}
+        row["cpu_baseline_ax"] = oracle_ax_rate(N)
         rows.append(row)
         mesh.close()
         print(json.dumps({"N": N, "done": True}), file=sys.stderr)
