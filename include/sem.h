@@ -294,7 +294,9 @@ sem_status sem_cg_query(sem_cg cg, sem_cg_result* result_host, void* stream);
  * (no graph) with CUDA events recorded on `stream` before the first kernel and after
  * each of the three kernels of every iteration (local operator, gather-scatter, vector
  * update); synchronises `stream` and returns the elapsed time of the k iterations in
- * total_ms_host and the mean duration of each kernel in kernel_ms_host[3]. */
+ * total_ms_host and the mean duration of each kernel in kernel_ms_host[3]. With
+ * opts.f64_arith the last update interval also holds the pending x update (see
+ * sem_cg_iterate), so the total covers all the work of the k iterations. */
 sem_status sem_cg_iterate_timed(sem_cg cg, int k, double* total_ms_host, double* kernel_ms_host, void* stream);
 
 sem_status sem_cg_destroy(sem_cg cg); /* waits for the streams the handle was used on */
