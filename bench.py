@@ -77,12 +77,22 @@ def measured_peaks():
         return HBM_FALLBACK_GBS, "fallback"
 
 
+KERNEL_SOURCES = ("k_ax.cuh", "k_common.cuh", "k_tma.cuh")  # every source the local operator is built from
+
+
+def kernel_digest() -> str:
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2108_12188_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
 def ncu_traffic(kernel_key: str):
-    """DRAM bytes per launch from the committed ncu summary, if the kernel source is unchanged."""
+    """DRAM bytes per launch from the committed ncu summary, if the kernel's sources are unchanged."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
-    src = os.path.join(ROOT, "paper_2108_12188_gb300", "csrc", "k_ax.cuh")
     try:
-        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        digest = kernel_digest()
         with open(path) as f:
             for line in f:
                 parts = line.split()

@@ -146,6 +146,15 @@ sem_status sem_mesh_get_mask(sem_mesh mesh, uint8_t* mask_host);
 sem_status sem_mesh_get_segments(sem_mesh mesh, int32_t* seg_off_host, int32_t* seg_idx_host,
                                  uint8_t* seg_mask_host);
 
+/* Self-test of the bounded waits that guard every TMA copy of the library (failure
+ * detection without a GPU fault): one block prepares an mbarrier for a 16-byte copy and waits
+ * for it with a limit of limit_ns nanoseconds (1 ms .. 2 s, else SEM_ERR_ARG). issue_copy = 1
+ * issues the copy: the wait completes, SEM_OK. issue_copy = 0 issues nothing: the wait gives
+ * up after the limit and the call returns SEM_ERR_TIMEOUT, the status a CG solve reports when
+ * a copy of the local operator does not arrive; the context stays usable. Synchronises
+ * `stream`; *elapsed_ms_host receives the kernel's duration. */
+sem_status sem_probe_bounded_wait(int64_t limit_ns, int issue_copy, double* elapsed_ms_host, void* stream);
+
 /* Physical coordinates of the local points (trilinear map, Section 5.1):
  * xyz_dev [3][n_local] FP64 (all x, then all y, then all z). Async. */
 sem_status sem_mesh_coords(sem_mesh mesh, double* xyz_dev, void* stream);

@@ -1,7 +1,7 @@
 // Bulk asynchronous copies (TMA, cp.async.bulk) from global to shared memory, completed on
 // an mbarrier, with bounded waits.
 //
-// A wait that does not complete within kSpinLimit polls returns false; callers then record
+// A wait that does not complete within kWaitLimitNs (or kSpinLimit polls) returns false; callers then record
 // an error status, stop issuing copies and leave the kernel (all threads of the block agree
 // through __syncthreads_or, so no thread is left at a barrier).
 #pragma once
@@ -53,10 +53,23 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
   return ok != 0;
 }
 
-// Bounded wait for the phase with the given parity; true if it completed.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
-  for (unsigned spin = 0; spin < kSpinLimit; ++spin)
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s: far above any copy's latency
+
+// Bounded wait for the phase with the given parity; true if it completed. It gives up after
+// limit_ns nanoseconds of the global timer, or kSpinLimit polls, whichever comes first.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, uint64_t limit_ns = kWaitLimitNs) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (unsigned spin = 0; spin < kSpinLimit; ++spin) {
     if (mbar_try_wait(bar, parity)) return true;
+    if (global_ns() - t0 > limit_ns) return false;
+  }
   return false;
 }
 

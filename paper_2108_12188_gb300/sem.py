@@ -30,7 +30,7 @@ EXPORTS = [
     "sem_cg_start", "sem_cg_iterate", "sem_cg_iterate_timed", "sem_cg_query", "sem_cg_destroy", "sem_launch_count", "sem_last_error",
     "sem_status_string", "sem_server_create", "sem_server_submit", "sem_server_poll", "sem_server_stats",
     "sem_server_destroy", "sem_autotune", "sem_autotune_save", "sem_autotune_load", "sem_mesh_info",
-    "sem_server_submit_mesh",
+    "sem_server_submit_mesh", "sem_probe_bounded_wait",
 ]
 
 
@@ -108,6 +108,7 @@ def load_library(path: str | None = None):
         "sem_mesh_numbering": [_I, _I64, _I64, _VP, _VP, _VP, _VP, C.POINTER(_I64)],
         "sem_mesh_get_info": [_VP, C.POINTER(MeshInfo)],
         "sem_mesh_info": [_VP, C.POINTER(_I64), C.POINTER(_I64), C.POINTER(_I64)],
+        "sem_probe_bounded_wait": [_I64, C.c_int, C.POINTER(C.c_double), _VP],
         "sem_mesh_get_glo_num": [_VP, _VP],
         "sem_mesh_get_mask": [_VP, _VP],
         "sem_mesh_get_segments": [_VP, _VP, _VP, _VP],
@@ -236,6 +237,14 @@ def sem_mesh_info(mesh) -> tuple:
     a, b, c = _I64(), _I64(), _I64()
     _check(load_library().sem_mesh_info(mesh, C.byref(a), C.byref(b), C.byref(c)))
     return int(a.value), int(b.value), int(c.value)
+
+
+def sem_probe_bounded_wait(limit_ns, issue_copy, stream=None):
+    """(status, kernel ms) of the bounded-wait self-test; SEM_ERR_TIMEOUT is a result here."""
+    ms = C.c_double()
+    st = _check(load_library().sem_probe_bounded_wait(int(limit_ns), int(issue_copy), C.byref(ms), _stream(stream)),
+                ok=(SEM_OK, SEM_ERR_TIMEOUT))
+    return st, float(ms.value)
 
 
 def sem_mesh_get_glo_num(mesh) -> np.ndarray:

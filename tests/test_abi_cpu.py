@@ -150,3 +150,12 @@ def test_null_handles_are_argument_errors(sem):
     assert lib.sem_mesh_destroy(None) == sem.SEM_OK
     assert lib.sem_server_destroy(None) == sem.SEM_OK
     assert "null" in lib.sem_last_error().decode()
+
+
+def test_probe_argument_errors(sem):
+    """The bounded-wait self-test validates its arguments before touching a device."""
+    lib = sem.load_library()
+    ms = sem.C.c_double()
+    assert lib.sem_probe_bounded_wait(10, 0, sem.C.byref(ms), None) == sem.SEM_ERR_ARG  # below 1 ms
+    assert lib.sem_probe_bounded_wait(3_000_000_000, 0, sem.C.byref(ms), None) == sem.SEM_ERR_ARG
+    assert lib.sem_probe_bounded_wait(20_000_000, 0, None, None) == sem.SEM_ERR_ARG

@@ -1,0 +1,43 @@
+"""Failure detection on the GPU without a fault: the bounded waits that guard every TMA copy
+give up after their time limit and report SEM_ERR_TIMEOUT (the copy is never issued, so
+nothing arrives), the CUDA context stays usable, and the same wait completes when the copy
+is issued."""
+import numpy as np
+import pytest
+
+from synthetic import BoxMesh
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sem():
+    import torch
+    from paper_2108_12188_gb300 import build_lib, sem as sem_mod
+    build_lib.build()
+    sem_mod.load_library()
+    torch.cuda.set_device(0)
+    return sem_mod
+
+
+def test_bounded_wait_completes_when_the_copy_arrives(sem):
+    st, ms = sem.sem_probe_bounded_wait(1_000_000_000, 1)
+    assert st == sem.SEM_OK and ms < 100.0, (st, ms)
+
+
+@pytest.mark.parametrize("limit_ms", [5, 50])
+def test_bounded_wait_times_out_and_the_context_survives(sem, limit_ms):
+    import torch
+    st, ms = sem.sem_probe_bounded_wait(limit_ms * 1_000_000, 0)
+    assert st == sem.SEM_ERR_TIMEOUT
+    assert limit_ms * 0.99 <= ms <= limit_ms + 500.0, ms
+    # the context still works: an operator application and a reduction afterwards
+    m = BoxMesh(2, 2, 2, jitter=0.1, seed=3)
+    mesh = sem.Mesh(3, m.vert_xyz, m.elem_verts)
+    u = torch.ones(mesh.n, dtype=torch.float64, device="cuda")
+    w = torch.empty_like(u)
+    sem.sem_ax(mesh.handle, sem.SEM_AX_STORED, sem.SEM_F64, u, w, assemble=False)
+    assert float(torch.linalg.norm(w)) / np.sqrt(mesh.n) < 1e-12  # A_L 1 = 0 element by element
+    st2, _ = sem.sem_probe_bounded_wait(1_000_000_000, 1)
+    assert st2 == sem.SEM_OK
+    mesh.close()
