@@ -265,11 +265,11 @@ extern "C" sem_status sem_server_submit_mesh(sem_server srv, sem_mesh mesh, cons
     // CG work vectors (FP64 CG, or FP32 CG with the FP64 refinement buffers)
     const size_t n = static_cast<size_t>(mesh->n);
     r->est_bytes = mesh->device_bytes + 16 * n + 12 * n + (opts->mixed ? 40 * n : 32 * n) + (8u << 20);
-    std::lock_guard<std::mutex> lock(srv->mu);
     if (r->est_bytes > srv->budget) return fail(SEM_ERR_ARG, "request needs more device memory than the budget");
-    // the caller's streams may go away: finish their work on the mesh now
+    // the caller's streams may go away: finish their work on the mesh now (without the lock)
     for (cudaStream_t u : mesh->used) SEM_CUDA_TRY(cudaStreamSynchronize(u));
     mesh->used.clear();
+    std::lock_guard<std::mutex> lock(srv->mu);
     r->mesh = mesh;
     r->t_submit = now_ms();
     r->ticket = srv->next_ticket++;
