@@ -56,7 +56,7 @@ typedef enum {
 /* SEM_F64: FP64 data and FP64 arithmetic. SEM_F32: FP32 data and arithmetic.
  * SEM_F64X: FP64 data (double* vectors, FP64 stored factors); the local operator runs in
  * double-float arithmetic (pairs of floats with error-free products and sums, about 47
- * significant bits) on the FP32 pipes, which GB300 issues 61 times faster than FP64. Only
+ * significant bits) on the FP32 pipes, which GB300 issues 64 times faster than FP64. Only
  * sem_ax with SEM_AX_STORED (and the CG options' f64_arith) use it, with the float-pair factors of
  * SEM_MESH_F64X_STORED if the mesh has them, else the FP64 ones; every other call treats
  * SEM_F64X like SEM_F64. Values below 2^-126 in magnitude are flushed to zero inside it. */

@@ -1,6 +1,6 @@
 // Local operator A_L = D^T G D (Eq. 4, Section 3.1) for FP64 data with stored FP64 factors,
 // computed in double-float arithmetic on the FP32 pipes (k_df.cuh): GB300 issues FP32
-// FMAs 61 times faster than FP64 ones, and the FP64 kernel is bound by the FP64 pipe.
+// FMAs 64 times faster than FP64 ones, and the FP64 kernel is bound by the FP64 pipe.
 //
 // Same decomposition as k_ax: thread t of an element contracts whole lines of NP values
 // (its i-row, its j-line and its k-column) in registers through the even/odd split of D and

@@ -2,7 +2,9 @@
 // preconditioner). Steps 9-11 are fused into one pass (Section 5.1's loop fusion):
 //   x += alpha p;  r -= alpha w;  z = M^-1 r;  partials of <r, z, c> and <r, r, c>,
 // and the last block to finish forms rho, beta, the iteration count and the stopping
-// decision on the device, so the host never waits inside an iteration.
+// decision on the device, so the host never waits inside an iteration. With the FP32 and
+// double-float operators the x update (one iteration late) and z = M^-1 r move into the
+// operator's prologue (fused update kernel; k_cg_flush adds the last pending x update).
 //
 // Weights c = 1 / multiplicity come from a per-point multiplicity byte and a 256-entry
 // table of exact reciprocals (interior points have multiplicity 1). Dot products are

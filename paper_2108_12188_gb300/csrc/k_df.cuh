@@ -1,7 +1,7 @@
 // Double-float arithmetic on the FP32 pipes for FP64 data.
 //
 // A value is carried as an unevaluated sum h + l of two floats. GB300 issues FP32 fused
-// multiply-adds 61 times faster than FP64 ones, so FP64 contractions are rewritten as
+// multiply-adds 64 times faster than FP64 ones (128 against 2 per clock per SM), so FP64 contractions are rewritten as
 // error-free transformations on floats:
 //   product   a * b  ->  p = fl(ah bh), e = fma(ah, bh, -p) (exact error), plus the cross
 //                        terms ah bl + al bh (al bl is below the working precision);
