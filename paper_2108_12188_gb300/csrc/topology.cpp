@@ -64,6 +64,35 @@ void parallel_for(int64_t n, int64_t grain, const F& f) {
   for (auto& x : th) x.join();
 }
 
+// Sorts v ascending on all host threads: the chunks are sorted in parallel, then merged
+// pairwise in parallel rounds. With distinct keys the result is that of std::sort.
+template <typename T>
+void parallel_sort(std::vector<T>& v) {
+  const int64_t n = static_cast<int64_t>(v.size());
+  const unsigned hw = std::thread::hardware_concurrency();
+  const int64_t nt = std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(hw == 0 ? 1 : hw, 32), n / 8192));
+  if (nt <= 1) {
+    std::sort(v.begin(), v.end());
+    return;
+  }
+  std::vector<int64_t> bnd(static_cast<size_t>(nt) + 1);
+  for (int64_t t = 0; t <= nt; ++t) bnd[t] = n * t / nt;
+  parallel_for(nt, 1, [&](int64_t t0, int64_t t1) {
+    for (int64_t t = t0; t < t1; ++t) std::sort(v.begin() + bnd[t], v.begin() + bnd[t + 1]);
+  });
+  std::vector<T> tmp(v.size());
+  for (int64_t w = 1; w < nt; w *= 2) {
+    const int64_t pairs = (nt + 2 * w - 1) / (2 * w);
+    parallel_for(pairs, 1, [&](int64_t p0, int64_t p1) {
+      for (int64_t q = p0; q < p1; ++q) {
+        const int64_t a = bnd[2 * w * q], m = bnd[std::min(nt, 2 * w * q + w)], b = bnd[std::min(nt, 2 * w * q + 2 * w)];
+        std::merge(v.begin() + a, v.begin() + m, v.begin() + m, v.begin() + b, tmp.begin() + a);
+      }
+    });
+    v.swap(tmp);
+  }
+}
+
 // Entity of an element-boundary position: dense key of the node, first element holding the
 // entity, number of elements holding it, Dirichlet flag, rank of this element among them.
 struct PosEntity {
@@ -147,14 +176,8 @@ sem_status build_topology(int N, int64_t nv, int64_t E, const int64_t* ev, const
         }
     }
   });
-  parallel_for(2, 1, [&](int64_t b0, int64_t b1) {  // the two sorts side by side
-    for (int64_t w = b0; w < b1; ++w) {
-      if (w == 0)
-        std::sort(erec.begin(), erec.end());
-      else
-        std::sort(frec.begin(), frec.end());
-    }
-  });
+  parallel_sort(erec);
+  parallel_sort(frec);
   std::vector<int64_t> edge_of(E * 12), efirst;
   std::vector<int32_t> ecount;
   std::vector<uint8_t> erank(E * 12);
@@ -259,7 +282,18 @@ sem_status build_topology(int N, int64_t nv, int64_t E, const int64_t* ev, const
       }
 
   // ---- Dirichlet entities: boundary faces (owned by one element; with vertex flags, only
-  // those whose four vertices are flagged) and the edges and vertices of their closure
+  // those whose four vertices are flagged) and the edges and vertices of their closure.
+  // The corners and edges on local face d*2 + s, from the position classification.
+  std::vector<int> lf_corners[6], lf_edges[6];
+  for (int d = 0; d < 3; ++d)
+    for (int s = 0; s < 2; ++s)
+      for (const int32_t r : bpos) {
+        const int q[3] = {r % Np, (r / Np) % Np, r / (Np * Np)};
+        if (q[d] != s * N) continue;
+        std::vector<int>& list = pos[r].cls == 1 ? lf_corners[d * 2 + s] : lf_edges[d * 2 + s];
+        if ((pos[r].cls == 1 || pos[r].cls == 2) && std::find(list.begin(), list.end(), pos[r].idx) == list.end())
+          list.push_back(pos[r].idx);
+      }
   std::vector<uint8_t> fdir(n_faces, 0), edir(n_edges, 0), vdir(nv, 0);
   for (int64_t e = 0; e < E; ++e) {
     const int64_t* v = ev + 8 * e;
@@ -279,12 +313,8 @@ sem_status build_topology(int N, int64_t nv, int64_t E, const int64_t* ev, const
           if (!all) continue;
         }
         fdir[f.face_id[lf]] = 1;
-        for (const int32_t r : bpos) {
-          const int q[3] = {r % Np, (r / Np) % Np, r / (Np * Np)};
-          if (q[d] != s * N) continue;
-          if (pos[r].cls == 1) vdir[v[pos[r].idx]] = 1;
-          if (pos[r].cls == 2) edir[f.edge_id[pos[r].idx]] = 1;
-        }
+        for (const int c : lf_corners[lf]) vdir[v[c]] = 1;
+        for (const int le : lf_edges[lf]) edir[f.edge_id[le]] = 1;
       }
   }
 
@@ -328,7 +358,7 @@ sem_status build_topology(int N, int64_t nv, int64_t E, const int64_t* ev, const
   for (int64_t e = 0; e < E; ++e) base[e + 1] += base[e];
   const int64_t n_glob = base[E];
 
-  // ---- ids: new nodes at first sight, then the nodes first seen in earlier elements
+  // ---- ids of the new nodes of each element (the others get theirs in the segment pass)
   std::unique_ptr<int32_t[]> first_id(new int32_t[n_keys]);
   std::unique_ptr<uint8_t[]> gcount(new uint8_t[n_glob]);  // copies of a boundary node, 0 if interior
   std::unique_ptr<uint8_t[]> gdir(new uint8_t[n_glob]);
@@ -362,21 +392,12 @@ sem_status build_topology(int N, int64_t nv, int64_t E, const int64_t* ev, const
       }
     }
   });
-  parallel_for(E, kGrain, [&](int64_t b0, int64_t b1) {
-    for (int64_t e = b0; e < b1; ++e) {
-      const ElemFrames& f = frames[e];
-      int32_t* glo = T.glo.data() + e * P;
-      for (const int32_t r : bpos) {
-        const PosEntity pe = entity(e, f, pos[r]);
-        if (pe.first != e) glo[r] = first_id[pe.key];
-      }
-    }
-  });
-  first_id.reset();
 
   // ---- gather-scatter segments: boundary nodes in ascending id (chunked prefix sums over
   // the global ids); the copies of a node sit in the ascending list of the elements that hold
-  // its entity, so a copy's slot is its segment's start plus its element's rank in that list
+  // its entity, so a copy's slot is its segment's start plus its element's rank in that list.
+  // The last pass also gives the element-boundary points first seen in earlier elements
+  // their ids.
   HostVec<int32_t> seg_of;
   seg_of.resize(n_glob);  // every element written below
   const int64_t gchunk = int64_t(1) << 20, n_gch = (n_glob + gchunk - 1) / gchunk;
@@ -420,13 +441,16 @@ sem_status build_topology(int N, int64_t nv, int64_t E, const int64_t* ev, const
   parallel_for(E, kGrain, [&](int64_t b0, int64_t b1) {
     for (int64_t e = b0; e < b1; ++e) {
       const ElemFrames& f = frames[e];
+      int32_t* glo = T.glo.data() + e * P;
       for (const int32_t r : bpos) {
         const int64_t loc = e * P + r;
         const PosEntity pe = entity(e, f, pos[r]);
-        T.seg_idx[T.seg_off[seg_of[T.glo[loc]]] + pe.rank] = static_cast<int32_t>(loc);
+        if (pe.first != e) glo[r] = first_id[pe.key];
+        T.seg_idx[T.seg_off[seg_of[glo[r]]] + pe.rank] = static_cast<int32_t>(loc);
       }
     }
   });
+  first_id.reset();
 
   T.N = N;
   T.Np = Np;
