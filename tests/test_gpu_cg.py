@@ -216,3 +216,28 @@ def test_cg_fused_prologue_every_order(sem, N):
         assert res["status"] == sem.SEM_OK, (N, res)
         assert _true_rel(prob, b, x) <= opts.rtol * (1 + 1e-3), N
     mesh.close()
+
+
+@pytest.fixture(scope="module")
+def c1_plain(c1):
+    """The oracle's unpreconditioned CG (Algorithm 1 exactly as the paper states it) on config 1."""
+    m, prob, b, ref, mesh = c1
+    return so.pcg(prob, b, rtol=1e-10, precond=False)
+
+
+@pytest.mark.parametrize("kw", [dict(), dict(variant=1, use_graph=0), dict(f64_arith=1),
+                                dict(mixed=2, inner_rtol=0.1), dict(mixed=2, inner_rtol=0.1, inner_variant=0, use_graph=0)],
+                         ids=["fp64-stored", "fp64-otf-eager", "double-float", "mixed-otf", "mixed-stored-eager"])
+def test_cg_unpreconditioned(sem, c1, c1_plain, kw):
+    """precond = 0: z = r (no M^-1 read; the FP32 operator's prologue copies three vectors
+    instead of four). Same gate as the preconditioned solves against the oracle's plain CG."""
+    m, prob, b, ref, mesh = c1
+    res, x = _solve(sem, mesh, prob, sem.sem_cg_default_opts(rtol=1e-10, precond=0, **kw))
+    assert res["status"] == sem.SEM_OK, res
+    assert _true_rel(prob, b, x) <= 1e-10 * (1 + 1e-3)
+    if not kw.get("mixed"):
+        assert abs(res["iters"] - c1_plain.iterations) <= max(1, 0.02 * c1_plain.iterations), \
+            (res["iters"], c1_plain.iterations)
+    err = np.abs(x.reshape(prob.shape()) - prob.exact_solution()).max()
+    err_ref = np.abs(c1_plain.x - prob.exact_solution()).max()
+    assert abs(err - err_ref) <= 5e-4 * err_ref + (1e-11 if kw.get("mixed") else 0.0), (err, err_ref)
