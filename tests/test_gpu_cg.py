@@ -241,3 +241,30 @@ def test_cg_unpreconditioned(sem, c1, c1_plain, kw):
     err = np.abs(x.reshape(prob.shape()) - prob.exact_solution()).max()
     err_ref = np.abs(c1_plain.x - prob.exact_solution()).max()
     assert abs(err - err_ref) <= 5e-4 * err_ref + (1e-11 if kw.get("mixed") else 0.0), (err, err_ref)
+
+
+def test_cg_partial_dirichlet_and_otf_scale(sem):
+    """Dirichlet nodes only on the bottom and top faces (vertex flags; the side faces keep the
+    natural boundary condition), solved with stored factors, with the one-word-per-point
+    on-the-fly variant (SEM_AX_OTF_SCALE), in double-float and in mixed precision; each
+    solution meets the oracle's true residual, FP64 iterations within 2% of the oracle's."""
+    import torch
+    m = BoxMesh(3, 3, 2, jitter=0.1, seed=9)
+    flags = ((m.vert_xyz[:, 2] < 1e-12) | (m.vert_xyz[:, 2] > 1 - 1e-12)).astype(np.uint8)
+    N = 5
+    prob = so.SemProblem(N, m.vert_xyz, m.elem_verts, dirichlet_vertex_flags=flags)
+    b = prob.rhs()
+    ref = so.pcg(prob, b, rtol=1e-10)
+    mesh = sem.Mesh(N, m.vert_xyz, m.elem_verts, dirichlet_vertex_flags=flags,
+                    flags=sem.SEM_MESH_F64_STORED | sem.SEM_MESH_OTF_SCALE)
+    assert np.array_equal(sem.sem_mesh_get_glo_num(mesh.handle), prob.glo_num)
+    for kw in (dict(), dict(variant=sem.SEM_AX_OTF_SCALE), dict(f64_arith=1),
+               dict(mixed=2, inner_variant=sem.SEM_AX_OTF_SCALE, inner_rtol=0.1)):
+        bd = torch.tensor(b.ravel(), device="cuda")
+        x = torch.zeros_like(bd)
+        res = sem.sem_cg_solve(mesh.handle, bd, x, sem.sem_cg_default_opts(rtol=1e-10, **kw))
+        assert res["status"] == sem.SEM_OK, (kw, res)
+        assert _true_rel(prob, b, x.cpu().numpy()) <= 1e-10 * (1 + 1e-3), kw
+        if not kw.get("mixed"):
+            assert abs(res["iters"] - ref.iterations) <= max(1, 0.02 * ref.iterations), (kw, res["iters"], ref.iterations)
+    mesh.close()
