@@ -41,3 +41,31 @@ def test_bounded_wait_times_out_and_the_context_survives(sem, limit_ms):
     st2, _ = sem.sem_probe_bounded_wait(1_000_000_000, 1)
     assert st2 == sem.SEM_OK
     mesh.close()
+
+
+def test_launch_count_matches_the_kernels_run(sem):
+    """sem_launch_count (the benchmark's gpu_launches) counts every kernel the library runs: one
+    for A_L, one more for the assembly; three per CG iteration, replayed from a graph or not."""
+    import torch
+    m = BoxMesh(3, 2, 2, jitter=0.1, seed=4)
+    mesh = sem.Mesh(4, m.vert_xyz, m.elem_verts)
+    u = torch.rand(mesh.n, dtype=torch.float64, device="cuda")
+    w = torch.empty_like(u)
+    c0 = sem.sem_launch_count()
+    sem.sem_ax(mesh.handle, sem.SEM_AX_STORED, sem.SEM_F64, u, w, assemble=False)
+    c1 = sem.sem_launch_count()
+    sem.sem_ax(mesh.handle, sem.SEM_AX_STORED, sem.SEM_F64, u, w, assemble=True)
+    c2 = sem.sem_launch_count()
+    assert (c1 - c0, c2 - c1) == (1, 2)
+    b = torch.empty_like(u)
+    sem.sem_rhs_sine(mesh.handle, 1, 1, 1, sem.SEM_F64, b)
+    for graph in (0, 1):
+        x = torch.zeros_like(b)
+        cg = sem.sem_cg_create(mesh.handle, sem.sem_cg_default_opts(rtol=0.0, max_iter=1 << 20, use_graph=graph))
+        sem.sem_cg_start(cg, b, x)
+        c3 = sem.sem_launch_count()
+        sem.sem_cg_iterate(cg, 5)
+        sem.sem_cg_query(cg)
+        assert sem.sem_launch_count() - c3 == 15, graph
+        sem.sem_cg_destroy(cg)
+    mesh.close()
