@@ -321,24 +321,28 @@ sem_status build_topology(int N, int64_t nv, int64_t E, const int64_t* ev, const
   // ---- the entity of a boundary position of element e
   const int64_t Nm1 = N - 1;
   const int64_t K_e = nv, K_f = K_e + n_edges * Nm1, n_keys = K_f + n_faces * Nm1 * Nm1;
-  auto entity = [&](int64_t e, const ElemFrames& f, const PosInfo& pi) -> PosEntity {
+  // (the tables are captured as plain pointers: the byte-wide stores of the passes below may
+  // alias anything, and pointers held in the closure need not be reloaded after them)
+  auto entity = [ev, N, Nm1, K_e, K_f, vf = vfirst.data(), vc = vcount.data(), vd = vdir.data(),
+                 vr = vrank.data(), ef = efirst.data(), ec = ecount.data(), ed = edir.data(), er = erank.data(),
+                 ff = ffirst.data(), fc = face_count.data(), fd = fdir.data(),
+                 fr = frank.data()](int64_t e, const ElemFrames& f, const PosInfo& pi) -> PosEntity {
     const int64_t* v = ev + 8 * e;
     if (pi.cls == 1) {
       const int64_t x = v[pi.idx];
-      return {x, vfirst[x], vcount[x], vdir[x], vrank[8 * e + pi.idx]};
+      return {x, vf[x], vc[x], vd[x], vr[8 * e + pi.idx]};
     }
     if (pi.cls == 2) {
       const int64_t id = f.edge_id[pi.idx];
       const int t = f.edge_rev[pi.idx] ? N - pi.c0 : pi.c0;
-      return {K_e + id * Nm1 + (t - 1), efirst[id], ecount[id], edir[id], erank[12 * e + pi.idx]};
+      return {K_e + id * Nm1 + (t - 1), ef[id], ec[id], ed[id], er[12 * e + pi.idx]};
     }
     const int lf = pi.idx;
     const int64_t id = f.face_id[lf];
     const int ps = f.face_oa[lf] == 0 ? pi.c0 : N - pi.c0;
     const int pt = f.face_ob[lf] == 0 ? pi.c1 : N - pi.c1;
     const int p0 = f.face_swap[lf] ? pt : ps, p1 = f.face_swap[lf] ? ps : pt;
-    return {K_f + id * Nm1 * Nm1 + (p0 - 1) * Nm1 + (p1 - 1), ffirst[id], face_count[id], fdir[id],
-            frank[6 * e + lf]};
+    return {K_f + id * Nm1 * Nm1 + (p0 - 1) * Nm1 + (p1 - 1), ff[id], fc[id], fd[id], fr[6 * e + lf]};
   };
 
   // ---- new nodes per element and the first id of each element's new nodes (prefix sum)
@@ -366,27 +370,34 @@ sem_status build_topology(int N, int64_t nv, int64_t E, const int64_t* ev, const
   T.mult.resize(n);
   T.mask.resize(n);
   parallel_for(E, kGrain, [&](int64_t b0, int64_t b1) {
+    const PosInfo* const ps = pos.data();
+    const ElemFrames* const fr = frames.data();
+    int32_t* __restrict__ const fid = first_id.get();
+    uint8_t* __restrict__ const gc = gcount.get();
+    uint8_t* __restrict__ const gd = gdir.get();
     for (int64_t e = b0; e < b1; ++e) {
-      const ElemFrames& f = frames[e];
-      int32_t* glo = T.glo.data() + e * P;
+      const ElemFrames& f = fr[e];
+      int32_t* __restrict__ const glo = T.glo.data() + e * P;
+      uint8_t* __restrict__ const mult = T.mult.data() + e * P;
+      uint8_t* __restrict__ const mask = T.mask.data() + e * P;
       int64_t id = base[e];
       for (int r = 0; r < P; ++r) {
-        const PosInfo pi = pos[r];
+        const PosInfo pi = ps[r];
         if (pi.cls == 0) {  // element interior: a new node, one copy, never on a boundary face
-          gcount[id] = 0;
-          gdir[id] = 0;
-          T.mult[e * P + r] = 1;
-          T.mask[e * P + r] = 0;
+          gc[id] = 0;
+          gd[id] = 0;
+          mult[r] = 1;
+          mask[r] = 0;
           glo[r] = static_cast<int32_t>(id++);
           continue;
         }
         const PosEntity pe = entity(e, f, pi);
-        T.mult[e * P + r] = static_cast<uint8_t>(pe.count);
-        T.mask[e * P + r] = pe.dir;
+        mult[r] = static_cast<uint8_t>(pe.count);
+        mask[r] = pe.dir;
         if (pe.first == e) {
-          first_id[pe.key] = static_cast<int32_t>(id);
-          gcount[id] = static_cast<uint8_t>(pe.count);
-          gdir[id] = pe.dir;
+          fid[pe.key] = static_cast<int32_t>(id);
+          gc[id] = static_cast<uint8_t>(pe.count);
+          gd[id] = pe.dir;
           glo[r] = static_cast<int32_t>(id++);
         }
       }
@@ -439,14 +450,22 @@ sem_status build_topology(int N, int64_t nv, int64_t E, const int64_t* ev, const
   });
   T.seg_idx.resize(T.seg_off[S]);  // every slot written once below
   parallel_for(E, kGrain, [&](int64_t b0, int64_t b1) {
+    const PosInfo* const ps = pos.data();
+    const ElemFrames* const fr = frames.data();
+    const int32_t* const fid = first_id.get();
+    const int32_t* const so = seg_of.data();
+    const int32_t* const off = T.seg_off.data();
+    int32_t* __restrict__ const idx = T.seg_idx.data();
+    const int32_t* const bp = bpos.data();
+    const int64_t nb = static_cast<int64_t>(bpos.size());
     for (int64_t e = b0; e < b1; ++e) {
-      const ElemFrames& f = frames[e];
-      int32_t* glo = T.glo.data() + e * P;
-      for (const int32_t r : bpos) {
-        const int64_t loc = e * P + r;
-        const PosEntity pe = entity(e, f, pos[r]);
-        if (pe.first != e) glo[r] = first_id[pe.key];
-        T.seg_idx[T.seg_off[seg_of[glo[r]]] + pe.rank] = static_cast<int32_t>(loc);
+      const ElemFrames& f = fr[e];
+      int32_t* __restrict__ const glo = T.glo.data() + e * P;
+      for (int64_t q = 0; q < nb; ++q) {
+        const int32_t r = bp[q];
+        const PosEntity pe = entity(e, f, ps[r]);
+        if (pe.first != e) glo[r] = fid[pe.key];
+        idx[off[so[glo[r]]] + pe.rank] = static_cast<int32_t>(e * P + r);
       }
     }
   });
