@@ -64,33 +64,23 @@ void parallel_for(int64_t n, int64_t grain, const F& f) {
   for (auto& x : th) x.join();
 }
 
-// Sorts v ascending on all host threads: the chunks are sorted in parallel, then merged
-// pairwise in parallel rounds. With distinct keys the result is that of std::sort.
-template <typename T>
-void parallel_sort(std::vector<T>& v) {
-  const int64_t n = static_cast<int64_t>(v.size());
-  const unsigned hw = std::thread::hardware_concurrency();
-  const int64_t nt = std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(hw == 0 ? 1 : hw, 32), n / 8192));
-  if (nt <= 1) {
-    std::sort(v.begin(), v.end());
-    return;
+// Sorts records whose first key is a vertex id in [0, nv) lexicographically: a stable counting
+// sort by the first key, then each (small) bucket sorted by the remaining keys on all host
+// threads. With distinct records the result is that of std::sort.
+template <size_t K>
+void sort_by_vertex(std::vector<std::array<int64_t, K>>& rec, int64_t nv) {
+  std::vector<int64_t> start(static_cast<size_t>(nv) + 1, 0);
+  for (const auto& x : rec) ++start[x[0] + 1];
+  for (int64_t v = 0; v < nv; ++v) start[v + 1] += start[v];
+  std::vector<std::array<int64_t, K>> out(rec.size());
+  {
+    std::vector<int64_t> at(start.begin(), start.end() - 1);
+    for (const auto& x : rec) out[at[x[0]]++] = x;
   }
-  std::vector<int64_t> bnd(static_cast<size_t>(nt) + 1);
-  for (int64_t t = 0; t <= nt; ++t) bnd[t] = n * t / nt;
-  parallel_for(nt, 1, [&](int64_t t0, int64_t t1) {
-    for (int64_t t = t0; t < t1; ++t) std::sort(v.begin() + bnd[t], v.begin() + bnd[t + 1]);
+  parallel_for(nv, 4096, [&](int64_t v0, int64_t v1) {
+    for (int64_t v = v0; v < v1; ++v) std::sort(out.begin() + start[v], out.begin() + start[v + 1]);
   });
-  std::vector<T> tmp(v.size());
-  for (int64_t w = 1; w < nt; w *= 2) {
-    const int64_t pairs = (nt + 2 * w - 1) / (2 * w);
-    parallel_for(pairs, 1, [&](int64_t p0, int64_t p1) {
-      for (int64_t q = p0; q < p1; ++q) {
-        const int64_t a = bnd[2 * w * q], m = bnd[std::min(nt, 2 * w * q + w)], b = bnd[std::min(nt, 2 * w * q + 2 * w)];
-        std::merge(v.begin() + a, v.begin() + m, v.begin() + m, v.begin() + b, tmp.begin() + a);
-      }
-    });
-    v.swap(tmp);
-  }
+  rec.swap(out);
 }
 
 // Entity of an element-boundary position: dense key of the node, first element holding the
@@ -176,10 +166,12 @@ sem_status build_topology(int N, int64_t nv, int64_t E, const int64_t* ev, const
         }
     }
   });
-  parallel_sort(erec);
-  parallel_sort(frec);
+  sort_by_vertex(erec, nv);
+  sort_by_vertex(frec, nv);
   std::vector<int64_t> edge_of(E * 12), efirst;
   std::vector<int32_t> ecount;
+  efirst.reserve(E * 12);
+  ecount.reserve(E * 12);
   std::vector<uint8_t> erank(E * 12);
   for (size_t r = 0; r < erec.size(); ++r) {
     if (r == 0 || erec[r][0] != erec[r - 1][0] || erec[r][1] != erec[r - 1][1]) {
@@ -194,6 +186,8 @@ sem_status build_topology(int N, int64_t nv, int64_t E, const int64_t* ev, const
   std::vector<std::array<int64_t, 3>>().swap(erec);
   std::vector<int64_t> face_of(E * 6), ffirst;
   std::vector<int32_t> face_count;
+  ffirst.reserve(E * 6);
+  face_count.reserve(E * 6);
   std::vector<uint8_t> frank(E * 6);
   for (size_t r = 0; r < frec.size(); ++r) {
     if (r == 0 || !std::equal(frec[r].begin(), frec[r].begin() + 4, frec[r - 1].begin())) {
