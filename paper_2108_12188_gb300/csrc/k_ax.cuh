@@ -263,14 +263,6 @@ __global__ void __launch_bounds__(NP * NP * EPB)
         rU[k] = val;
         sA[Stage<NP>::at(i, j, k)] = val;
       }
-      if constexpr (kTmaIn) {
-        __syncthreads();  // the input copies are consumed
-        in_pend = tma_in && grp + gridDim.x < n_groups;
-        if (in_pend && threadIdx.x == 0) {  // next group's, during phases 1-5
-          const int64_t e0 = (grp + gridDim.x) * EPB;
-          issue_in(e0, static_cast<int>(E - e0 < EPB ? E - e0 : EPB));
-        }
-      }
     } else {
 #pragma unroll
       for (int k = 0; k < NP; ++k) {
@@ -288,6 +280,13 @@ __global__ void __launch_bounds__(NP * NP * EPB)
       }
     }
     __syncthreads();
+    if constexpr (kTmaIn) {  // the input copies are consumed: the next group's, during phases 1-5
+      in_pend = tma_in && grp + gridDim.x < n_groups;
+      if (in_pend && threadIdx.x == 0) {
+        const int64_t e0 = (grp + gridDim.x) * EPB;
+        issue_in(e0, static_cast<int>(E - e0 < EPB ? E - e0 : EPB));
+      }
+    }
 
     // phase 1: i-row (j, k) = (i, j) of A -> ur into B; the column -> ut
     T rT[NP];
