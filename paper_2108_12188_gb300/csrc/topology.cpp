@@ -405,7 +405,7 @@ sem_status build_topology(int N, int64_t nv, int64_t E, const int64_t* ev, const
   // their ids.
   HostVec<int32_t> seg_of;
   seg_of.resize(n_glob);  // every element written below
-  const int64_t gchunk = int64_t(1) << 20, n_gch = (n_glob + gchunk - 1) / gchunk;
+  const int64_t gchunk = int64_t(1) << 16, n_gch = (n_glob + gchunk - 1) / gchunk;
   std::vector<int64_t> ch_seg(n_gch + 1, 0), ch_cp(n_gch + 1, 0);
   parallel_for(n_gch, 1, [&](int64_t c0, int64_t c1) {
     for (int64_t c = c0; c < c1; ++c) {
@@ -478,7 +478,7 @@ void build_gs_host(const Topology& T, GsHost& H) {
   const int64_t S = static_cast<int64_t>(T.seg_mask.size());
   auto cls = [](int c) { return c <= 1 ? 0 : c <= 2 ? 1 : c <= 4 ? 2 : c <= 8 ? 3 : 4; };
   // per chunk of segments: how many fall in each class (and copies of the CSR class)
-  const int64_t chunk = int64_t(1) << 18, n_ch = (S + chunk - 1) / chunk;
+  const int64_t chunk = int64_t(1) << 15, n_ch = (S + chunk - 1) / chunk;
   std::vector<std::array<int64_t, 6>> cnt(n_ch + 1, std::array<int64_t, 6>{0, 0, 0, 0, 0, 0});
   parallel_for(n_ch, 1, [&](int64_t c0, int64_t c1) {
     for (int64_t c = c0; c < c1; ++c) {
