@@ -199,7 +199,8 @@ sem_status sem_glsc3(sem_mesh mesh, sem_prec prec, const void* a_dev, const void
  * the array, so calls that overlap on the GPU (other streams or host threads) race and give
  * wrong results; the counter is cleared on `stream` before each launch; the first call on
  * each device looks up the array's device address and must come before any stream capture
- * is started. Async. */
+ * is started; that address is kept for the life of the process, so the call must not be used
+ * after cudaDeviceReset. Async. */
 sem_status sem_glsc3_noalloc(sem_mesh mesh, sem_prec prec, const void* a_dev, const void* b_dev, double* result_dev,
                              void* stream);
 

@@ -36,6 +36,26 @@ void count_launch(int k) {
   if (!t_capturing) g_launches.fetch_add(static_cast<uint64_t>(k), std::memory_order_relaxed);
 }
 
+void note_stream(sem_mesh m, cudaStream_t s) {
+  for (cudaStream_t u : m->used)
+    if (u == s) return;
+  m->used.push_back(s);
+}
+
+sem_status check_mesh(sem_mesh m) {
+  if (!m) return fail(SEM_ERR_ARG, "null mesh");
+  int dev = -1;
+  SEM_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev != m->device) return fail(SEM_ERR_ARG, "the mesh belongs to another CUDA device than the current one");
+  return SEM_OK;
+}
+
+sem_status check_ptr(const void* p, const char* name) {
+  if (!p) return fail(SEM_ERR_ARG, std::string(name) + " is null");
+  if (reinterpret_cast<uintptr_t>(p) % 16 != 0) return fail(SEM_ERR_ARG, std::string(name) + " is not 16-byte aligned");
+  return SEM_OK;
+}
+
 namespace {
 
 // Stream-ordered allocation on `s` (the memory is usable on `s` at once and on other streams
@@ -62,31 +82,11 @@ void dfree(T*& p, cudaStream_t s) {
   p = nullptr;
 }
 
-void note_stream(sem_mesh m, cudaStream_t s) {
-  for (cudaStream_t u : m->used)
-    if (u == s) return;
-  m->used.push_back(s);
-}
-
 #define SEM_TRY(expr)                 \
   do {                                \
     sem_status _s = (expr);           \
     if (_s != SEM_OK) return _s;      \
   } while (0)
-
-sem_status check_mesh(sem_mesh m) {
-  if (!m) return fail(SEM_ERR_ARG, "null mesh");
-  int dev = -1;
-  SEM_CUDA_TRY(cudaGetDevice(&dev));
-  if (dev != m->device) return fail(SEM_ERR_ARG, "the mesh belongs to another CUDA device than the current one");
-  return SEM_OK;
-}
-
-sem_status check_ptr(const void* p, const char* name) {
-  if (!p) return fail(SEM_ERR_ARG, std::string(name) + " is null");
-  if (reinterpret_cast<uintptr_t>(p) % 16 != 0) return fail(SEM_ERR_ARG, std::string(name) + " is not 16-byte aligned");
-  return SEM_OK;
-}
 
 sem_status check_prec(int prec) {
   if (prec != SEM_F64 && prec != SEM_F32 && prec != SEM_F64X)

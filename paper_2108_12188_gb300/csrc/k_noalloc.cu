@@ -14,7 +14,9 @@
 //    cleared on the call's stream before each launch, and calls that overlap on the GPU
 //    (different streams, or different host threads) race on the array and give wrong sums.
 //  - The first call on each device looks up the array's device address with that device
-//    current; make that first call before any stream capture is started.
+//    current; make that first call before any stream capture is started. The address is kept
+//    for the life of the process, so the call must not be used after cudaDeviceReset (or
+//    after the device's primary context has been destroyed and created again).
 #include <mutex>
 
 #include "k_common.cuh"
@@ -78,34 +80,33 @@ using namespace sem;
 
 extern "C" sem_status sem_glsc3_noalloc(sem_mesh m, sem_prec prec, const void* a, const void* b, double* result,
                                         void* stream) {
-  if (!m) return fail(SEM_ERR_ARG, "null mesh");
-  if (prec != SEM_F64 && prec != SEM_F32) return fail(SEM_ERR_ARG, "precision must be SEM_F64 or SEM_F32");
-  if (!a || !b || !result) return fail(SEM_ERR_ARG, "a_dev, b_dev and result_dev must be given");
-  if (reinterpret_cast<uintptr_t>(a) % 16 || reinterpret_cast<uintptr_t>(b) % 16)
-    return fail(SEM_ERR_ARG, "a_dev and b_dev must be 16-byte aligned");
-  int dev = -1;
-  SEM_CUDA_TRY(cudaGetDevice(&dev));
-  if (dev != m->device) return fail(SEM_ERR_ARG, "the mesh belongs to another CUDA device than the current one");
-  if (m->n > static_cast<int64_t>(kNoAllocBlocks) * kNoAllocChunk)
-    return fail(SEM_ERR_ARG, "sem_glsc3_noalloc handles at most " +
-                                 std::to_string(static_cast<int64_t>(kNoAllocBlocks) * kNoAllocChunk) +
-                                 " local points (its static scratch holds " + std::to_string(kNoAllocBlocks) +
-                                 " block partials); this mesh has " + std::to_string(m->n));
-  unsigned char* scratch = nullptr;
-  sem_status st = scratch_address(&scratch);
-  if (st != SEM_OK) return st;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  SEM_CUDA_TRY(cudaMemsetAsync(scratch, 0, kCounterBytes, s));
-  const int grid = static_cast<int>((m->n + kNoAllocChunk - 1) / kNoAllocChunk);
-  if (prec == SEM_F64)
-    k_glsc3_chunked<double><<<grid, kNoAllocThreads, 0, s>>>(m->n, static_cast<const double*>(a),
-                                                              static_cast<const double*>(b), m->mult, m->ctab,
-                                                              scratch, result);
-  else
-    k_glsc3_chunked<float><<<grid, kNoAllocThreads, 0, s>>>(m->n, static_cast<const float*>(a),
-                                                             static_cast<const float*>(b), m->mult, m->ctab,
-                                                             scratch, result);
-  count_launch();
-  SEM_CUDA_TRY(cudaGetLastError());
-  return SEM_OK;
+  return guarded([&]() -> sem_status {
+    sem_status st = check_mesh(m);
+    if (st != SEM_OK) return st;
+    if (prec != SEM_F64 && prec != SEM_F32) return fail(SEM_ERR_ARG, "precision must be SEM_F64 or SEM_F32");
+    if ((st = check_ptr(a, "a_dev")) != SEM_OK || (st = check_ptr(b, "b_dev")) != SEM_OK) return st;
+    if (!result) return fail(SEM_ERR_ARG, "result_dev is null");
+    if (m->n > static_cast<int64_t>(kNoAllocBlocks) * kNoAllocChunk)
+      return fail(SEM_ERR_ARG, "sem_glsc3_noalloc handles at most " +
+                                   std::to_string(static_cast<int64_t>(kNoAllocBlocks) * kNoAllocChunk) +
+                                   " local points (its static scratch holds " + std::to_string(kNoAllocBlocks) +
+                                   " block partials); this mesh has " + std::to_string(m->n));
+    unsigned char* scratch = nullptr;
+    if ((st = scratch_address(&scratch)) != SEM_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    note_stream(m, s);  // sem_mesh_destroy waits for this stream before releasing mult and ctab
+    SEM_CUDA_TRY(cudaMemsetAsync(scratch, 0, kCounterBytes, s));
+    const int grid = static_cast<int>((m->n + kNoAllocChunk - 1) / kNoAllocChunk);
+    if (prec == SEM_F64)
+      k_glsc3_chunked<double><<<grid, kNoAllocThreads, 0, s>>>(m->n, static_cast<const double*>(a),
+                                                                static_cast<const double*>(b), m->mult, m->ctab,
+                                                                scratch, result);
+    else
+      k_glsc3_chunked<float><<<grid, kNoAllocThreads, 0, s>>>(m->n, static_cast<const float*>(a),
+                                                               static_cast<const float*>(b), m->mult, m->ctab,
+                                                               scratch, result);
+    count_launch();
+    SEM_CUDA_TRY(cudaGetLastError());
+    return SEM_OK;
+  });
 }

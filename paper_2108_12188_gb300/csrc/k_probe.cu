@@ -2,8 +2,9 @@
 // thread initialises an mbarrier for a 16-byte copy and waits for it with a time limit. With
 // the copy issued the wait completes; without it nothing ever arrives, the wait gives up after
 // the limit and the kernel reports SEM_ERR_TIMEOUT, the status a local-operator kernel sets
-// when its factor or input copy does not arrive. No copy is left in flight when the kernel
-// ends, and the context stays usable.
+// when its factor or input copy does not arrive. Before leaving after a timeout the kernel
+// waits, again with a time limit, for a copy it had issued; it does not guarantee that such a
+// copy has landed if that second wait also gives up. The context stays usable.
 #include "k_common.cuh"
 #include "k_tma.cuh"
 

@@ -3,7 +3,9 @@
 //
 // A wait that does not complete within kWaitLimitNs (or kSpinLimit polls) returns false; callers then record
 // an error status, stop issuing copies and leave the kernel (all threads of the block agree
-// through __syncthreads_or, so no thread is left at a barrier).
+// through __syncthreads_or, so no thread is left at a barrier). Before leaving, the block waits
+// once more, with the same limit, for the copies it still has in flight; if that wait also gives
+// up, a copy may still be in flight when the block exits (the error status is set either way).
 #pragma once
 
 #include <cstdint>

@@ -37,6 +37,19 @@ sem_status guarded(F&& body) {
 sem_status cuda_fail(cudaError_t e, const char* what);
 void count_launch(int k = 1);
 
+}  // namespace sem
+
+struct sem_mesh_s;
+
+namespace sem {
+
+// Checks shared by the C entry points (api.cpp): a mesh of the current device, a non-null
+// 16-byte aligned device pointer. note_stream records a stream the mesh's memory is used on,
+// so that sem_mesh_destroy waits for it before the memory is released.
+sem_status check_mesh(sem_mesh_s* m);
+sem_status check_ptr(const void* p, const char* name);
+void note_stream(sem_mesh_s* m, cudaStream_t s);
+
 #define SEM_CUDA_TRY(expr)                                    \
   do {                                                        \
     cudaError_t _e = (expr);                                  \

@@ -1,8 +1,10 @@
 """sem_glsc3_noalloc: the weighted inner product for callers that cannot let the library
 allocate device memory (programs that own all device memory through their own pool, or loops
 that cannot take cudaMalloc's device-wide synchronisation). Its scratch is a static device
-array, so it is checked against sem_glsc3 (the allocating entry point) on two calls in a row,
-and its size limit is checked. Kept in a file of its own that pytest collects last."""
+array, so it is checked against sem_glsc3 (the allocating entry point) and against the
+oracle's <a, b, c> on two calls in a row, on meshes whose point counts give one block (fewer
+points than one chunk), a ragged last chunk, and many chunks; and its size limit is checked.
+Kept in a file of its own that pytest collects last."""
 import ctypes
 
 import numpy as np
@@ -13,6 +15,7 @@ from synthetic import BoxMesh, local_field
 pytestmark = pytest.mark.gpu
 
 MAX_POINTS = 4096 * 8192
+CHUNK = 8192
 
 
 @pytest.fixture(scope="module")
@@ -25,16 +28,27 @@ def sem():
     return sem_mod
 
 
+# (nx, ny, nz, N): 5,832 points (one block, which is also the last); 61,440 points (8
+# chunks, the last one short); 658,560 points (81 chunks, the last one short)
+MESHES = [(3, 3, 3, 5), (6, 5, 4, 7), (16, 12, 10, 6)]
+
+
+@pytest.mark.parametrize("shape", MESHES, ids=["one_block", "ragged", "many_chunks"])
 @pytest.mark.parametrize("prec", [0, 1], ids=["f64", "f32"])
-def test_noalloc_matches_glsc3_twice(sem, prec):
+def test_noalloc_matches_glsc3_and_oracle_twice(sem, prec, shape):
     import torch
-    m = BoxMesh(16, 12, 10, jitter=0.1, seed=4)
-    mesh = sem.Mesh(7, m.vert_xyz, m.elem_verts, flags=0)
+    from oracle import sem_oracle as so
+    nx, ny, nz, N = shape
+    m = BoxMesh(nx, ny, nz, jitter=0.1, seed=4)
+    mesh = sem.Mesh(N, m.vert_xyz, m.elem_verts, flags=0)
+    assert mesh.n % CHUNK != 0 and (mesh.n < CHUNK) == (shape == MESHES[0])
     dt = torch.float64 if prec == 0 else torch.float32
     a = torch.tensor(local_field(mesh.n, seed=21), dtype=dt, device="cuda")
     b = torch.tensor(local_field(mesh.n, seed=22), dtype=dt, device="cuda")
     ref = torch.zeros(1, dtype=torch.float64, device="cuda")
     sem.sem_glsc3(mesh.handle, prec, a, b, ref)
+    c = so.number_nodes(N, m.elem_verts).c()
+    want = so.glsc3(a.double().cpu().numpy(), b.double().cpu().numpy(), c)
     lib = sem.load_library()
     stream = torch.cuda.current_stream().cuda_stream
     scale = float(torch.sum(torch.abs(a.double() * b.double())))
@@ -45,6 +59,7 @@ def test_noalloc_matches_glsc3_twice(sem, prec):
         assert st == sem.SEM_OK, lib.sem_last_error()
         torch.cuda.synchronize()
         assert abs(out.item() - ref.item()) <= 1e-13 * scale, (call, out.item(), ref.item())
+        assert abs(out.item() - want) <= 1e-13 * scale, (call, out.item(), want)
     mesh.close()
 
 
