@@ -311,15 +311,44 @@ sem_status sem_cg_iterate_timed(sem_cg cg, int k, double* total_ms_host, double*
 
 sem_status sem_cg_destroy(sem_cg cg); /* waits for the streams the handle was used on */
 
+/* Solves `count` independent problems A_i x_i = b_i (1 <= count <= 256) together by mixed
+ * precision (opts->mixed = 1 or 2, as in sem_cg_solve; opts->inner_variant SEM_AX_OTF or
+ * SEM_AX_AUTO, which here means SEM_AX_OTF): the FP32 inner CG iterations of all problems run in
+ * shared launches over a device-side table of the problems (one operator launch per polynomial
+ * order present, one gather-scatter and one vector-update launch per iteration, replayed as a
+ * CUDA graph of opts->check_every iterations), and the FP64 refinement steps (residual b - A x
+ * with the FP64 operator of opts->variant, x += d) are launched per problem between those runs.
+ * Algorithm 1 with z = M^-1 r; the batching itself has no counterpart in the paper. Every
+ * problem's arithmetic is fixed by the problem alone (partial sums per fixed part of its mesh,
+ * combined in a fixed order), so each x is bit-identical to the x this call gives for the same
+ * problem alone or in any other mix. It may differ in the last bits from sem_cg_solve's x, whose
+ * reductions are split differently. meshes[i]: meshes of the current device (one mesh may serve
+ * several problems); b_dev[i], x_dev[i]: FP64 [n_local of meshes[i]], x_dev[i] holds x0 on entry
+ * and the solution on return, no two x_dev alike; results_host[count] receives each problem's
+ * result (iterations are inner FP32 iterations, outer_iters the refinement steps). Blocks until
+ * every problem has finished; returns SEM_OK if all converged, else the status of the first
+ * problem that did not (results_host says which). Work space is allocated stream-ordered on
+ * `stream` and freed before the call returns. */
+sem_status sem_cg_solve_batch(int count, const sem_mesh* meshes, const double* const* b_dev, double* const* x_dev,
+                              const sem_cg_opts* opts, sem_cg_result* results_host, void* stream);
+
 /* ---- Solve server (continuous batching of Poisson solves) ----
- * Requests are queued on submit and admitted first in, first out when a worker slot is free
- * and the device memory the request needs (estimated from E, N and its options) fits in the
- * budget; each admitted request runs on its own CUDA stream (mesh set-up, right-hand side,
- * sem_cg_solve, copy of x to host memory, release), so admitted solves overlap on the GPU and
- * new requests enter as earlier ones finish. A request's result does not depend on the other
- * requests (same launches and fixed-order reductions as alone). A failing request (invalid
- * mesh, non-convergence) reports its status alone. The server uses the device current at
- * sem_server_create. The paper has no server; this serves its solver (Algorithm 1). */
+ * Requests are queued on submit and admitted first in, first out when the device memory the
+ * request needs (estimated from E, N and its options) fits in the budget and a worker thread is
+ * free; the worker builds the request's mesh and right-hand side on its own CUDA stream. Then:
+ *  - small mixed-precision requests (n_local <= batch_max_points, mixed = 1 or 2, on-the-fly
+ *    inner operator) join the batch: one engine thread advances all of them together in shared
+ *    launches over a device-side table of the admitted solves (as sem_cg_solve_batch does),
+ *    admitting new ones and retiring finished ones between rounds of batch_round_iters
+ *    iterations; the worker is free again as soon as it has handed the solve over;
+ *  - every other request is solved by the worker with sem_cg_solve on its own stream, so these
+ *    solves overlap with each other and with the batch on the GPU.
+ * When a solve ends, x is copied to host memory and the request's device memory is released,
+ * so new requests enter as earlier ones finish. A request's result does not depend on the other
+ * requests: each takes the same path alone and in any mix, and both paths reduce in a fixed
+ * order per request. A failing request (invalid mesh, non-convergence) reports its status alone.
+ * The server uses the device current at sem_server_create. The paper has no server; this serves
+ * its solver (Algorithm 1). */
 typedef struct sem_server_s* sem_server;
 
 typedef struct {
@@ -341,10 +370,22 @@ typedef struct {
   double setup_ms;    /* mesh, right-hand side */
   double solve_ms;    /* CG and copy of x to host memory */
   double latency_ms;  /* submit -> solution available in host memory */
+  int batched;        /* 1 if the request was solved in the batch */
 } sem_server_result;
 
-/* hbm_budget_bytes: device memory the admitted requests may hold together; max_slots: solves
- * running at once (worker threads). */
+typedef struct {
+  size_t hbm_budget_bytes;  /* device memory the admitted requests may hold together */
+  int max_slots;            /* worker threads (1..256): concurrent set-ups and non-batched solves */
+  int64_t batch_max_points; /* requests with at most this many local points join the batch; 0: no batch */
+  int batch_max_solves;     /* solves in the batch at once (1..256) */
+  int batch_round_iters;    /* batched FP32 iterations between admissions and refinement steps (>= 1) */
+} sem_server_config;
+
+/* Defaults: the given budget and slots, batch_max_points 2,097,152, batch_max_solves 64,
+ * batch_round_iters 20. */
+sem_status sem_server_default_config(size_t hbm_budget_bytes, int max_slots, sem_server_config* cfg_host);
+sem_status sem_server_create_config(const sem_server_config* cfg, sem_server* out);
+/* sem_server_create_config with sem_server_default_config(hbm_budget_bytes, max_slots). */
 sem_status sem_server_create(size_t hbm_budget_bytes, int max_slots, sem_server* out);
 /* Copies the request and queues it; never waits for the GPU. SEM_ERR_ARG if the request alone
  * needs more than the budget. */
@@ -361,7 +402,12 @@ sem_status sem_server_submit_mesh(sem_server server, sem_mesh mesh, const double
  * ticket is released (later polls of it return SEM_ERR_ARG). */
 sem_status sem_server_poll(sem_server server, uint64_t ticket, double* x_host, int64_t x_capacity,
                            sem_server_result* res);
+/* queued: waiting for admission; active: admitted and not finished (set-up, batch or solve);
+ * bytes_in_use: their estimated device memory. Any pointer may be NULL. */
 sem_status sem_server_stats(sem_server server, int* queued, int* active, size_t* bytes_in_use);
+/* Counters of the batch engine: rounds run, the most solves in one round, and the mean number
+ * of solves per round. Any pointer may be NULL. */
+sem_status sem_server_batch_stats(sem_server server, int64_t* rounds, int* max_batch, double* mean_batch);
 /* Drops queued requests, waits for the running ones, frees the server. */
 sem_status sem_server_destroy(sem_server server);
 

@@ -36,6 +36,8 @@ void count_launch(int k) {
   if (!t_capturing) g_launches.fetch_add(static_cast<uint64_t>(k), std::memory_order_relaxed);
 }
 
+void set_capturing(bool on) { t_capturing = on; }
+
 void note_stream(sem_mesh m, cudaStream_t s) {
   for (cudaStream_t u : m->used)
     if (u == s) return;
@@ -184,6 +186,8 @@ void resolve_variant(sem_mesh m, sem_prec prec, sem_ax_variant v, sem_ax_variant
   *out_shape = t.valid ? t.shape[vslot(r)] : 0;
 }
 
+}  // namespace
+
 sem_status launch_ax_any(sem_mesh m, sem_prec prec, sem_ax_variant v, bool cg, AxLaunch a, cudaStream_t s) {
   resolve_variant(m, prec, v, &v, &a.shape);
   a.E = m->E;
@@ -226,7 +230,6 @@ sem_status ensure_jacobi(sem_mesh m, cudaStream_t s) {
   return SEM_OK;
 }
 
-}  // namespace
 }  // namespace sem
 
 using namespace sem;

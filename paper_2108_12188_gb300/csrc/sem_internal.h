@@ -35,7 +35,10 @@ sem_status guarded(F&& body) {
   }
 }
 sem_status cuda_fail(cudaError_t e, const char* what);
+// Counts kernel launches (sem_launch_count); launches made while this thread captures a CUDA
+// graph (set_capturing(true)) are not counted, the graph's launch counts them.
 void count_launch(int k = 1);
+void set_capturing(bool on);
 
 }  // namespace sem
 
@@ -49,6 +52,12 @@ namespace sem {
 sem_status check_mesh(sem_mesh_s* m);
 sem_status check_ptr(const void* p, const char* name);
 void note_stream(sem_mesh_s* m, cudaStream_t s);
+
+#define SEM_TRY_STATUS(expr)              \
+  do {                                    \
+    const sem_status _st = (expr);        \
+    if (_st != SEM_OK) return _st;        \
+  } while (0)
 
 #define SEM_CUDA_TRY(expr)                                    \
   do {                                                        \
@@ -145,6 +154,49 @@ struct GsPlan {
   int64_t total() const { return n[0] + n[1] + n[2] + n[3] + nx; }
 };
 
+// ---- batched CG over a table of solves (k_batch.cu, batch.cpp) ----
+// Several independent FP32 CG solves (the inner iteration of mixed-precision refinement,
+// on-the-fly factors, fused prologue) advance together: each batched kernel strides over the
+// work items of every solve in a device-side table. Every work item covers a fixed part of
+// one solve (an element group, a chunk of segments, a chunk of points) and writes its partial
+// sums to that solve's own arrays; per-solve counters let the item that finishes a solve's
+// last part form its scalars in a fixed order. A solve's arithmetic therefore does not depend
+// on which other solves share the table, nor on the launch shapes.
+constexpr int kBatchMax = 256;        // solves in one table
+constexpr int kBatchThreads = 256;    // threads of the gather-scatter, update and flush kernels
+constexpr int kBatchGsSeg = 512;      // segments per gather-scatter work item
+constexpr int kBatchChunk = 4096;     // points per update / flush work item
+
+struct BatchSolve {
+  int NP;                  // points per direction
+  int64_t E, n;
+  const float* coef;       // [E][24] FP32 trilinear coefficients
+  float *x, *p, *r, *w;    // inner CG vectors (x: the correction d)
+  const float* minv;       // Jacobi inverse or null
+  const uint8_t* mult;
+  const double* ctab;
+  GsPlan gs;
+  CgScalars* st;           // inner CG scalars
+  double* ax_part;         // [ax_cnt] partial <p, w> of each element group
+  double* up_part;         // [2 up_cnt] partial <r, z, c>, <r, r, c> of each chunk
+  int* err;
+  int64_t ax_beg, ax_cnt;  // element groups: first item in the work list of its order, count
+  int64_t gs_beg;          // first gather-scatter item in the table's list
+  int64_t gs_at[6];        // local gather-scatter item where the classes of width 2, 4, 8, 1 and the
+                           // CSR lists start; gs_at[5] = the solve's gather-scatter items
+  int64_t up_beg, up_cnt;  // update / flush items (chunks of kBatchChunk points)
+};
+struct BatchOrder {
+  int s_lo, s_hi;  // solves of this order occupy table entries [s_lo, s_hi)
+  int64_t items;   // element groups of those solves
+};
+struct BatchTable {
+  int count;
+  int64_t gs_items, up_items;
+  BatchOrder order[kMaxNp + 1];  // indexed by points per direction
+  BatchSolve s[kBatchMax];
+};
+
 }  // namespace sem
 
 // The mesh object behind the opaque handle.
@@ -231,6 +283,11 @@ inline sem_status launch_ax_f32(int N, sem_ax_variant v, bool cg, const AxLaunch
 // elements per block of shape choice 0 / 1 for N + 1 points per direction (host side)
 int ax_elements_per_block(int N, int shape);
 sem_status launch_ax_f64x(int N, sem_ax_variant v, bool cg_mode, const AxLaunch& a, cudaStream_t s);
+// The local operator of a mesh (api.cpp): resolves SEM_AX_AUTO and the block shape, fills the
+// mesh's data pointers into `a` and launches the kernel of the precision.
+sem_status launch_ax_any(sem_mesh_s* m, sem_prec prec, sem_ax_variant v, bool cg, AxLaunch a, cudaStream_t s);
+// Builds the mesh's Jacobi inverse (FP64 and FP32) once; synchronises `s` when it builds it.
+sem_status ensure_jacobi(sem_mesh_s* m, cudaStream_t s);
 // element type of a precision's data: FP64 for SEM_F64 and SEM_F64X
 inline sem_prec data_prec(sem_prec p) { return p == SEM_F32 ? SEM_F32 : SEM_F64; }
 
@@ -259,6 +316,16 @@ inline bool whole_dot(sem_prec prec) { return prec != SEM_F64; }  // FP32 and do
 inline bool fused_cg(sem_prec prec) { return prec != SEM_F64; }
 sem_status launch_dssum_cg(sem_prec prec, const GsPlan& g, void* w, const void* p, CgScalars* st,
                            const double* ax_partials, int ax_blocks, double* partials, cudaStream_t s);
+// Batched kernels (k_batch.cu) over the device table `t` (host copy `h` gives the orders present
+// and is read on the host only). One CG iteration: an operator launch per order present, then
+// the gather-scatter and the update; the flush ends a run of iterations. launch_batch_status copies
+// every solve's scalars to out[0 .. count).
+int batch_ax_elements_per_group(int NP);
+sem_status launch_batch_ax(int NP, const BatchTable* t, cudaStream_t s);
+sem_status launch_batch_gs(const BatchTable* t, cudaStream_t s);
+sem_status launch_batch_update(const BatchTable* t, cudaStream_t s);
+sem_status launch_batch_flush(const BatchTable* t, cudaStream_t s);
+sem_status launch_batch_status(const BatchTable* t, int count, CgScalars* out, cudaStream_t s);
 // Jacobi: assembled diagonal inverted (0 on Dirichlet nodes) on every element-boundary copy.
 sem_status launch_dssum_invert(const GsPlan& g, const double* d, double* m64, float* m32, cudaStream_t s);
 
@@ -286,5 +353,77 @@ sem_status launch_ir_correct(int64_t n, double* x, const float* d, cudaStream_t 
 // beta = rho_new / rho, p kept; partials needs 2 x gridDim doubles.
 sem_status launch_cg_replace(int64_t n, const float* rnew, float* r, float* z, const float* minv, const uint8_t* mult,
                              const double* ctab, CgScalars* st, double* partials, cudaStream_t s);
+
+}  // namespace sem
+
+namespace sem {
+
+// ---- batched mixed-precision solves (batch.cpp) ----
+// One solve of the batch engine: A x = b on mesh m (FP64 b and x, device), refined in FP64
+// around an FP32 inner CG whose iterations run in the shared batched launches. The engine
+// owns the work space it allocates for the job; the caller keeps m, b and x.
+struct BatchJob {
+  sem_mesh m = nullptr;
+  const double* b = nullptr;
+  double* x = nullptr;
+  sem_cg_opts o{};
+  void* user = nullptr;      // the caller's tag
+  // result (valid once the engine reports the job done)
+  sem_cg_result res{};
+  // engine state
+  int state = 0;
+  int total_inner = 0, outer = 0, before = 0;
+  int64_t groups = 0, chunks = 0;
+  float *r32 = nullptr, *z32 = nullptr, *p32 = nullptr, *w32 = nullptr, *d32 = nullptr, *rr32 = nullptr;
+  double *w64 = nullptr, *r64 = nullptr;
+  CgScalars *ist = nullptr, *ost = nullptr;
+  double *ax_part = nullptr, *up_part = nullptr, *init_part = nullptr, *opart = nullptr;
+  CgScalars ost_h{};  // the last refinement residual's scalars
+};
+
+class BatchEngine {
+ public:
+  BatchEngine() = default;
+  BatchEngine(const BatchEngine&) = delete;
+  BatchEngine& operator=(const BatchEngine&) = delete;
+  ~BatchEngine();
+  // All work is enqueued on `s` (which must outlive the engine).
+  sem_status init(cudaStream_t s);
+  // Checks the job's options (mixed 1 or 2), builds the mesh's Jacobi inverse if needed,
+  // allocates the job's work space on the engine's stream and queues the job.
+  sem_status add(BatchJob* j);
+  // One round: the FP64 refinement steps that are due, then `iters` batched FP32 CG iterations
+  // of every job whose inner solve runs, then their statuses (synchronises the stream).
+  // Finished jobs move to the done list.
+  sem_status round(int iters);
+  std::vector<BatchJob*> take_done();
+  // Frees the job's work space (stream-ordered on the engine's stream).
+  void release(BatchJob* j);
+  size_t running() const { return jobs_.size(); }
+
+ private:
+  sem_status residual(BatchJob* j, CgScalars* host_out);
+  sem_status start_inner(BatchJob* j);
+  void finish(BatchJob* j, int status);
+  sem_status upload_table();
+  sem_status iterate(int iters);
+  cudaStream_t s_ = nullptr;
+  cudaStream_t cap_ = nullptr;  // private stream for graph capture
+  BatchTable* tab_d_ = nullptr;
+  BatchTable* tab_h_ = nullptr;  // pinned
+  CgScalars* stat_d_ = nullptr;
+  CgScalars* stat_h_ = nullptr;  // pinned [kBatchMax]
+  CgScalars* ost_pin_ = nullptr; // pinned [kBatchMax]: refinement residual scalars
+  std::vector<BatchJob*> jobs_;   // not finished
+  std::vector<BatchJob*> table_;  // jobs in the device table, in table order
+  std::vector<BatchJob*> done_;
+  bool dirty_ = true;
+  struct Graph {
+    unsigned orders;
+    int iters;
+    cudaGraphExec_t exec;
+  };
+  std::vector<Graph> graphs_;
+};
 
 }  // namespace sem

@@ -1,17 +1,22 @@
 // Solve server: admits Poisson solve requests of different sizes and orders by a device
-// memory budget and runs the admitted ones concurrently, each on its own non-blocking CUDA
-// stream, so their kernels overlap on the GPU; requests that arrive while others run are
-// admitted as slots and memory free up (continuous batching at the level of solves).
+// memory budget and runs the admitted ones concurrently; requests that arrive while others
+// run are admitted as memory frees up (continuous batching).
 //
 // A request carries its mesh (vertices, connectivity, order), the wave numbers of the
-// manufactured right-hand side and CG options; the worker that takes it builds the mesh,
-// the right-hand side, solves, copies x to host memory and releases everything. A request
-// may instead hand over a mesh the caller built and a host right-hand side. Every
-// device allocation is stream-ordered, so one request's set-up or teardown never waits for
-// the others' kernels. A request that fails (bad mesh, non-convergence) fails alone.
+// manufactured right-hand side and CG options (or a mesh the caller built and a host
+// right-hand side). A worker thread builds the mesh and the right-hand side on its own
+// non-blocking stream. Small mixed-precision requests are then handed to the batch engine
+// thread, which advances all of them together in shared launches over a device-side table of
+// the admitted solves (BatchEngine, batch.cpp), taking new ones in and retiring finished ones
+// between rounds; the worker is free again at once. Other requests are solved by their worker
+// with sem_cg_solve on the worker's stream. Every device allocation is stream-ordered, so one
+// request's set-up or teardown never waits for the others' kernels. A request that fails (bad
+// mesh, non-convergence) fails alone.
 //
-// Results do not depend on what else runs: each solve's launches and reductions are the
-// same as when it runs alone (fixed grids, fixed-order sums, no atomics on values).
+// Results do not depend on what else runs: a request takes the same path alone and in a mix
+// (the path depends on its size and options only), and on both paths its launches and
+// reductions are fixed by the request itself (fixed grids or per-request work items,
+// fixed-order sums, no atomics on values).
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -41,6 +46,7 @@ struct Request {
   sem_cg_opts opts{};
   size_t est_bytes = 0;
   int64_t n_local = 0;
+  bool batched = false;
   // results
   bool done = false;
   sem_server_result res{};
@@ -57,6 +63,8 @@ struct sem_server_s {
   int device = 0;
   size_t budget = 0, in_use = 0;
   int max_slots = 1, active = 0;
+  int64_t batch_max_points = 0;
+  int batch_max_solves = 1, batch_round_iters = 1;
   bool stop = false;
   uint64_t next_ticket = 1;
   std::deque<Request*> queue;
@@ -64,6 +72,13 @@ struct sem_server_s {
   std::mutex mu;
   std::condition_variable cv;
   std::vector<std::thread> workers;
+  // batch engine thread and the solves handed to it (set up, not yet in the engine)
+  std::thread engine;
+  bool engine_stop = false;
+  std::deque<sem::BatchJob*> batch_in;
+  std::condition_variable batch_cv;
+  int64_t batch_rounds = 0, batch_solve_rounds = 0;  // rounds run; sum over rounds of the solves in them
+  int batch_max = 0;                                 // most solves in one round
 };
 
 namespace {
@@ -120,6 +135,24 @@ void run_request(sem_server srv, Request* r) {
   }
   if (st == SEM_OK && cudaMemsetAsync(x, 0, info.n_local * sizeof(double), s) != cudaSuccess) st = SEM_ERR_CUDA;
   const double t1 = now_ms();
+  if (st == SEM_OK && r->batched) {  // hand the solve over to the batch engine
+    if (cudaStreamSynchronize(s) != cudaSuccess) st = SEM_ERR_CUDA;
+    if (st == SEM_OK) {
+      mesh->used.clear();  // this stream has drained and goes away; the engine records its own
+      auto* j = new sem::BatchJob();
+      j->m = mesh;
+      j->b = b;
+      j->x = x;
+      j->o = r->opts;
+      j->user = r;
+      cudaStreamDestroy(s);
+      std::lock_guard<std::mutex> lock(srv->mu);
+      res.setup_ms = t1 - t0;
+      srv->batch_in.push_back(j);
+      srv->batch_cv.notify_all();
+      return;
+    }
+  }
   sem_cg_result cg{};
   if (st == SEM_OK) {
     sem_status solve = sem_cg_solve(mesh, b, x, &r->opts, &cg, s);
@@ -154,11 +187,120 @@ void run_request(sem_server srv, Request* r) {
   res.setup_ms = t1 - t0;
   res.solve_ms = t2 - t1;
   res.latency_ms = t2 - r->t_submit;
+  res.batched = 0;
   r->x = std::move(xh);
   r->done = true;
   srv->in_use -= r->est_bytes;
   --srv->active;
   srv->cv.notify_all();
+}
+
+// A batched solve has ended (or failed to start): x to host memory, release, report.
+void finish_batched(sem_server srv, sem::BatchEngine* eng, sem::BatchJob* j, cudaStream_t es, sem_status st,
+                    double t_handover) {
+  Request* r = static_cast<Request*>(j->user);
+  const int64_t n = j->m->n;
+  std::vector<double> xh;
+  if (st == SEM_OK) {
+    try {
+      xh.resize(static_cast<size_t>(n));
+    } catch (const std::bad_alloc&) {
+      st = SEM_ERR_OOM;
+    }
+  }
+  if (st == SEM_OK && (cudaMemcpyAsync(xh.data(), j->x, xh.size() * sizeof(double), cudaMemcpyDeviceToHost, es) !=
+                           cudaSuccess ||
+                       cudaStreamSynchronize(es) != cudaSuccess))
+    st = SEM_ERR_CUDA;
+  const double t2 = now_ms();
+  if (eng) eng->release(j);
+  cudaFreeAsync(const_cast<double*>(j->b), es);
+  cudaFreeAsync(j->x, es);
+  sem_mesh_destroy(j->m);
+  const sem_cg_result cg = j->res;
+  delete j;
+  std::lock_guard<std::mutex> lock(srv->mu);
+  sem_server_result& res = r->res;
+  res.status = st == SEM_OK ? cg.status : st;
+  res.n_local = n;
+  res.cg = cg;
+  res.cg.time_ms = t2 - t_handover;
+  res.queue_ms = r->t_start - r->t_submit;
+  res.solve_ms = t2 - t_handover;
+  res.latency_ms = t2 - r->t_submit;
+  res.batched = 1;
+  r->x = std::move(xh);
+  r->done = true;
+  srv->in_use -= r->est_bytes;
+  --srv->active;
+  srv->cv.notify_all();
+}
+
+// The batch engine thread: takes handed-over solves into the engine (up to batch_max_solves at
+// once), runs rounds while any solve is running, and reports the solves that end.
+void engine_loop(sem_server srv) {
+  cudaSetDevice(srv->device);
+  cudaStream_t es = nullptr;
+  sem::BatchEngine eng;
+  sem_status est = cudaStreamCreateWithFlags(&es, cudaStreamNonBlocking) == cudaSuccess ? SEM_OK : SEM_ERR_CUDA;
+  if (est == SEM_OK) est = eng.init(es);
+  std::unordered_map<sem::BatchJob*, double> handed;  // hand-over times
+  for (;;) {
+    std::vector<sem::BatchJob*> incoming;
+    {
+      std::unique_lock<std::mutex> lock(srv->mu);
+      if (eng.running() == 0)
+        srv->batch_cv.wait(lock, [&] { return srv->engine_stop || !srv->batch_in.empty(); });
+      if (srv->engine_stop && srv->batch_in.empty() && eng.running() == 0) break;
+      while (!srv->batch_in.empty() &&
+             eng.running() + incoming.size() < static_cast<size_t>(srv->batch_max_solves)) {
+        incoming.push_back(srv->batch_in.front());
+        srv->batch_in.pop_front();
+      }
+    }
+    const double t = now_ms();
+    for (sem::BatchJob* j : incoming) {
+      handed[j] = t;
+      sem_status a = est == SEM_OK ? eng.add(j) : est;
+      if (a != SEM_OK) {
+        finish_batched(srv, nullptr, j, es, a, t);
+        handed.erase(j);
+      }
+    }
+    if (eng.running() > 0) {
+      const int in_round = static_cast<int>(eng.running());
+      sem_status rs = eng.round(srv->batch_round_iters);
+      if (rs != SEM_OK) est = rs;  // the device state of the batch is unknown: fail what runs
+      std::lock_guard<std::mutex> lock(srv->mu);
+      ++srv->batch_rounds;
+      srv->batch_solve_rounds += in_round;
+      if (in_round > srv->batch_max) srv->batch_max = in_round;
+    }
+    for (sem::BatchJob* j : eng.take_done()) {
+      finish_batched(srv, &eng, j, es, SEM_OK, handed[j]);
+      handed.erase(j);
+    }
+    if (est != SEM_OK && eng.running() > 0) {
+      for (auto& hj : handed) finish_batched(srv, &eng, hj.first, es, est, hj.second);
+      handed.clear();
+      break;  // later hand-overs fail at once (below)
+    }
+  }
+  // only after a failure of the engine: report what is still handed over
+  for (;;) {
+    sem::BatchJob* j = nullptr;
+    {
+      std::unique_lock<std::mutex> lock(srv->mu);
+      srv->batch_cv.wait(lock, [&] { return srv->engine_stop || !srv->batch_in.empty(); });
+      if (srv->batch_in.empty()) break;
+      j = srv->batch_in.front();
+      srv->batch_in.pop_front();
+    }
+    finish_batched(srv, nullptr, j, es, est == SEM_OK ? SEM_ERR_CUDA : est, now_ms());
+  }
+  if (es) {
+    cudaStreamSynchronize(es);
+  }
 }
 
 void worker_loop(sem_server srv) {
@@ -189,36 +331,76 @@ void worker_loop(sem_server srv) {
 using sem::fail;
 using sem::guarded;
 
-extern "C" sem_status sem_server_create(size_t hbm_budget_bytes, int max_slots, sem_server* out) {
+namespace {
+
+// The path a request takes: the batch for small mixed-precision solves with the on-the-fly
+// inner operator (the batched kernels' operator), its worker's own stream otherwise.
+bool routes_to_batch(const sem_server_s* srv, int64_t n_local, const sem_cg_opts& o) {
+  return srv->batch_max_points > 0 && n_local <= srv->batch_max_points && (o.mixed == 1 || o.mixed == 2) &&
+         (o.inner_variant == SEM_AX_OTF || o.inner_variant == SEM_AX_AUTO);
+}
+
+}  // namespace
+
+extern "C" sem_status sem_server_default_config(size_t hbm_budget_bytes, int max_slots, sem_server_config* cfg) {
   return guarded([&]() -> sem_status {
-    if (!out) return fail(SEM_ERR_ARG, "out is null");
+    if (!cfg) return fail(SEM_ERR_ARG, "cfg is null");
+    cfg->hbm_budget_bytes = hbm_budget_bytes;
+    cfg->max_slots = max_slots;
+    cfg->batch_max_points = 2097152;
+    cfg->batch_max_solves = 64;
+    cfg->batch_round_iters = 20;
+    return SEM_OK;
+  });
+}
+
+extern "C" sem_status sem_server_create_config(const sem_server_config* cfg, sem_server* out) {
+  return guarded([&]() -> sem_status {
+    if (!out || !cfg) return fail(SEM_ERR_ARG, "null argument");
     *out = nullptr;
-    if (max_slots < 1 || max_slots > 256 || hbm_budget_bytes == 0)
+    if (cfg->max_slots < 1 || cfg->max_slots > 256 || cfg->hbm_budget_bytes == 0)
       return fail(SEM_ERR_ARG, "need 1 <= max_slots <= 256 and a non-zero budget");
+    if (cfg->batch_max_points < 0 || cfg->batch_max_solves < 1 || cfg->batch_max_solves > sem::kBatchMax ||
+        cfg->batch_round_iters < 1)
+      return fail(SEM_ERR_ARG, "need batch_max_points >= 0, 1 <= batch_max_solves <= 256, batch_round_iters >= 1");
     auto srv = std::make_unique<sem_server_s>();
     SEM_CUDA_TRY(cudaGetDevice(&srv->device));
     // keep freed stream-ordered memory in the pool between requests (this process only)
     cudaMemPool_t pool;
     if (cudaDeviceGetDefaultMemPool(&pool, srv->device) == cudaSuccess) {
-      uint64_t keep = hbm_budget_bytes;
+      uint64_t keep = cfg->hbm_budget_bytes;
       cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
     }
-    srv->budget = hbm_budget_bytes;
-    srv->max_slots = max_slots;
+    srv->budget = cfg->hbm_budget_bytes;
+    srv->max_slots = cfg->max_slots;
+    srv->batch_max_points = cfg->batch_max_points;
+    srv->batch_max_solves = cfg->batch_max_solves;
+    srv->batch_round_iters = cfg->batch_round_iters;
     try {
-      for (int q = 0; q < max_slots; ++q) srv->workers.emplace_back(worker_loop, srv.get());
-    } catch (const std::exception&) {  // a worker could not be started: stop the ones that did
+      srv->engine = std::thread(engine_loop, srv.get());
+      for (int q = 0; q < cfg->max_slots; ++q) srv->workers.emplace_back(worker_loop, srv.get());
+    } catch (const std::exception&) {  // a thread could not be started: stop the ones that did
       {
         std::lock_guard<std::mutex> lock(srv->mu);
         srv->stop = true;
+        srv->engine_stop = true;
       }
       srv->cv.notify_all();
+      srv->batch_cv.notify_all();
       for (auto& t : srv->workers) t.join();
-      return fail(SEM_ERR_OOM, "could not start the server's worker threads");
+      if (srv->engine.joinable()) srv->engine.join();
+      return fail(SEM_ERR_OOM, "could not start the server's threads");
     }
     *out = srv.release();
     return SEM_OK;
   });
+}
+
+extern "C" sem_status sem_server_create(size_t hbm_budget_bytes, int max_slots, sem_server* out) {
+  sem_server_config cfg{};
+  const sem_status st = sem_server_default_config(hbm_budget_bytes, max_slots, &cfg);
+  if (st != SEM_OK) return st;
+  return sem_server_create_config(&cfg, out);
 }
 
 extern "C" sem_status sem_server_submit(sem_server srv, const sem_request* req, uint64_t* ticket) {
@@ -238,6 +420,7 @@ extern "C" sem_status sem_server_submit(sem_server srv, const sem_request* req, 
     const size_t Np = static_cast<size_t>(req->N) + 1;
     r->n_local = static_cast<int64_t>(static_cast<size_t>(req->E) * Np * Np * Np);
     r->est_bytes = estimate_bytes(req->E, req->N, req->opts);
+    r->batched = routes_to_batch(srv, r->n_local, r->opts);
     std::lock_guard<std::mutex> lock(srv->mu);
     if (r->est_bytes > srv->budget) return fail(SEM_ERR_ARG, "request needs more device memory than the budget");
     r->t_submit = now_ms();
@@ -265,6 +448,7 @@ extern "C" sem_status sem_server_submit_mesh(sem_server srv, sem_mesh mesh, cons
     // CG work vectors (FP64 CG, or FP32 CG with the FP64 refinement buffers)
     const size_t n = static_cast<size_t>(mesh->n);
     r->est_bytes = mesh->device_bytes + 16 * n + 12 * n + (opts->mixed ? 40 * n : 32 * n) + (8u << 20);
+    r->batched = routes_to_batch(srv, r->n_local, r->opts);
     if (r->est_bytes > srv->budget) return fail(SEM_ERR_ARG, "request needs more device memory than the budget");
     // the caller's streams may go away: finish their work on the mesh now (without the lock)
     for (cudaStream_t u : mesh->used) SEM_CUDA_TRY(cudaStreamSynchronize(u));
@@ -317,6 +501,18 @@ extern "C" sem_status sem_server_stats(sem_server srv, int* queued, int* active,
   });
 }
 
+extern "C" sem_status sem_server_batch_stats(sem_server srv, int64_t* rounds, int* max_batch, double* mean_batch) {
+  return guarded([&]() -> sem_status {
+    if (!srv) return fail(SEM_ERR_ARG, "null server");
+    std::lock_guard<std::mutex> lock(srv->mu);
+    if (rounds) *rounds = srv->batch_rounds;
+    if (max_batch) *max_batch = srv->batch_max;
+    if (mean_batch)
+      *mean_batch = srv->batch_rounds ? static_cast<double>(srv->batch_solve_rounds) / srv->batch_rounds : 0.0;
+    return SEM_OK;
+  });
+}
+
 extern "C" sem_status sem_server_destroy(sem_server srv) {
   return guarded([&]() -> sem_status {
     if (!srv) return SEM_OK;
@@ -327,6 +523,12 @@ extern "C" sem_status sem_server_destroy(sem_server srv) {
     }
     srv->cv.notify_all();
     for (auto& t : srv->workers) t.join();
+    {  // every hand-over has happened: the engine finishes the batch and stops
+      std::lock_guard<std::mutex> lock(srv->mu);
+      srv->engine_stop = true;
+    }
+    srv->batch_cv.notify_all();
+    if (srv->engine.joinable()) srv->engine.join();
     delete srv;
     return SEM_OK;
   });

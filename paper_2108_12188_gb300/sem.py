@@ -30,7 +30,8 @@ EXPORTS = [
     "sem_cg_start", "sem_cg_iterate", "sem_cg_iterate_timed", "sem_cg_query", "sem_cg_destroy", "sem_launch_count", "sem_last_error",
     "sem_status_string", "sem_server_create", "sem_server_submit", "sem_server_poll", "sem_server_stats",
     "sem_server_destroy", "sem_autotune", "sem_autotune_save", "sem_autotune_load", "sem_mesh_info",
-    "sem_server_submit_mesh", "sem_probe_bounded_wait",
+    "sem_server_submit_mesh", "sem_probe_bounded_wait", "sem_cg_solve_batch", "sem_server_default_config",
+    "sem_server_create_config", "sem_server_batch_stats",
 ]
 
 
@@ -81,12 +82,18 @@ class Request(C.Structure):
 
 class ServerResult(C.Structure):
     _fields_ = [("status", C.c_int), ("n_local", C.c_int64), ("cg", CgResult), ("queue_ms", C.c_double),
-                ("setup_ms", C.c_double), ("solve_ms", C.c_double), ("latency_ms", C.c_double)]
+                ("setup_ms", C.c_double), ("solve_ms", C.c_double), ("latency_ms", C.c_double),
+                ("batched", C.c_int)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_ if f != "cg"}
         d["cg"] = self.cg.as_dict()
         return d
+
+
+class ServerConfig(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_size_t), ("max_slots", C.c_int), ("batch_max_points", C.c_int64),
+                ("batch_max_solves", C.c_int), ("batch_round_iters", C.c_int)]
 
 
 _lib = None
@@ -130,10 +137,15 @@ def load_library(path: str | None = None):
         "sem_cg_iterate_timed": [_VP, _I, C.POINTER(_D), C.POINTER(_D), _VP],
         "sem_cg_destroy": [_VP],
         "sem_server_create": [C.c_size_t, _I, C.POINTER(_VP)],
+        "sem_server_default_config": [C.c_size_t, _I, C.POINTER(ServerConfig)],
+        "sem_server_create_config": [C.POINTER(ServerConfig), C.POINTER(_VP)],
+        "sem_cg_solve_batch": [_I, C.POINTER(_VP), C.POINTER(_VP), C.POINTER(_VP), C.POINTER(CgOpts),
+                               C.POINTER(CgResult), _VP],
         "sem_server_submit": [_VP, C.POINTER(Request), C.POINTER(C.c_uint64)],
         "sem_server_submit_mesh": [_VP, _VP, _VP, C.POINTER(CgOpts), C.POINTER(C.c_uint64)],
         "sem_server_poll": [_VP, C.c_uint64, _VP, _I64, C.POINTER(ServerResult)],
         "sem_server_stats": [_VP, C.POINTER(_I), C.POINTER(_I), C.POINTER(C.c_size_t)],
+        "sem_server_batch_stats": [_VP, C.POINTER(_I64), C.POINTER(_I), C.POINTER(_D)],
         "sem_server_destroy": [_VP],
         "sem_autotune": [_VP, _I, _I, C.POINTER(TuneReport), _VP],
         "sem_autotune_save": [C.c_char_p],
@@ -360,6 +372,26 @@ def sem_cg_solve(mesh, b, x, opts=None, stream=None, raise_on=(SEM_ERR_ARG, SEM_
     return res.as_dict()
 
 
+def sem_cg_solve_batch(meshes, bs, xs, opts=None, stream=None,
+                       raise_on=(SEM_ERR_ARG, SEM_ERR_MESH, SEM_ERR_OOM, SEM_ERR_CUDA, SEM_ERR_UNSUPPORTED)) -> list:
+    """Solves the problems (meshes[i], bs[i], xs[i]) together (see include/sem.h); returns one
+    result dict per problem."""
+    import torch
+    k = len(meshes)
+    if not (len(bs) == len(xs) == k):
+        raise ValueError("meshes, bs and xs must have the same length")
+    hm = (_VP * k)(*[m.handle if isinstance(m, Mesh) else m for m in meshes])
+    ns = [sem_mesh_get_info(hm[q])["n_local"] for q in range(k)]
+    hb = (_VP * k)(*[_dev(bs[q], torch.float64, ns[q], "b") for q in range(k)])
+    hx = (_VP * k)(*[_dev(xs[q], torch.float64, ns[q], "x") for q in range(k)])
+    res = (CgResult * k)()
+    o = opts or sem_cg_default_opts(mixed=2, inner_rtol=0.1)
+    st = load_library().sem_cg_solve_batch(k, hm, hb, hx, C.byref(o), res, _stream(stream))
+    if st in raise_on:
+        _check(st)
+    return [res[q].as_dict() for q in range(k)]
+
+
 def sem_cg_create(mesh, opts=None):
     out = _VP()
     _check(load_library().sem_cg_create(mesh, C.byref(opts or sem_cg_default_opts()), C.byref(out)))
@@ -398,9 +430,25 @@ def sem_cg_destroy(cg):
 # solve server
 # ---------------------------------------------------------------------------
 
-def sem_server_create(hbm_budget_bytes: int, max_slots: int):
+def sem_server_default_config(hbm_budget_bytes: int, max_slots: int, **overrides) -> ServerConfig:
+    cfg = ServerConfig()
+    _check(load_library().sem_server_default_config(int(hbm_budget_bytes), int(max_slots), C.byref(cfg)))
+    for k, v in overrides.items():
+        if not hasattr(cfg, k):
+            raise KeyError(k)
+        setattr(cfg, k, v)
+    return cfg
+
+
+def sem_server_create(hbm_budget_bytes: int, max_slots: int, **config):
+    """A server with the default configuration, or with the given sem_server_config fields
+    (batch_max_points, batch_max_solves, batch_round_iters) changed."""
     out = _VP()
-    _check(load_library().sem_server_create(int(hbm_budget_bytes), int(max_slots), C.byref(out)))
+    if config:
+        cfg = sem_server_default_config(hbm_budget_bytes, max_slots, **config)
+        _check(load_library().sem_server_create_config(C.byref(cfg), C.byref(out)))
+    else:
+        _check(load_library().sem_server_create(int(hbm_budget_bytes), int(max_slots), C.byref(out)))
     return out
 
 
@@ -450,6 +498,12 @@ def sem_server_stats(server):
     q, a, b = _I(), _I(), C.c_size_t()
     _check(load_library().sem_server_stats(server, C.byref(q), C.byref(a), C.byref(b)))
     return {"queued": q.value, "active": a.value, "bytes_in_use": b.value}
+
+
+def sem_server_batch_stats(server):
+    r, m, a = _I64(), _I(), _D()
+    _check(load_library().sem_server_batch_stats(server, C.byref(r), C.byref(m), C.byref(a)))
+    return {"rounds": int(r.value), "max_batch": int(m.value), "mean_batch": float(a.value)}
 
 
 def sem_server_destroy(server):

@@ -30,13 +30,18 @@ def _opts(sem, mixed=1):
                                    inner_rtol=1e-5 if mixed == 1 else 0.1, check_every=20)
 
 
-def _solo(sem, m, N, sine, opts):
+def _solo(sem, m, N, sine, opts, batched=False):
+    """The request solved alone by the path the server took: the batched solver for requests
+    the server batched, sem_cg_solve for the others."""
     import torch
     mesh = sem.Mesh(N, m.vert_xyz, m.elem_verts, flags=0)
     b = torch.empty(mesh.n, dtype=torch.float64, device="cuda")
     sem.sem_rhs_sine(mesh.handle, *sine, sem.SEM_F64, b)
     x = torch.zeros_like(b)
-    res = sem.sem_cg_solve(mesh.handle, b, x, opts)
+    if batched:
+        res = sem.sem_cg_solve_batch([mesh], [b], [x], opts)[0]
+    else:
+        res = sem.sem_cg_solve(mesh.handle, b, x, opts)
     out = x.cpu().numpy()
     mesh.close()
     return res, out
@@ -57,11 +62,12 @@ def _drain(sem, srv, tickets):
     return results
 
 
-@pytest.mark.parametrize("mixed", [1, 2], ids=["restarted", "reliable-updates"])
-def test_results_alone_equal_results_in_the_mix(sem, mixed):
+@pytest.mark.parametrize("mixed,batch", [(1, 0), (2, 0), (2, 1 << 21)],
+                         ids=["restarted-streams", "reliable-updates-streams", "reliable-updates-batched"])
+def test_results_alone_equal_results_in_the_mix(sem, mixed, batch):
     opts = _opts(sem, mixed)
     meshes = [BoxMesh(*d, jitter=0.1, seed=40 + q) for q, (d, _, _) in enumerate(REQS)]
-    srv = sem.sem_server_create(8 << 30, 4)
+    srv = sem.sem_server_create(8 << 30, 4, batch_max_points=batch)
     tickets = [sem.sem_server_submit(srv, N, m.vert_xyz, m.elem_verts, sine, opts)
                for m, (_, N, sine) in zip(meshes, REQS)]
     results = _drain(sem, srv, tickets)
@@ -70,7 +76,8 @@ def test_results_alone_equal_results_in_the_mix(sem, mixed):
         res, x = results[t]
         assert res["status"] == sem.SEM_OK, res
         assert res["latency_ms"] >= res["setup_ms"] > 0
-        solo, x_solo = _solo(sem, m, N, sine, opts)
+        assert res["batched"] == int(batch > 0), res
+        solo, x_solo = _solo(sem, m, N, sine, opts, batched=batch > 0)
         assert solo["status"] == sem.SEM_OK and solo["iters"] == res["cg"]["iters"]
         np.testing.assert_array_equal(x, x_solo)  # identical alone and in the mix
     # and one of them against the FP64 oracle's true residual
