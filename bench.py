@@ -11,9 +11,14 @@ value = local points per step / device time per step (GDOF/s), aggregated over r
 Also reported: the local operator alone for FP64/FP32 x stored/on-the-fly factors (with
 L2 flushed between timed calls) with its error against the FP64 oracle on sampled
 elements; the end-to-end rate through sem_cg_solve with pinned host buffers; the oracle
-on the host cores (cpu_baseline); SM clocks during the timed region.
+on the host cores (cpu_baseline); SM clocks during the timed region. Two legs cover the rest
+of the metric (rank 0; --no-legs skips them): solve_c3, the 64^3 full solve to 1e-10 by FP64
+CG, by FP32 CG with FP64 reliable updates and by double-float CG (seconds, iterations, true
+residual, error to the manufactured solution); serve_c5, 1000 served solve requests at one
+arrival rate (p50/p99 latency, solves/s), with the server's batch of small requests.
 
-python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--no-legs]
+python bench.py --workload solve|serve|sweep   (the full solve, serving and order-sweep studies)
 """
 from __future__ import annotations
 
@@ -483,7 +488,9 @@ def run_gpu(args):
                 "kernel": "k_ax<8,double,stored,CG>", "kernel_ms": ax_ms,
                 "hbm_achieved_gbs": ax_bytes / (ax_ms * 1e-3) / 1e9, "hbm_peak_gbs": hbm_gbs,
                 "hbm_frac": ax_bytes / (ax_ms * 1e-3) / 1e9 / hbm_gbs,
-                "peak_source": f"FP64 FMA issue rate (2/clk/SM) x 152 SMs x 2070 MHz; HBM {peak_src}",
+                "peak_source": f"FP64 FMA issue rate (2/clk/SM) x 152 SMs x 2070 MHz, derived (nominal); HBM {peak_src}",
+                "fp64_probe_fma_per_clk_per_sm": [1.6, 1.9],  # FMA-chain probe on GB300 (measured range)
+                "fp64_pipe_active_ncu": 0.845,  # ncu FP64-pipe utilisation of this kernel (profiles/)
                 "per_kernel_ms": {"ax": kernel_ms[0], "gather_scatter": kernel_ms[1], "update": kernel_ms[2]},
                 "step_bytes_algorithmic": cg_bytes_per_point(NORD) * n,
                 "step_hbm_frac": cg_bytes_per_point(NORD) * n / (ms_step * 1e-3) / 1e9 / hbm_gbs}
@@ -581,6 +588,20 @@ def run_gpu(args):
                        "rel_res": r1["rel_res"], "status": sem.sem_status_string(r1["status"])}
     mesh1.close()
 
+    # ---- the solve and serving legs of the metric (rank 0; replicas run the step above only)
+    legs = {}
+    if rank == 0 and not args.no_legs:
+        mesh.close()  # the 32^3 mesh's factors are not needed any more
+        legs["solve_c3"] = solve_leg(sem)
+        torch.cuda.empty_cache()
+        with ClockSampler(local_rank) as clk_s:
+            serve = serve_stream(sem, args.leg_requests, args.leg_rate, 0, args.slots, 2097152)
+        serve["clocks"] = clk_s.summary()
+        serve["workload"] = ("solve requests: n^3 box, n~U{8..40}, N~U{5,7,9}, jitter 0.1h, sine RHS a,b,c~U{1,2,3}, "
+                             "rtol 1e-8 FP32 CG with FP64 reliable updates, Poisson arrivals, 100 GB admission "
+                             "budget, requests of at most 2,097,152 local points batched")
+        legs["serve_c5"] = serve
+
     if rank == 0:
         cpu = run_cpu_baseline()
         out = {
@@ -592,7 +613,7 @@ def run_gpu(args):
                        "l2": "inputs larger than L2 (about 1.1 GB of algorithmic traffic per step)",
                        "gflop_s_eq11": flops_eq11(NORD) * n / (ms_step * 1e-3) / 1e9},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "clocks": clk.summary(), "ax": ax, "cg_4cube_n7": cg_c1, "step_f64x": step_f64x,
+            "clocks": clk.summary(), "ax": ax, "cg_4cube_n7": cg_c1, "step_f64x": step_f64x, **legs,
         }
         print(json.dumps(out))
     mesh.close()
@@ -616,19 +637,18 @@ def solve_metrics(sem, mesh, b, x, xyz):
     return math.sqrt(rr.item() / bb.item()), float(torch.max(torch.abs(x - exact)))
 
 
-def run_solve(args):
-    """Full-solve configuration: 64^3 hexahedra (+-0.15h, seed 2), N = 7, 134,217,728 local
-    points, manufactured sine right-hand side; plain FP64 Jacobi-CG (stored factors), the same
-    with the double-float operator, and FP32 on-the-fly inner Jacobi-CG with FP64 iterative
-    refinement, all to 1e-10 (the double-float operator's own error, about 1e-14 of |A||x|,
-    can leave its true residual above that)."""
+def solve_leg(sem, nel: int = 64, solvers=("fp64_cg", "mixed_reliable", "f64x_cg"), inner_rtol: float = 1e-5) -> dict:
+    """Full-solve configuration: nel^3 hexahedra (+-0.15h, seed 2), N = 7 (64^3: 134,217,728
+    local points), manufactured sine right-hand side, each solver to the relative residual 1e-10:
+      fp64_cg         FP64 Jacobi-CG, stored FP64 factors;
+      mixed_reliable  FP32 Jacobi-CG with on-the-fly factors and FP64 reliable updates (the
+                      true FP64 residual replaces the FP32 one after each 10x reduction);
+      f64x_cg         Jacobi-CG with the double-float operator, restarts from the FP64 residual;
+      mixed_otf       FP32 inner CG to inner_rtol with restarted FP64 refinement.
+    Per solver: device seconds (CUDA events around sem_cg_solve), iterations, the true residual
+    b - A x (FP64 operator) and the max nodal error to sin(pi x) sin(pi y) sin(pi z)."""
     import torch
-    from paper_2108_12188_gb300 import build_lib, sem
     from synthetic import BoxMesh
-    build_lib.build()
-    sem.load_library()
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    nel = args.nel
     t0 = time.perf_counter()
     m = BoxMesh(nel, nel, nel, jitter=JITTER, seed=2)
     mesh = sem.Mesh(NORD, m.vert_xyz, m.elem_verts, flags=sem.SEM_MESH_F64_STORED | sem.SEM_MESH_F64X_STORED)
@@ -644,109 +664,138 @@ def run_solve(args):
     del mj
     for prec in (sem.SEM_F64, sem.SEM_F32):  # block shapes of this order (set-up); used by every variant
         sem.sem_autotune(mesh.handle, prec, reps=5)
-    runs = {}
     configs = {
         "fp64_cg": sem.sem_cg_default_opts(rtol=1e-10, variant=sem.SEM_AX_STORED, check_every=50),
         "f64x_cg": sem.sem_cg_default_opts(rtol=1e-10, variant=sem.SEM_AX_STORED, check_every=50, f64_arith=1),
         "mixed_otf": sem.sem_cg_default_opts(rtol=1e-10, mixed=1, variant=sem.SEM_AX_STORED,
-                                             inner_variant=sem.SEM_AX_OTF, inner_rtol=args.inner_rtol,
-                                             check_every=50),
+                                             inner_variant=sem.SEM_AX_OTF, inner_rtol=inner_rtol, check_every=50),
         "mixed_reliable": sem.sem_cg_default_opts(rtol=1e-10, mixed=2, variant=sem.SEM_AX_STORED,
                                                   inner_variant=sem.SEM_AX_OTF, inner_rtol=0.1, check_every=50),
     }
-    for name, opts in configs.items():
+    runs = {}
+    for name in solvers:
         x.zero_()
         torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        res = sem.sem_cg_solve(mesh.handle, b, x, opts)
-        e1.record()
-        e1.synchronize()
+        with ClockSampler(torch.cuda.current_device()) as clk:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            res = sem.sem_cg_solve(mesh.handle, b, x, configs[name])
+            e1.record()
+            e1.synchronize()
         rel, err = solve_metrics(sem, mesh, b, x, xyz)
         runs[name] = {"seconds": e0.elapsed_time(e1) / 1e3, "host_seconds": res["time_ms"] / 1e3,
                       "iterations": res["iters"], "outer_iterations": res["outer_iters"],
                       "status": sem.sem_status_string(res["status"]), "solver_rel_res": res["rel_res"],
-                      "true_rel_res": rel, "max_err_vs_sine": err}
-    out = {"metric": "CG time to 1e-10 (s)", "value": runs["mixed_reliable"]["seconds"], "unit": "s",
-           "higher_is_better": False, "n_gpus": 1, "dtype": "f64 (outer) / f32 (inner)", "data": "synthetic",
-           "config": {"workload": f"{nel}^3 hexahedra on [0,1]^3, jitter +-0.15h (seed 2), N={NORD}, "
-                                  f"{n} local points, sine right-hand side, rtol 1e-10",
-                      "inner_rtol": args.inner_rtol, "mesh_setup_s": setup_s},
-           **runs, "speedup_mixed_vs_fp64": runs["fp64_cg"]["seconds"] / runs["mixed_reliable"]["seconds"],
-           "speedup_restarted_vs_fp64": runs["fp64_cg"]["seconds"] / runs["mixed_otf"]["seconds"]}
-    print(json.dumps(out))
+                      "true_rel_res": rel, "max_err_vs_sine": err, "clocks": clk.summary()}
     mesh.close()
+    out = {"workload": f"{nel}^3 hexahedra on [0,1]^3, jitter +-0.15h (seed 2), N={NORD}, {n} local points, "
+                       "sine right-hand side, rtol 1e-10", "n_local": n, "mesh_setup_s": setup_s, **runs}
+    if "fp64_cg" in runs and "mixed_reliable" in runs:
+        out["speedup_mixed_reliable_vs_fp64"] = runs["fp64_cg"]["seconds"] / runs["mixed_reliable"]["seconds"]
+    return out
 
 
-def run_serve(args):
-    """Serving configuration: a stream of Poisson-solve requests with Poisson arrivals; each is a
-    box mesh n^3 with n ~ U{8..40}, N ~ U{5,7,9}, interior jitter +-0.1h, right-hand side
-    sin(a pi x) sin(b pi y) sin(c pi z) with a, b, c ~ U{1,2,3}, tolerance 1e-8, FP32 inner CG
-    with FP64 reliable updates (residual replacement after each 10x reduction); admission by a
-    100 GB device-memory budget. Reports p50/p99 latency
-    (submit -> solution in host memory) and solves/s per arrival rate."""
-    import numpy as np
+def run_solve(args):
+    """The full-solve configuration alone, with every solver (see solve_leg)."""
     import torch
     from paper_2108_12188_gb300 import build_lib, sem
-    from synthetic import BoxMesh, splitmix64
     build_lib.build()
     sem.load_library()
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    leg = solve_leg(sem, args.nel, ("fp64_cg", "f64x_cg", "mixed_otf", "mixed_reliable"), args.inner_rtol)
+    print(json.dumps({"metric": "CG time to 1e-10 (s)", "value": leg["mixed_reliable"]["seconds"], "unit": "s",
+                      "higher_is_better": False, "n_gpus": 1, "dtype": "f64 (outer) / f32 (inner)",
+                      "data": "synthetic", "config": {"workload": leg["workload"], "inner_rtol": args.inner_rtol},
+                      **leg}))
+
+
+def serve_stream(sem, requests: int, rate: float, seed: int, slots: int, batch_points: int, round_iters: int = 20):
+    """One request stream through a fresh server: `requests` Poisson-solve requests with Poisson
+    arrivals at `rate` per second (seeded), each an n^3 box with n ~ U{8..40}, N ~ U{5,7,9},
+    jitter 0.1h, sine right-hand side with a, b, c ~ U{1,2,3}, rtol 1e-8, FP32 CG with FP64
+    reliable updates; 100 GB admission budget. Requests of at most batch_points local points run
+    in the server's batch (0: none). Latency = submit -> solution in host memory."""
+    import numpy as np
+    from synthetic import BoxMesh, splitmix64
     opts = sem.sem_cg_default_opts(rtol=1e-8, mixed=2, variant=sem.SEM_AX_OTF, inner_variant=sem.SEM_AX_OTF,
                                    inner_rtol=0.1, check_every=25)
     budget = 100 * 10 ** 9
+    R = requests
+    draws = splitmix64(1000 + seed, 0, 6 * R)
+    srv = sem.sem_server_create(budget, slots, batch_max_points=int(batch_points), batch_round_iters=round_iters)
+    rng_t = np.random.default_rng(2000 + seed)
+    arrivals = np.cumsum(rng_t.exponential(1.0 / rate, size=R))
+    tickets, done, pending = [], {}, set()
+    t0 = time.perf_counter()
+    q = 0
+    while len(done) < R:
+        now = time.perf_counter() - t0
+        while q < R and arrivals[q] <= now:
+            d = draws[6 * q: 6 * q + 6]
+            nel = 8 + int(d[0] % 33)
+            N = (5, 7, 9)[int(d[1] % 3)]
+            sine = tuple(1 + int(v % 3) for v in d[2:5])
+            mesh = BoxMesh(nel, nel, nel, jitter=0.1, seed=int(d[5] % (1 << 31)))
+            t = sem.sem_server_submit(srv, N, mesh.vert_xyz, mesh.elem_verts, sine, opts)
+            tickets.append(t)
+            pending.add(t)
+            q += 1
+        for t in list(pending):
+            r = sem.sem_server_poll(srv, t, want_x=False)
+            if r is not None:
+                sem.sem_server_poll(srv, t, want_x=True)  # take the solution, release the ticket
+                done[t] = r[0]
+                pending.discard(t)
+        time.sleep(0.002)
+    wall = time.perf_counter() - t0
+    bstats = sem.sem_server_batch_stats(srv)
+    sem.sem_server_destroy(srv)
+    lat = np.array([done[t]["latency_ms"] for t in tickets])
+    bat = np.array([done[t]["batched"] for t in tickets], dtype=bool)
+    ok = sum(1 for t in tickets if done[t]["status"] == sem.SEM_OK)
+    pts = sum(done[t]["n_local"] for t in tickets)
+    out = {"arrival_rate_per_s": rate, "requests": R, "ok": ok, "batch_max_points": int(batch_points),
+           "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+           "mean_ms": float(lat.mean()), "solves_per_s": R / wall, "wall_s": wall,
+           "mean_queue_ms": float(np.mean([done[t]["queue_ms"] for t in tickets])),
+           "mean_setup_ms": float(np.mean([done[t]["setup_ms"] for t in tickets])),
+           "mean_solve_ms": float(np.mean([done[t]["solve_ms"] for t in tickets])),
+           "local_points": int(pts), "batched_requests": int(bat.sum()), "batch": bstats}
+    if bat.any():
+        out["batched_p50_ms"] = float(np.percentile(lat[bat], 50))
+        out["batched_p99_ms"] = float(np.percentile(lat[bat], 99))
+    if (~bat).any():
+        out["unbatched_p50_ms"] = float(np.percentile(lat[~bat], 50))
+        out["unbatched_p99_ms"] = float(np.percentile(lat[~bat], 99))
+    return out
+
+
+def run_serve(args):
+    """Serving configuration (see serve_stream) at each arrival rate of --rates, with the
+    server's batch (--batch-points local points at most per batched request) and without it
+    (0). Reports p50/p99 latency and solves/s per rate and setting."""
+    import torch
+    from paper_2108_12188_gb300 import build_lib, sem
+    build_lib.build()
+    sem.load_library()
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     rates = [float(r) for r in args.rates.split(",")]
-    out_rates = []
-    total_points = 0
-    for ri, lam in enumerate(rates):
-        R = args.requests
-        draws = splitmix64(1000 + ri, 0, 6 * R)
-        srv = sem.sem_server_create(budget, args.slots)
-        rng_t = np.random.default_rng(2000 + ri)
-        arrivals = np.cumsum(rng_t.exponential(1.0 / lam, size=R))
-        tickets, done, pending = [], {}, set()
-        t0 = time.perf_counter()
-        q = 0
-        while len(done) < R:
-            now = time.perf_counter() - t0
-            while q < R and arrivals[q] <= now:
-                d = draws[6 * q: 6 * q + 6]
-                nel = 8 + int(d[0] % 33)
-                N = (5, 7, 9)[int(d[1] % 3)]
-                sine = tuple(1 + int(v % 3) for v in d[2:5])
-                mesh = BoxMesh(nel, nel, nel, jitter=0.1, seed=int(d[5] % (1 << 31)))
-                t = sem.sem_server_submit(srv, N, mesh.vert_xyz, mesh.elem_verts, sine, opts)
-                tickets.append((t, nel, N))
-                pending.add(t)
-                q += 1
-            for t in list(pending):
-                r = sem.sem_server_poll(srv, t, want_x=False)
-                if r is not None:
-                    sem.sem_server_poll(srv, t, want_x=True)  # take the solution, release the ticket
-                    done[t] = r[0]
-                    pending.discard(t)
-            time.sleep(0.002)
-        wall = time.perf_counter() - t0
-        sem.sem_server_destroy(srv)
-        lat = np.array([done[t]["latency_ms"] for t, _, _ in tickets])
-        ok = sum(1 for t, _, _ in tickets if done[t]["status"] == sem.SEM_OK)
-        pts = sum(done[t]["n_local"] for t, _, _ in tickets)
-        total_points += pts
-        out_rates.append({"arrival_rate_per_s": lam, "requests": R, "ok": ok,
-                          "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                          "mean_ms": float(lat.mean()), "solves_per_s": R / wall, "wall_s": wall,
-                          "mean_queue_ms": float(np.mean([done[t]["queue_ms"] for t, _, _ in tickets])),
-                          "mean_setup_ms": float(np.mean([done[t]["setup_ms"] for t, _, _ in tickets])),
-                          "mean_solve_ms": float(np.mean([done[t]["solve_ms"] for t, _, _ in tickets])),
-                          "local_points": int(pts)})
-    main = out_rates[-1]
+    settings = [int(b) for b in args.batch_points.split(",")]
+    runs = []
+    for bp in settings:
+        for ri, lam in enumerate(rates):
+            runs.append(serve_stream(sem, args.requests, lam, ri, args.slots, bp))
+            print(json.dumps({"rate": lam, "batch_points": bp, "p50_ms": runs[-1]["p50_ms"],
+                              "p99_ms": runs[-1]["p99_ms"], "solves_per_s": runs[-1]["solves_per_s"]}),
+                  file=sys.stderr)
+    main = runs[0]
     print(json.dumps({
         "metric": "served p50/p99 latency (ms)", "value": main["p50_ms"], "unit": "ms", "higher_is_better": False,
         "n_gpus": 1, "dtype": "f64 (outer) / f32 (inner)", "data": "synthetic",
         "config": {"workload": "solve requests: n^3 box, n~U{8..40}, N~U{5,7,9}, jitter 0.1h, sine RHS a,b,c~U{1,2,3}, "
                                "rtol 1e-8 FP32 CG with FP64 reliable updates, Poisson arrivals, 100 GB admission budget",
-                   "requests_per_rate": args.requests, "slots": args.slots},
-        "p99_ms": main["p99_ms"], "rates": out_rates}))
+                   "requests_per_rate": args.requests, "slots": args.slots, "batch_points": settings},
+        "p99_ms": main["p99_ms"], "runs": runs}))
 
 
 def oracle_ax_rate(N: int, nel: int = 8, reps: int = 3) -> dict:
@@ -839,8 +888,13 @@ def main():
                          "serve: the request-stream latency measurement")
     ap.add_argument("--requests", type=int, default=1000, help="requests per arrival rate (serve)")
     ap.add_argument("--rates", default="1,2,4", help="arrival rates in requests/s (serve)")
-    ap.add_argument("--slots", type=int, default=16, help="concurrent solves (serve)")
+    ap.add_argument("--slots", type=int, default=16, help="worker threads of the server (serve)")
+    ap.add_argument("--batch-points", default="2097152,0",
+                    help="server batch limits in local points to compare, 0 = no batch (serve)")
     ap.add_argument("--nel", type=int, default=64, help="elements per direction of the solve workload")
+    ap.add_argument("--no-legs", action="store_true", help="ax: skip the full-solve and serving legs")
+    ap.add_argument("--leg-requests", type=int, default=1000, help="ax: requests of the serving leg")
+    ap.add_argument("--leg-rate", type=float, default=4.0, help="ax: arrival rate of the serving leg (1/s)")
     ap.add_argument("--inner-rtol", type=float, default=1e-5)
     args = ap.parse_args()
     if args.warmup < 3:

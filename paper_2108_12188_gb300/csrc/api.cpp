@@ -760,7 +760,17 @@ sem_status cg_start(sem_cg c, const void* b, void* x, bool x0_is_zero, cudaStrea
     AxLaunch a{};
     a.u = x;
     a.w = c->w;
-    SEM_TRY(launch_ax_any(m, c->prec, c->variant, false, a, s));
+    // The residual of a (re)start is formed with the native FP64 operator also when the
+    // iterations run in double-float arithmetic: a restart after the recursive residual has
+    // converged then replaces it by the true residual b - A x, and the solve corrects the
+    // double-float operator's own rounding (about 1e-14 of |A| |x|) instead of stalling on it.
+    sem_prec rp = c->prec;
+    sem_ax_variant rv = c->variant;
+    if (rp == SEM_F64X) {
+      rp = SEM_F64;
+      if (rv == SEM_AX_STORED && !m->G64) rv = SEM_AX_OTF;
+    }
+    SEM_TRY(launch_ax_any(m, rp, rv, false, a, s));
     SEM_TRY(launch_dssum(data_prec(c->prec), m->gs, c->w, 1, s));
     ax0 = c->w;
   }
