@@ -709,7 +709,8 @@ def run_solve(args):
                       **leg}))
 
 
-def serve_stream(sem, requests: int, rate: float, seed: int, slots: int, batch_points: int, round_iters: int = 20):
+def serve_stream(sem, requests: int, rate: float, seed: int, slots: int, batch_points: int, round_iters: int = 20,
+                 priorities: int = 1):
     """One request stream through a fresh server: `requests` Poisson-solve requests with Poisson
     arrivals at `rate` per second (seeded), each an n^3 box with n ~ U{8..40}, N ~ U{5,7,9},
     jitter 0.1h, sine right-hand side with a, b, c ~ U{1,2,3}, rtol 1e-8, FP32 CG with FP64
@@ -722,7 +723,8 @@ def serve_stream(sem, requests: int, rate: float, seed: int, slots: int, batch_p
     budget = 100 * 10 ** 9
     R = requests
     draws = splitmix64(1000 + seed, 0, 6 * R)
-    srv = sem.sem_server_create(budget, slots, batch_max_points=int(batch_points), batch_round_iters=round_iters)
+    srv = sem.sem_server_create(budget, slots, batch_max_points=int(batch_points), batch_round_iters=round_iters,
+                                size_priorities=int(priorities))
     rng_t = np.random.default_rng(2000 + seed)
     arrivals = np.cumsum(rng_t.exponential(1.0 / rate, size=R))
     tickets, done, pending = [], {}, set()
@@ -755,6 +757,7 @@ def serve_stream(sem, requests: int, rate: float, seed: int, slots: int, batch_p
     ok = sum(1 for t in tickets if done[t]["status"] == sem.SEM_OK)
     pts = sum(done[t]["n_local"] for t in tickets)
     out = {"arrival_rate_per_s": rate, "requests": R, "ok": ok, "batch_max_points": int(batch_points),
+           "size_priorities": int(priorities),
            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
            "mean_ms": float(lat.mean()), "solves_per_s": R / wall, "wall_s": wall,
            "mean_queue_ms": float(np.mean([done[t]["queue_ms"] for t in tickets])),
@@ -781,20 +784,23 @@ def run_serve(args):
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     rates = [float(r) for r in args.rates.split(",")]
     settings = [int(b) for b in args.batch_points.split(",")]
+    prios = [int(p) for p in args.priorities.split(",")]
     runs = []
-    for bp in settings:
-        for ri, lam in enumerate(rates):
-            runs.append(serve_stream(sem, args.requests, lam, ri, args.slots, bp))
-            print(json.dumps({"rate": lam, "batch_points": bp, "p50_ms": runs[-1]["p50_ms"],
-                              "p99_ms": runs[-1]["p99_ms"], "solves_per_s": runs[-1]["solves_per_s"]}),
-                  file=sys.stderr)
+    for pr in prios:
+        for bp in settings:
+            for ri, lam in enumerate(rates):
+                runs.append(serve_stream(sem, args.requests, lam, ri, args.slots, bp, priorities=pr))
+                print(json.dumps({"rate": lam, "batch_points": bp, "priorities": pr, "p50_ms": runs[-1]["p50_ms"],
+                                  "p99_ms": runs[-1]["p99_ms"], "solves_per_s": runs[-1]["solves_per_s"]}),
+                      file=sys.stderr)
     main = runs[0]
     print(json.dumps({
         "metric": "served p50/p99 latency (ms)", "value": main["p50_ms"], "unit": "ms", "higher_is_better": False,
         "n_gpus": 1, "dtype": "f64 (outer) / f32 (inner)", "data": "synthetic",
         "config": {"workload": "solve requests: n^3 box, n~U{8..40}, N~U{5,7,9}, jitter 0.1h, sine RHS a,b,c~U{1,2,3}, "
                                "rtol 1e-8 FP32 CG with FP64 reliable updates, Poisson arrivals, 100 GB admission budget",
-                   "requests_per_rate": args.requests, "slots": args.slots, "batch_points": settings},
+                   "requests_per_rate": args.requests, "slots": args.slots, "batch_points": settings,
+                   "size_priorities": prios},
         "p99_ms": main["p99_ms"], "runs": runs}))
 
 
@@ -891,6 +897,7 @@ def main():
     ap.add_argument("--slots", type=int, default=16, help="worker threads of the server (serve)")
     ap.add_argument("--batch-points", default="2097152,0",
                     help="server batch limits in local points to compare, 0 = no batch (serve)")
+    ap.add_argument("--priorities", default="1", help="size-ordered stream priorities to compare, 1 on / 0 off (serve)")
     ap.add_argument("--nel", type=int, default=64, help="elements per direction of the solve workload")
     ap.add_argument("--no-legs", action="store_true", help="ax: skip the full-solve and serving legs")
     ap.add_argument("--leg-requests", type=int, default=1000, help="ax: requests of the serving leg")

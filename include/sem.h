@@ -379,10 +379,13 @@ typedef struct {
   int64_t batch_max_points; /* requests with at most this many local points join the batch; 0: no batch */
   int batch_max_solves;     /* solves in the batch at once (1..256) */
   int batch_round_iters;    /* batched FP32 iterations between admissions and refinement steps (>= 1) */
+  int size_priorities;      /* 1: each request's stream gets a CUDA stream priority by its size, the
+                             * smaller the higher (the batch the highest), so short solves are served
+                             * first on a busy GPU; 0: default priority for all */
 } sem_server_config;
 
 /* Defaults: the given budget and slots, batch_max_points 2,097,152, batch_max_solves 64,
- * batch_round_iters 20. */
+ * batch_round_iters 20, size_priorities 1. */
 sem_status sem_server_default_config(size_t hbm_budget_bytes, int max_slots, sem_server_config* cfg_host);
 sem_status sem_server_create_config(const sem_server_config* cfg, sem_server* out);
 /* sem_server_create_config with sem_server_default_config(hbm_budget_bytes, max_slots). */

@@ -64,6 +64,57 @@ __device__ __forceinline__ float div_fast<float>(float a, float b) {
   return __fdividef(a, b);
 }
 
+// On-the-fly geometry along one k-column (i, j) of an element (Section 5.1's rematerialised
+// factors). The trilinear map x = a0 + a1 xi + a2 eta + a3 gam + a4 xi eta + a5 xi gam
+// + a6 eta gam + a7 xi eta gam has the Jacobian columns
+//   g0 = dx/dxi = P0 + gam Q0,  g1 = dx/deta = P1 + gam Q1,  g2 = dx/dgam (constant along k),
+// so the cofactor rows c0 = g1 x g2, c1 = g2 x g0, c2 = g0 x g1 (c_b = det J times row b of
+// J^-1) and det J = g0 . c0 are polynomials in gam of degree 1, 1, 2 and 2. Their coefficients
+// are formed once per column; each point then costs 14 multiply-adds for C and det J, and
+//   G v = (w_i w_j w_k / det J) C (C^T v)
+// 21 more, instead of forming G.
+template <typename T>
+struct OtfColumn {
+  Vec3<T> c0a, c0b, c1a, c1b, c2a, c2b, c2c;
+  T da, db, dc;
+
+  __device__ __forceinline__ void init(const T* __restrict__ a, T xi, T eta) {
+    const Vec3<T> a1{a[3], a[4], a[5]}, a2{a[6], a[7], a[8]}, a3{a[9], a[10], a[11]};
+    const Vec3<T> a4{a[12], a[13], a[14]}, a5{a[15], a[16], a[17]}, a6{a[18], a[19], a[20]};
+    const Vec3<T> a7{a[21], a[22], a[23]};
+    const Vec3<T> g2{a3.x + a5.x * xi + a6.x * eta + a7.x * xi * eta, a3.y + a5.y * xi + a6.y * eta + a7.y * xi * eta,
+                     a3.z + a5.z * xi + a6.z * eta + a7.z * xi * eta};
+    const Vec3<T> P0{a1.x + a4.x * eta, a1.y + a4.y * eta, a1.z + a4.z * eta};
+    const Vec3<T> Q0{a5.x + a7.x * eta, a5.y + a7.y * eta, a5.z + a7.z * eta};
+    const Vec3<T> P1{a2.x + a4.x * xi, a2.y + a4.y * xi, a2.z + a4.z * xi};
+    const Vec3<T> Q1{a6.x + a7.x * xi, a6.y + a7.y * xi, a6.z + a7.z * xi};
+    c0a = cross(P1, g2);
+    c0b = cross(Q1, g2);
+    c1a = cross(g2, P0);
+    c1b = cross(g2, Q0);
+    c2a = cross(P0, P1);
+    const Vec3<T> u = cross(P0, Q1), v = cross(Q0, P1);
+    c2b = {u.x + v.x, u.y + v.y, u.z + v.z};
+    c2c = cross(Q0, Q1);
+    da = dot3(P0, c0a);
+    db = dot3(Q0, c0a) + dot3(P0, c0b);
+    dc = dot3(Q0, c0b);
+  }
+  __device__ __forceinline__ T det(T gam) const { return da + gam * (db + gam * dc); }
+  // (vr, vs, vt) = sc C (C^T (ur, us, ut)) at gam; sc = w_i w_j w_k / det J
+  __device__ __forceinline__ void apply(T gam, T sc, T& ur, T& us, T& ut) const {
+    const Vec3<T> c0{c0a.x + gam * c0b.x, c0a.y + gam * c0b.y, c0a.z + gam * c0b.z};
+    const Vec3<T> c1{c1a.x + gam * c1b.x, c1a.y + gam * c1b.y, c1a.z + gam * c1b.z};
+    const Vec3<T> c2{c2a.x + gam * (c2b.x + gam * c2c.x), c2a.y + gam * (c2b.y + gam * c2c.y),
+                     c2a.z + gam * (c2b.z + gam * c2c.z)};
+    const Vec3<T> q{sc * (c0.x * ur + c1.x * us + c2.x * ut), sc * (c0.y * ur + c1.y * us + c2.y * ut),
+                    sc * (c0.z * ur + c1.z * us + c2.z * ut)};
+    ur = dot3(c0, q);
+    us = dot3(c1, q);
+    ut = dot3(c2, q);
+  }
+};
+
 // Element stride of the stored factors (the mesh pads each element's [6][P] block to 16 bytes).
 template <int NP, typename T>
 __host__ __device__ constexpr int ax_gstride() {
@@ -329,23 +380,12 @@ __global__ void __launch_bounds__(NP * NP * EPB)
     }
 
     // phase 3: (vr, vs, vt) = G (ur, us, ut) on the column
-    // OTF: per-thread parts of the Jacobian columns that do not depend on k
-    Vec3<T> g2{}, P0{}, Q0{}, P1{}, Q1{};
+    // OTF: the column's cofactor polynomials (a0, the centroid, is not needed)
+    OtfColumn<T> geo{};
     T wij = T(0);
     if constexpr (OTF) {
       if (valid) {
-        const T* a = coef + e * 24;  // a0..a7, each (x, y, z); a0 (the centroid) is not needed
-        const T xi = tab.xi[i], eta = tab.xi[j];
-        const Vec3<T> a1{a[3], a[4], a[5]}, a2{a[6], a[7], a[8]}, a3{a[9], a[10], a[11]};
-        const Vec3<T> a4{a[12], a[13], a[14]}, a5{a[15], a[16], a[17]}, a6{a[18], a[19], a[20]};
-        const Vec3<T> a7{a[21], a[22], a[23]};
-        // x(xi,eta,gam) = a0 + a1 xi + a2 eta + a3 gam + a4 xi eta + a5 xi gam + a6 eta gam + a7 xi eta gam
-        g2 = {a3.x + a5.x * xi + a6.x * eta + a7.x * xi * eta, a3.y + a5.y * xi + a6.y * eta + a7.y * xi * eta,
-              a3.z + a5.z * xi + a6.z * eta + a7.z * xi * eta};
-        P0 = {a1.x + a4.x * eta, a1.y + a4.y * eta, a1.z + a4.z * eta};
-        Q0 = {a5.x + a7.x * eta, a5.y + a7.y * eta, a5.z + a7.z * eta};
-        P1 = {a2.x + a4.x * xi, a2.y + a4.y * xi, a2.z + a4.z * xi};
-        Q1 = {a6.x + a7.x * xi, a6.y + a7.y * xi, a6.z + a7.z * xi};
+        geo.init(coef + e * 24, tab.xi[i], tab.xi[j]);
         wij = tab.w[i] * tab.w[j];
       }
     }
@@ -364,21 +404,16 @@ __global__ void __launch_bounds__(NP * NP * EPB)
       T vr, vs, vt;
       if constexpr (OTF) {
         const T gam = tab.xi[k];
-        const Vec3<T> g0{P0.x + gam * Q0.x, P0.y + gam * Q0.y, P0.z + gam * Q0.z};
-        const Vec3<T> g1{P1.x + gam * Q1.x, P1.y + gam * Q1.y, P1.z + gam * Q1.z};
-        const Vec3<T> c0 = cross(g1, g2), c1 = cross(g2, g0), c2 = cross(g0, g1);
         T sc;
         if constexpr (GEO == 2) {
           sc = valid ? scale[base + k * NP2] : T(0);
         } else {
-          const T det = dot3(g0, c0);
-          sc = valid ? div_fast(wij * tab.w[k], det) : T(0);
+          sc = valid ? div_fast(wij * tab.w[k], geo.det(gam)) : T(0);
         }
-        const Vec3<T> q{c0.x * ur + c1.x * us + c2.x * ut, c0.y * ur + c1.y * us + c2.y * ut,
-                        c0.z * ur + c1.z * us + c2.z * ut};
-        vr = sc * dot3(c0, q);
-        vs = sc * dot3(c1, q);
-        vt = sc * dot3(c2, q);
+        vr = ur;
+        vs = us;
+        vt = ut;
+        geo.apply(gam, sc, vr, vs, vt);
       } else {
         const T* gp = sG + slot * GS + k * NP2 + tid;
         const T g11 = gp[0 * P], g12 = gp[1 * P], g13 = gp[2 * P], g22 = gp[3 * P], g23 = gp[4 * P],
@@ -428,16 +463,25 @@ __global__ void __launch_bounds__(NP * NP * EPB)
     }
     __syncthreads();
 
-    // phase 5: w on the column
+    // phase 5: w on the column (FP32 CG mode: the column's part of <p, w> as one multiply-add
+    // chain, added to the compensated block sum once per column)
+    T col = T(0);
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
       const int at = Stage<NP>::at(i, j, k);
       const T acc = sB[at] + sA[at] + rW[k];
       if (valid) w[base + k * NP2] = acc;
       if constexpr (CG) {
-        const bool interior = i > 0 && i < NP - 1 && j > 0 && j < NP - 1 && k > 0 && k < NP - 1;
-        if (valid && (kWholeDot || interior)) dot.add(rU[k], acc);
+        if constexpr (kWholeDot) {
+          col = fma(rU[k], acc, col);
+        } else {
+          const bool interior = i > 0 && i < NP - 1 && j > 0 && j < NP - 1 && k > 0 && k < NP - 1;
+          if (valid && interior) dot.add(rU[k], acc);
+        }
       }
+    }
+    if constexpr (CG && kWholeDot) {
+      if (valid) dot.add_sum(col);
     }
     __syncthreads();  // the staging buffers are free for the next group
   }

@@ -104,21 +104,11 @@ __global__ void __launch_bounds__(NP * NP * EPB)
     }
     __syncthreads();
     // phase 3: (vr, vs, vt) = G (ur, us, ut) with G rebuilt from the element's coefficients:
-    // G v = (w_i w_j w_k / det J) C (C^T v), C the cofactor rows of J
-    Vec3<F> g2{}, P0{}, Q0{}, P1{}, Q1{};
+    // G v = (w_i w_j w_k / det J) C (C^T v), C the cofactor rows of J (OtfColumn)
+    OtfColumn<F> geo{};
     F wij = F(0);
     if (valid) {
-      const F* a = d->coef + e * 24;
-      const F xi = tab.xi[i], eta = tab.xi[j];
-      const Vec3<F> a1{a[3], a[4], a[5]}, a2{a[6], a[7], a[8]}, a3{a[9], a[10], a[11]};
-      const Vec3<F> a4{a[12], a[13], a[14]}, a5{a[15], a[16], a[17]}, a6{a[18], a[19], a[20]};
-      const Vec3<F> a7{a[21], a[22], a[23]};
-      g2 = {a3.x + a5.x * xi + a6.x * eta + a7.x * xi * eta, a3.y + a5.y * xi + a6.y * eta + a7.y * xi * eta,
-            a3.z + a5.z * xi + a6.z * eta + a7.z * xi * eta};
-      P0 = {a1.x + a4.x * eta, a1.y + a4.y * eta, a1.z + a4.z * eta};
-      Q0 = {a5.x + a7.x * eta, a5.y + a7.y * eta, a5.z + a7.z * eta};
-      P1 = {a2.x + a4.x * xi, a2.y + a4.y * xi, a2.z + a4.z * xi};
-      Q1 = {a6.x + a7.x * xi, a6.y + a7.y * xi, a6.z + a7.z * xi};
+      geo.init(d->coef + e * 24, tab.xi[i], tab.xi[j]);
       wij = tab.w[i] * tab.w[j];
     }
     F rR[NP], rS[NP];
@@ -130,18 +120,9 @@ __global__ void __launch_bounds__(NP * NP * EPB)
     }
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
-      const F ur = rR[k], us = rS[k], ut = rT[k];
       const F gam = tab.xi[k];
-      const Vec3<F> g0{P0.x + gam * Q0.x, P0.y + gam * Q0.y, P0.z + gam * Q0.z};
-      const Vec3<F> g1{P1.x + gam * Q1.x, P1.y + gam * Q1.y, P1.z + gam * Q1.z};
-      const Vec3<F> c0 = cross(g1, g2), c1 = cross(g2, g0), c2 = cross(g0, g1);
-      const F det = dot3(g0, c0);
-      const F sc = valid ? div_fast(wij * tab.w[k], det) : F(0);
-      const Vec3<F> v{c0.x * ur + c1.x * us + c2.x * ut, c0.y * ur + c1.y * us + c2.y * ut,
-                      c0.z * ur + c1.z * us + c2.z * ut};
-      rR[k] = sc * dot3(c0, v);
-      rS[k] = sc * dot3(c1, v);
-      rT[k] = sc * dot3(c2, v);
+      const F sc = valid ? div_fast(wij * tab.w[k], geo.det(gam)) : F(0);
+      geo.apply(gam, sc, rR[k], rS[k], rT[k]);
     }
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
@@ -169,18 +150,19 @@ __global__ void __launch_bounds__(NP * NP * EPB)
       }
     }
     __syncthreads();
-    // phase 5: w on the column, and this group's part of <p, w> (over every point)
+    // phase 5: w on the column, and this group's part of <p, w> (over every point; the column
+    // as one multiply-add chain, added to a compensated sum)
     DotAcc<F> dot;
     F* __restrict__ w = d->w;
+    F col = F(0);
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
       const int at = Stage<NP>::at(i, j, k);
       const F acc = sB[at] + sA[at] + rW[k];
-      if (valid) {
-        w[base + k * NP2] = acc;
-        dot.add(rU[k], acc);
-      }
+      if (valid) w[base + k * NP2] = acc;
+      col = fmaf(rU[k], acc, col);
     }
+    if (valid) dot.add_sum(col);
     // (block_sum's barriers also keep the staging buffers until every thread has read them)
     const double s = block_sum(dot.value(), sRed);
     if (threadIdx.x == 0) d->ax_part[grp] = s;

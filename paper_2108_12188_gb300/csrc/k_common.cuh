@@ -171,6 +171,7 @@ template <>
 struct DotAcc<double> {
   double s = 0.0;
   __device__ __forceinline__ void add(double x, double y) { s = fma(x, y, s); }
+  __device__ __forceinline__ void add_sum(double v) { s += v; }
   __device__ __forceinline__ double value() const { return s; }
 };
 
@@ -186,6 +187,14 @@ struct DotAcc<float> {
     const float t = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
     hi = s;
     lo = __fadd_rn(lo, __fadd_rn(t, e));
+  }
+  // adds a partial sum formed elsewhere (Knuth's two-sum; its error goes to the low part)
+  __device__ __forceinline__ void add_sum(float v) {
+    const float s = __fadd_rn(hi, v);
+    const float bb = __fsub_rn(s, hi);
+    const float t = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(v, bb));
+    hi = s;
+    lo = __fadd_rn(lo, t);
   }
   __device__ __forceinline__ double value() const { return static_cast<double>(hi) + static_cast<double>(lo); }
 };

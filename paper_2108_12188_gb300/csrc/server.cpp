@@ -65,6 +65,8 @@ struct sem_server_s {
   int max_slots = 1, active = 0;
   int64_t batch_max_points = 0;
   int batch_max_solves = 1, batch_round_iters = 1;
+  bool size_priorities = true;
+  int prio_least = 0, prio_greatest = 0;  // the device's CUDA stream priority range
   bool stop = false;
   uint64_t next_ticket = 1;
   std::deque<Request*> queue;
@@ -98,6 +100,18 @@ size_t estimate_bytes(int64_t E, int N, const sem_cg_opts& o) {
   return b + (8u << 20);
 }
 
+// CUDA stream priority of a request's work: with size priorities, the fewer local points the
+// higher the priority (the batch engine's stream takes the highest), one level per factor 2
+// above 2^21 points, so that the GPU's block scheduler serves short solves first; otherwise
+// the default priority.
+int request_priority(const sem_server_s* srv, int64_t n_local) {
+  if (!srv->size_priorities || srv->prio_greatest == srv->prio_least) return srv->prio_least;
+  int level = 0;
+  for (int64_t t = int64_t(1) << 21; t < n_local && level < 62; t <<= 1) ++level;
+  const int p = srv->prio_greatest + 1 + level;  // greatest is the numerically lowest
+  return p < srv->prio_least ? p : srv->prio_least;
+}
+
 void run_request(sem_server srv, Request* r) {
   cudaSetDevice(srv->device);
   sem_server_result& res = r->res;
@@ -107,7 +121,8 @@ void run_request(sem_server srv, Request* r) {
   double* x = nullptr;
   sem_status st = SEM_OK;
   const double t0 = now_ms();
-  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) st = SEM_ERR_CUDA;
+  if (cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, request_priority(srv, r->n_local)) != cudaSuccess)
+    st = SEM_ERR_CUDA;
   unsigned flags = 0;
   if (r->opts.variant == SEM_AX_STORED) flags |= r->opts.f64_arith ? SEM_MESH_F64X_STORED : SEM_MESH_F64_STORED;
   if (r->opts.mixed && r->opts.inner_variant == SEM_AX_STORED) flags |= SEM_MESH_F32_STORED;
@@ -242,7 +257,9 @@ void engine_loop(sem_server srv) {
   cudaSetDevice(srv->device);
   cudaStream_t es = nullptr;
   sem::BatchEngine eng;
-  sem_status est = cudaStreamCreateWithFlags(&es, cudaStreamNonBlocking) == cudaSuccess ? SEM_OK : SEM_ERR_CUDA;
+  const int prio = srv->size_priorities ? srv->prio_greatest : srv->prio_least;
+  sem_status est =
+      cudaStreamCreateWithPriority(&es, cudaStreamNonBlocking, prio) == cudaSuccess ? SEM_OK : SEM_ERR_CUDA;
   if (est == SEM_OK) est = eng.init(es);
   std::unordered_map<sem::BatchJob*, double> handed;  // hand-over times
   for (;;) {
@@ -350,6 +367,7 @@ extern "C" sem_status sem_server_default_config(size_t hbm_budget_bytes, int max
     cfg->batch_max_points = 2097152;
     cfg->batch_max_solves = 64;
     cfg->batch_round_iters = 20;
+    cfg->size_priorities = 1;
     return SEM_OK;
   });
 }
@@ -376,6 +394,8 @@ extern "C" sem_status sem_server_create_config(const sem_server_config* cfg, sem
     srv->batch_max_points = cfg->batch_max_points;
     srv->batch_max_solves = cfg->batch_max_solves;
     srv->batch_round_iters = cfg->batch_round_iters;
+    srv->size_priorities = cfg->size_priorities != 0;
+    SEM_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&srv->prio_least, &srv->prio_greatest));
     try {
       srv->engine = std::thread(engine_loop, srv.get());
       for (int q = 0; q < cfg->max_slots; ++q) srv->workers.emplace_back(worker_loop, srv.get());

@@ -93,7 +93,7 @@ class ServerResult(C.Structure):
 
 class ServerConfig(C.Structure):
     _fields_ = [("hbm_budget_bytes", C.c_size_t), ("max_slots", C.c_int), ("batch_max_points", C.c_int64),
-                ("batch_max_solves", C.c_int), ("batch_round_iters", C.c_int)]
+                ("batch_max_solves", C.c_int), ("batch_round_iters", C.c_int), ("size_priorities", C.c_int)]
 
 
 _lib = None
