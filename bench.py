@@ -503,14 +503,17 @@ def run_gpu(args):
                                         ("stored", sem.SEM_AX_STORED, "f32", sem.SEM_F32),
                                         ("otf", sem.SEM_AX_OTF, "f64", sem.SEM_F64),
                                         ("otf", sem.SEM_AX_OTF, "f32", sem.SEM_F32),
+                                        ("otf_tc", sem.SEM_AX_OTF, "f32", sem.SEM_F32),
                                         ("otfscale", sem.SEM_AX_OTF_SCALE, "f64", sem.SEM_F64),
                                         ("otfscale", sem.SEM_AX_OTF_SCALE, "f32", sem.SEM_F32)):
         dt = torch.float32 if prec == sem.SEM_F32 else torch.float64
         u = x0.to(dt)
         w = torch.empty_like(u)
+        if vname == "otf_tc":  # the line contractions on the tensor cores (block shape choice 3)
+            sem.sem_autotune_set(NORD, sem.SEM_F32, sem.SEM_AX_OTF, sem.SEM_TENSOR_SHAPE)
         med, lo, hi = time_ax(sem, mesh, variant, prec, u, w, flush, reps=10, warmup=2, assemble=False)
         med_a, _, _ = time_ax(sem, mesh, variant, prec, u, w, flush, reps=5, warmup=1, assemble=True)
-        byt = ax_bytes_per_point(vname, "f32" if pname == "f32" else "f64", NORD) * n
+        byt = ax_bytes_per_point("otf" if vname == "otf_tc" else vname, "f32" if pname == "f32" else "f64", NORD) * n
         fl = flops_eq11(NORD) * n
         if pname == "f64x":  # FP64 data, FP32-pipe arithmetic: report against the HBM roof
             t_roof = byt / (hbm_gbs * 1e9)
@@ -518,6 +521,8 @@ def run_gpu(args):
             peak_tf = PEAK_FP64_TFLOPS if pname == "f64" else PEAK_FP32_TFLOPS
             t_roof = max(byt / (hbm_gbs * 1e9), fl / (peak_tf * 1e12))
         err = ax_error_vs_oracle(sem, mesh, m, variant, prec) if rank == 0 else None
+        if vname == "otf_tc":
+            sem.sem_autotune_set(NORD, sem.SEM_F32, sem.SEM_AX_OTF, 0)
         ax[f"{pname}_{vname}"] = {
             "ms": med, "ms_min": lo, "ms_max": hi, "gdof_s": n / (med * 1e-3) / 1e9,
             "gflop_s_eq11": fl / (med * 1e-3) / 1e9, "hbm_gbs": byt / (med * 1e-3) / 1e9,

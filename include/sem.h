@@ -216,7 +216,8 @@ sem_status sem_rhs_sine(sem_mesh mesh, int a, int b, int c, sem_prec prec, void*
 /* ---- Autotuning of the local operator ----
  * sem_autotune times every candidate implementation of A_L on this mesh (stored, on-the-fly
  * or on-the-fly with per-point scale where available, times two block shapes: elements per
- * thread block; the per-point-scale variant has one shape)
+ * thread block; the per-point-scale variant has one shape; for FP32 on the fly at N = 7 also
+ * shape 3, the line contractions on the tensor cores: mma.sync TF32 with split operands)
  * with CUDA events over `reps` launches each, and records the fastest for the mesh's order
  * and the precision, process-wide; SEM_AX_AUTO then uses it, and explicit variants use the
  * faster block shape. Synchronises `stream`. sem_autotune_save / sem_autotune_load write and
@@ -224,7 +225,7 @@ sem_status sem_rhs_sine(sem_mesh mesh, int a, int b, int c, sem_prec prec, void*
  * with SEM_ERR_ARG). The paper has no tuner (its kernels are fixed FPGA pipelines). */
 typedef struct {
   int variant;            /* sem_ax_variant */
-  int shape;              /* block shape choice 0 / 1 */
+  int shape;              /* block shape choice 0 / 1, or 3 (tensor cores) */
   int elements_per_block;
   double ms;              /* mean time of one A_L application */
 } sem_tune_entry;
@@ -238,6 +239,12 @@ typedef struct {
 } sem_tune_report;
 
 sem_status sem_autotune(sem_mesh mesh, sem_prec prec, int reps, sem_tune_report* report_host, void* stream);
+/* Sets the block shape choice of one variant for an order and precision by hand (shape 0 or
+ * 1, or 3 = the FP32 on-the-fly operator with its line contractions on the tensor cores, where
+ * compiled: N = 7); SEM_AX_AUTO keeps its choice (or the variant given, if the order and
+ * precision were never tuned). sem_autotune_clear forgets every tuning result. */
+sem_status sem_autotune_set(int N, sem_prec prec, sem_ax_variant variant, int shape);
+sem_status sem_autotune_clear(void);
 sem_status sem_autotune_save(const char* path);
 sem_status sem_autotune_load(const char* path);
 

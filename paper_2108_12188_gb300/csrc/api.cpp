@@ -201,6 +201,7 @@ sem_status launch_ax_any(sem_mesh m, sem_prec prec, sem_ax_variant v, bool cg, A
   if (v == SEM_AX_OTF_SCALE && !a.scale)
     return fail(SEM_ERR_ARG, "per-point scales were not requested at mesh creation (SEM_MESH_OTF_SCALE)");
   if (prec == SEM_F64X) return launch_ax_f64x(m->N, v, cg, a, s);
+  if (a.shape == kTensorShape && ax_tensor_available(m->N, prec, v)) return launch_ax_tc(m->N, cg, a, s);
   return prec == SEM_F64 ? launch_ax_f64(m->N, v, cg, a, s) : launch_ax_f32(m->N, v, cg, a, s);
 }
 
@@ -1237,10 +1238,12 @@ extern "C" sem_status sem_autotune(sem_mesh m, sem_prec prec, int reps, sem_tune
       if (v == SEM_AX_STORED && !has_factors(m, prec)) continue;
       if (v != SEM_AX_STORED && prec == SEM_F64X) continue;
       if (v == SEM_AX_OTF_SCALE && !has_scales(m)) continue;
-      for (int shape = 0; shape < 2 && st == SEM_OK; ++shape) {
+      for (int shape : {0, 1, kTensorShape}) {
+        if (st != SEM_OK) break;
         if (shape == 1 && (prec == SEM_F64X || v == SEM_AX_OTF_SCALE ||
                            ax_elements_per_block(m->N, 1) == ax_elements_per_block(m->N, 0)))
           continue;
+        if (shape == kTensorShape && !ax_tensor_available(m->N, prec, v)) continue;
         AxLaunch a{};
         a.u = u;
         a.w = w;
@@ -1252,6 +1255,7 @@ extern "C" sem_status sem_autotune(sem_mesh m, sem_prec prec, int reps, sem_tune
         a.scale = prec == SEM_F32 ? static_cast<const void*>(m->scale32) : static_cast<const void*>(m->scale64);
         auto launch = [&] {
           if (prec == SEM_F64X) return launch_ax_f64x(m->N, v, false, a, s);
+          if (shape == kTensorShape) return launch_ax_tc(m->N, false, a, s);
           return prec == SEM_F64 ? launch_ax_f64(m->N, v, false, a, s) : launch_ax_f32(m->N, v, false, a, s);
         };
         for (int q = 0; q < 2 && st == SEM_OK; ++q) st = launch();
@@ -1265,7 +1269,7 @@ extern "C" sem_status sem_autotune(sem_mesh m, sem_prec prec, int reps, sem_tune
         sem_tune_entry& c = rep->candidates[rep->n_candidates++];
         c.variant = v;
         c.shape = shape;
-        c.elements_per_block = prec == SEM_F64X ? 0 : ax_elements_per_block(m->N, shape);
+        c.elements_per_block = prec == SEM_F64X ? 0 : shape == kTensorShape ? 1 : ax_elements_per_block(m->N, shape);
         c.ms = ms / reps;
       }
     }
@@ -1296,6 +1300,36 @@ extern "C" sem_status sem_autotune(sem_mesh m, sem_prec prec, int reps, sem_tune
     }
     std::lock_guard<std::mutex> lock(g_tune_mu);
     g_tune[prec][m->N] = t;
+    return SEM_OK;
+  });
+}
+
+extern "C" sem_status sem_autotune_set(int N, sem_prec prec, sem_ax_variant variant, int shape) {
+  return guarded([&]() -> sem_status {
+    if (N < 1 || N > SEM_MAX_N) return fail(SEM_ERR_UNSUPPORTED, "polynomial order out of range");
+    SEM_TRY(check_prec(prec));
+    if (variant != SEM_AX_STORED && variant != SEM_AX_OTF && variant != SEM_AX_OTF_SCALE)
+      return fail(SEM_ERR_ARG, "variant must be SEM_AX_STORED, SEM_AX_OTF or SEM_AX_OTF_SCALE");
+    const bool ok = shape == 0 || (shape == 1 && variant != SEM_AX_OTF_SCALE && prec != SEM_F64X) ||
+                    (shape == kTensorShape && ax_tensor_available(N, prec, variant));
+    if (!ok) return fail(SEM_ERR_ARG, "block shape choice not available for this order, precision and variant");
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    TuneSlot& t = g_tune[prec][N];
+    if (!t.valid) {
+      t = TuneSlot{};
+      t.valid = true;
+      t.best = variant;
+    }
+    t.shape[vslot(variant)] = shape;
+    return SEM_OK;
+  });
+}
+
+extern "C" sem_status sem_autotune_clear(void) {
+  return guarded([&]() -> sem_status {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    for (auto& row : g_tune)
+      for (TuneSlot& t : row) t = TuneSlot{};
     return SEM_OK;
   });
 }
@@ -1333,7 +1367,8 @@ extern "C" sem_status sem_autotune_load(const char* path) {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     while (f >> p >> N >> best >> s0 >> s1 >> s2 >> m0 >> m1 >> m2) {
       if (p < 0 || p > 2 || N < 1 || N > SEM_MAX_N || !(best == 0 || best == 1 || best == 3) || s0 < 0 || s0 > 1 ||
-          s1 < 0 || s1 > 1 || s2 != 0)
+          !(s1 == 0 || s1 == 1 || (s1 == kTensorShape && ax_tensor_available(N, static_cast<sem_prec>(p), SEM_AX_OTF))) ||
+          s2 != 0)
         return fail(SEM_ERR_ARG, "corrupt tuning table");
       TuneSlot& t = g_tune[p][N];
       t.valid = true;

@@ -282,6 +282,11 @@ inline sem_status launch_ax_f32(int N, sem_ax_variant v, bool cg, const AxLaunch
 }
 // elements per block of shape choice 0 / 1 for N + 1 points per direction (host side)
 int ax_elements_per_block(int N, int shape);
+// Block shape choice kTensorShape: the FP32 on-the-fly operator with its line contractions on
+// the tensor cores (k_ax_tc.cu), where compiled (ax_tensor_available); one element per block.
+constexpr int kTensorShape = 3;
+bool ax_tensor_available(int N, sem_prec prec, sem_ax_variant v);
+sem_status launch_ax_tc(int N, bool cg_mode, const AxLaunch& a, cudaStream_t s);
 sem_status launch_ax_f64x(int N, sem_ax_variant v, bool cg_mode, const AxLaunch& a, cudaStream_t s);
 // The local operator of a mesh (api.cpp): resolves SEM_AX_AUTO and the block shape, fills the
 // mesh's data pointers into `a` and launches the kernel of the precision.

@@ -31,7 +31,7 @@ EXPORTS = [
     "sem_status_string", "sem_server_create", "sem_server_submit", "sem_server_poll", "sem_server_stats",
     "sem_server_destroy", "sem_autotune", "sem_autotune_save", "sem_autotune_load", "sem_mesh_info",
     "sem_server_submit_mesh", "sem_probe_bounded_wait", "sem_cg_solve_batch", "sem_server_default_config",
-    "sem_server_create_config", "sem_server_batch_stats",
+    "sem_server_create_config", "sem_server_batch_stats", "sem_autotune_set", "sem_autotune_clear",
 ]
 
 
@@ -150,6 +150,8 @@ def load_library(path: str | None = None):
         "sem_autotune": [_VP, _I, _I, C.POINTER(TuneReport), _VP],
         "sem_autotune_save": [C.c_char_p],
         "sem_autotune_load": [C.c_char_p],
+        "sem_autotune_set": [_I, _I, _I, _I],
+        "sem_autotune_clear": [],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -514,6 +516,17 @@ def sem_autotune(mesh, prec, reps=10, stream=None) -> dict:
     rep = TuneReport()
     _check(load_library().sem_autotune(mesh, int(prec), int(reps), C.byref(rep), _stream(stream)))
     return rep.as_dict()
+
+
+def sem_autotune_set(N, prec, variant, shape):
+    _check(load_library().sem_autotune_set(int(N), int(prec), int(variant), int(shape)))
+
+
+def sem_autotune_clear():
+    _check(load_library().sem_autotune_clear())
+
+
+SEM_TENSOR_SHAPE = 3
 
 
 def sem_autotune_save(path):
