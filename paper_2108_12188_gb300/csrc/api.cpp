@@ -124,6 +124,9 @@ void free_mesh(sem_mesh m) {
   }
   dfree(m->gs_xoff, h);
   dfree(m->gs_xidx, h);
+  for (int c = 0; c < kGsClasses; ++c) dfree(m->gs_cg_rec[c], h);
+  dfree(m->gs_cg_xidx, h);
+  dfree(m->cg_perm, h);
   dfree(m->gs_xmsk, h);
   dfree(m->mult, h);
   dfree(m->minv64, h);
@@ -231,6 +234,49 @@ sem_status ensure_jacobi(sem_mesh m, cudaStream_t s) {
   return SEM_OK;
 }
 
+// The CG layout of the operator's output (CgMap) and the gather-scatter plan in it, built once
+// per mesh on its first CG handle: the plan's copy indices mapped on the device.
+sem_status ensure_cg_layout(sem_mesh m, cudaStream_t s) {
+  if (m->cg_perm) return SEM_OK;
+  note_stream(m, s);
+  const int P = m->Np * m->Np * m->Np;
+  size_t bytes = 0;
+  sem_status st = dmalloc(&m->cg_perm, static_cast<size_t>(P), &bytes, s);
+  if (st == SEM_OK) st = launch_cg_perm(m->Np, m->cg_perm, s);
+  CgMap map;
+  map.perm = m->cg_perm;
+  map.P = P;
+  map.magic = ~0ull / static_cast<unsigned long long>(P) + 1ull;
+  GsPlan g = m->gs;
+  for (int c = 0; c < kGsClasses && st == SEM_OK; ++c) {
+    const int64_t cnt = m->gs.n[c] * kGsWidth[c];
+    if (cnt == 0) continue;
+    if ((st = dmalloc(&m->gs_cg_rec[c], static_cast<size_t>(cnt), &bytes, s)) == SEM_OK)
+      st = launch_map_indices(cnt, m->gs_rec[c], m->gs_cg_rec[c], map, s);
+    g.rec[c] = m->gs_cg_rec[c];
+  }
+  if (st == SEM_OK && m->gs_xidx_count > 0) {
+    if ((st = dmalloc(&m->gs_cg_xidx, static_cast<size_t>(m->gs_xidx_count), &bytes, s)) == SEM_OK)
+      st = launch_map_indices(m->gs_xidx_count, m->gs_xidx, m->gs_cg_xidx, map, s);
+    g.xidx = m->gs_cg_xidx;
+  }
+  if (st == SEM_OK) {
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = cuda_fail(e, "cudaStreamSynchronize (CG layout)");
+  }
+  if (st != SEM_OK) {
+    for (int c = 0; c < kGsClasses; ++c) dfree(m->gs_cg_rec[c], s);
+    dfree(m->gs_cg_xidx, s);
+    dfree(m->cg_perm, s);
+    cudaStreamSynchronize(s);
+    return st;
+  }
+  m->gs_cg = g;
+  m->cg_map = map;
+  m->device_bytes += bytes;
+  return SEM_OK;
+}
+
 }  // namespace sem
 
 using namespace sem;
@@ -315,6 +361,7 @@ extern "C" sem_status sem_mesh_create(int N, int64_t nv, const double* vert_xyz,
     }
     SEM_STEP(dmalloc(&m->gs_xoff, H.xoff.size(), &acc, s));
     SEM_STEP(dmalloc(&m->gs_xidx, H.xidx.size(), &acc, s));
+    m->gs_xidx_count = static_cast<int64_t>(H.xidx.size());
     SEM_STEP(dmalloc(&m->gs_xmsk, H.xmsk.size(), &acc, s));
     SEM_STEP(dmalloc(&m->mult, T.mult.size(), &acc, s));
     SEM_STEP(dmalloc(&m->ctab, 256, &acc, s));
@@ -689,6 +736,7 @@ sem_status cg_alloc(sem_mesh m, sem_prec prec, sem_ax_variant v, int precond, do
     return fail(SEM_ERR_UNSUPPORTED, "double-float FP64 arithmetic runs the stored-factor variant only");
   if (v == SEM_AX_OTF_SCALE && !has_scales(m))
     return fail(SEM_ERR_ARG, "per-point scales were not requested at mesh creation (SEM_MESH_OTF_SCALE)");
+  if (cg_layout(prec)) SEM_TRY(ensure_cg_layout(m, m->home));
   sem_cg c = new sem_cg_s();
   c->m = m;
   c->prec = prec;
@@ -800,14 +848,16 @@ AxLaunch cg_ax_launch(sem_cg c) {
   return a;
 }
 
+// QQ^T and the mask on w (FP64 data: in the CG layout); every CG-mode operator formed the whole
+// <p, w>.
 sem_status cg_enqueue_gs(sem_cg c, cudaStream_t s) {
-  return launch_dssum_cg(data_prec(c->prec), c->m->gs, c->w, whole_dot(c->prec) ? nullptr : c->p, c->st, c->ax_part,
-                         c->ax_blocks, c->gs_part, s);
+  return launch_dssum_cg(data_prec(c->prec), cg_layout(c->prec) ? c->m->gs_cg : c->m->gs, c->w,
+                         whole_dot(c->prec) ? nullptr : c->p, c->st, c->ax_part, c->ax_blocks, c->gs_part, s);
 }
 
 sem_status cg_enqueue_update(sem_cg c, cudaStream_t s) {
   return launch_cg_update(data_prec(c->prec), fused_cg(c->prec), c->m->n, c->x, c->p, c->r, c->w, c->z, minv_of(c),
-                          c->m->mult, c->m->ctab, c->st, c->upd_part, s);
+                          c->m->mult, c->m->ctab, c->st, c->upd_part, c->m->cg_map, s);
 }
 
 // fused_cg: the x update of the last iteration run (a no-op if there is none)

@@ -18,12 +18,17 @@
 // which costs 21 multiply-adds instead of building six factors and applying them.
 //
 // CG mode (Algorithm 1, steps 5-6 fused, Section 5.1): the prologue forms p = z + beta p
-// and stores it, and the epilogue adds p.w into a per-block partial of <p, w, c>: FP64 over
-// element-interior points (untouched by the gather-scatter), FP32 over every point. The
-// FP32 prologue also takes the previous iteration's x update and z = M^-1 r (phase 0 below).
+// and stores it, the epilogue stores w (FP64 in the CG layout, cg_pos: boundary points first)
+// and adds p.w over every point into a per-block partial of <p, w, c> (the sum over the local
+// points of p_i (A_L p)_i is <p, QQ^T A_L p, c>, p having one value per global node and 0 on
+// Dirichlet nodes), so the gather-scatter reads no p. FP64 adds the interior points' products
+// with FP64 multiply-adds and the boundary points' in double-float arithmetic on the FP32
+// pipes, which the FP64-pipe-bound kernel leaves idle. The FP32 prologue also takes the
+// previous iteration's x update and z = M^-1 r (phase 0 below).
 #pragma once
 
 #include "k_common.cuh"
+#include "k_df.cuh"
 #include "k_tma.cuh"
 
 namespace sem {
@@ -183,9 +188,8 @@ __global__ void __launch_bounds__(NP * NP * EPB)
          T* __restrict__ p, const T* __restrict__ r, const T* __restrict__ minv, T* __restrict__ x,
          CgScalars* __restrict__ st, double* __restrict__ partials, int* __restrict__ err) {
   constexpr bool OTF = GEO != 0;
-  // CG mode: FP32 adds p.w over every point (the gather-scatter then reads no p); FP64 over
-  // the element interior only (the boundary part is added in the gather-scatter, one copy
-  // per shared node), which keeps the FP64 pipe to one FMA per interior point
+  // CG mode: FP32 adds p.w over every point as FP32 column sums; FP64 adds the interior
+  // points with FP64 multiply-adds and the boundary points in double-float arithmetic
   constexpr bool kWholeDot = sizeof(T) == 4;
   constexpr bool kFused = sizeof(T) == 4;  // the fused CG prologue of phase 0
   constexpr int NP2 = NP * NP, P = NP2 * NP, GS = ax_gstride<NP, T>(), SZ = Stage<NP>::kSize;
@@ -250,6 +254,7 @@ __global__ void __launch_bounds__(NP * NP * EPB)
   T* sA = sA0 + slot * SZ;
   T* sB = sB0 + slot * SZ;
   DotAcc<T> dot;
+  df2 bdot{0.f, 0.f};  // FP64 CG mode: boundary points' part of <p, w>
   unsigned parity = 0, parity_in = 0;
   bool in_pend = tma_in;  // an input copy is in flight (uniform over the block)
   __syncthreads();
@@ -470,14 +475,21 @@ __global__ void __launch_bounds__(NP * NP * EPB)
     for (int k = 0; k < NP; ++k) {
       const int at = Stage<NP>::at(i, j, k);
       const T acc = sB[at] + sA[at] + rW[k];
-      if (valid) w[base + k * NP2] = acc;
       if constexpr (CG) {
+        if (valid) w[kWholeDot ? base + k * NP2 : e * P + cg_pos(NP, i, j, k)] = acc;  // FP64: CG layout
         if constexpr (kWholeDot) {
           col = fma(rU[k], acc, col);
         } else {
           const bool interior = i > 0 && i < NP - 1 && j > 0 && j < NP - 1 && k > 0 && k < NP - 1;
-          if (valid && interior) dot.add(rU[k], acc);
+          if (valid && interior) {
+            dot.add(rU[k], acc);
+          } else if (valid) {
+            const df2 a = df_from_double(rU[k]), b = df_from_double(acc);
+            df_fma_acc(bdot, a.h, a.l, b.h, b.l);
+          }
         }
+      } else {
+        if (valid) w[base + k * NP2] = acc;
       }
     }
     if constexpr (CG && kWholeDot) {
@@ -486,7 +498,7 @@ __global__ void __launch_bounds__(NP * NP * EPB)
     __syncthreads();  // the staging buffers are free for the next group
   }
   if constexpr (CG) {
-    const double s = block_sum(dot.value(), sRed);
+    const double s = block_sum(dot.value() + (static_cast<double>(bdot.h) + static_cast<double>(bdot.l)), sRed);
     if (threadIdx.x == 0) partials[blockIdx.x] = s;
   }
 }

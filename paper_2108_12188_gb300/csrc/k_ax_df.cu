@@ -301,7 +301,7 @@ __global__ void __launch_bounds__(NP * NP * ax_epb<NP>(), (CG && NP == 8) ? 4 : 
     for (int k = 0; k < NP; ++k) {
       const int at = Stage<NP>::at(i, j, k);
       const df2 acc = df_norm(df_add_nr(df_add_nr(sB[at], sA[at]), rW[k]));
-      if (valid) w[base + k * NP2] = df_to_double(acc);
+      if (valid) w[CG ? e * P + cg_pos(NP, i, j, k) : base + k * NP2] = df_to_double(acc);  // CG: CG layout
       if constexpr (CG) {
         if (valid) df_fma_acc(dot, rU[k].h, rU[k].l, acc.h, acc.l);
       }

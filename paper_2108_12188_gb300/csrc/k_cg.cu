@@ -126,14 +126,15 @@ struct Vec16<float> {
 
 // Algorithm 1 steps 9-13 with z = M^-1 r. Each thread takes 16 bytes of every vector per
 // step (vector loads and stores; FUSED: two steps at a time with all their loads issued
-// first); the last n mod (16 / sizeof(T)) points are done singly.
+// first); the last n mod (16 / sizeof(T)) points are done singly. FP64 w, written by the
+// operator in the CG layout and assembled there by the gather-scatter, is read through `map`.
 // FUSED: the operator's CG prologue makes x += alpha p (one iteration later) and recomputes
 // z = M^-1 r, so this kernel leaves x alone and stores no z (z is formed for the dots only).
 template <typename T, bool FUSED>
 __global__ void k_cg_update(int64_t n, T* __restrict__ x, const T* __restrict__ p, T* __restrict__ r,
                             const T* __restrict__ w, T* __restrict__ z, const T* __restrict__ minv,
                             const uint8_t* __restrict__ mult, const double* __restrict__ ctab, CgScalars* st,
-                            double* __restrict__ partials) {
+                            double* __restrict__ partials, const CgMap map) {
   __shared__ double sRed[kThreads / 32];
   if (st->done) return;
   using VT = typename Vec16<T>::type;
@@ -149,7 +150,22 @@ __global__ void k_cg_update(int64_t n, T* __restrict__ x, const T* __restrict__ 
   };
   auto load = [&](int64_t q, Pack& k) {
     k.r = reinterpret_cast<const VT*>(r)[q];
-    k.w = reinterpret_cast<const VT*>(w)[q];
+    if constexpr (sizeof(T) == 4) {
+      k.w = reinterpret_cast<const VT*>(w)[q];
+    } else {  // w of the V points q V .. q V + V - 1, read in the CG layout
+      T* ws = reinterpret_cast<T*>(&k.w);
+      const int64_t i0 = q * V;
+      unsigned long long e = __umul64hi(static_cast<unsigned long long>(i0), map.magic);
+      int loc = static_cast<int>(i0 - static_cast<int64_t>(e) * map.P);
+#pragma unroll
+      for (int l = 0; l < V; ++l) {
+        ws[l] = w[static_cast<int64_t>(e) * map.P + __ldg(map.perm + loc)];
+        if (++loc == map.P) {
+          loc = 0;
+          ++e;
+        }
+      }
+    }
     k.m = minv ? reinterpret_cast<const VT*>(minv)[q] : VT{};
     k.c = reinterpret_cast<const MT*>(mult)[q];
     if constexpr (!FUSED) {
@@ -195,7 +211,7 @@ __global__ void k_cg_update(int64_t n, T* __restrict__ x, const T* __restrict__ 
     }
     for (int64_t i = nv * V + t0; i < n; i += stride) {
       T xi = FUSED ? T(0) : x[i], ri = r[i], zi;
-      point(xi, FUSED ? T(0) : p[i], ri, w[i], zi, minv ? minv[i] : T(0), mult[i]);
+      point(xi, FUSED ? T(0) : p[i], ri, w[sizeof(T) == 4 ? i : cg_at(map, i)], zi, minv ? minv[i] : T(0), mult[i]);
       r[i] = ri;
       if constexpr (!FUSED) {
         x[i] = xi;
@@ -300,7 +316,7 @@ sem_status launch_cg_init(sem_prec prec, int64_t n, const void* b, const void* a
 
 sem_status launch_cg_update(sem_prec prec, bool fused, int64_t n, void* x, const void* p, void* r, const void* w,
                             void* z, const void* minv, const uint8_t* mult, const double* ctab, CgScalars* st,
-                            double* partials, cudaStream_t s) {
+                            double* partials, const CgMap& map, cudaStream_t s) {
   const int grid = vec_grid(n, prec != SEM_F64 ? resident_blocks<k_cg_update<float, true>>(kThreads)
                                : fused         ? resident_blocks<k_cg_update<double, true>>(kThreads)
                                                : resident_blocks<k_cg_update<double, false>>(kThreads));
@@ -312,15 +328,15 @@ sem_status launch_cg_update(sem_prec prec, bool fused, int64_t n, void* x, const
     auto* zd = static_cast<double*>(z);
     auto* md = static_cast<const double*>(minv);
     if (fused)
-      k_cg_update<double, true><<<grid, kThreads, 0, s>>>(n, xd, pd, rd, wd, zd, md, mult, ctab, st, partials);
+      k_cg_update<double, true><<<grid, kThreads, 0, s>>>(n, xd, pd, rd, wd, zd, md, mult, ctab, st, partials, map);
     else
-      k_cg_update<double, false><<<grid, kThreads, 0, s>>>(n, xd, pd, rd, wd, zd, md, mult, ctab, st, partials);
+      k_cg_update<double, false><<<grid, kThreads, 0, s>>>(n, xd, pd, rd, wd, zd, md, mult, ctab, st, partials, map);
   } else {
     if (!fused) return fail(SEM_ERR_UNSUPPORTED, "the FP32 CG update runs with the fused operator prologue only");
     k_cg_update<float, true><<<grid, kThreads, 0, s>>>(n, static_cast<float*>(x), static_cast<const float*>(p),
                                                        static_cast<float*>(r), static_cast<const float*>(w),
                                                        static_cast<float*>(z), static_cast<const float*>(minv), mult,
-                                                       ctab, st, partials);
+                                                       ctab, st, partials, map);
   }
   count_launch();
   SEM_CUDA_TRY(cudaGetLastError());
@@ -473,6 +489,40 @@ sem_status launch_cg_replace(int64_t n, const float* rnew, float* r, float* z, c
 
 sem_status launch_ir_correct(int64_t n, double* x, const float* d, cudaStream_t s) {
   k_ir_correct<<<vec_grid(n, resident_blocks<k_ir_correct>(kThreads)), kThreads, 0, s>>>(n, x, d);
+  count_launch();
+  SEM_CUDA_TRY(cudaGetLastError());
+  return SEM_OK;
+}
+
+namespace {
+
+__global__ void k_cg_perm(int NP, int* __restrict__ perm) {
+  const int P = NP * NP * NP;
+  for (int loc = blockIdx.x * blockDim.x + threadIdx.x; loc < P; loc += gridDim.x * blockDim.x)
+    perm[loc] = cg_pos(NP, loc % NP, (loc / NP) % NP, loc / (NP * NP));
+}
+
+__global__ void k_map_indices(int64_t count, const int32_t* __restrict__ in, int32_t* __restrict__ out, const CgMap map) {
+  for (int64_t q = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; q < count;
+       q += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int32_t v = in[q];
+    out[q] = v < 0 ? v : static_cast<int32_t>(cg_at(map, v));
+  }
+}
+
+}  // namespace
+
+sem_status launch_cg_perm(int NP, int* perm, cudaStream_t s) {
+  const int P = NP * NP * NP;
+  k_cg_perm<<<(P + kThreads - 1) / kThreads, kThreads, 0, s>>>(NP, perm);
+  count_launch();
+  SEM_CUDA_TRY(cudaGetLastError());
+  return SEM_OK;
+}
+
+sem_status launch_map_indices(int64_t count, const int32_t* in, int32_t* out, const CgMap& map, cudaStream_t s) {
+  if (count <= 0) return SEM_OK;
+  k_map_indices<<<vec_grid(count, resident_blocks<k_map_indices>(kThreads)), kThreads, 0, s>>>(count, in, out, map);
   count_launch();
   SEM_CUDA_TRY(cudaGetLastError());
   return SEM_OK;

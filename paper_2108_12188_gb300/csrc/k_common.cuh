@@ -154,6 +154,30 @@ int resident_blocks(int threads) {
 
 __host__ __device__ constexpr int ceil_div(long long a, long long b) { return static_cast<int>((a + b - 1) / b); }
 
+// Position of point (i, j, k) of an element in the CG layout (see CgMap): with MB = 4 NP - 4
+// boundary points per interior k-plane and NB = NP^3 - (NP - 2)^3 boundary points per element,
+// the k = 0 plane, then for 0 < k < N its row j = 0, the ends i = 0 and i = N of rows 0 < j < N,
+// its row j = N, then the k = N plane, and after the NB boundary points the interior ones.
+__host__ __device__ __forceinline__ int cg_pos(int NP, int i, int j, int k) {
+  const int N = NP - 1, NP2 = NP * NP, MB = 4 * NP - 4;
+  if (k == 0) return j * NP + i;
+  if (k == N) return NP2 + (N - 1) * MB + j * NP + i;
+  const int base = NP2 + (k - 1) * MB;
+  if (j == 0) return base + i;
+  if (j == N) return base + NP + 2 * (NP - 2) + i;
+  if (i == 0) return base + NP + 2 * (j - 1);
+  if (i == N) return base + NP + 2 * (j - 1) + 1;
+  const int NB = 2 * NP2 + (NP - 2) * MB;
+  return NB + ((k - 1) * (NP - 2) + (j - 1)) * (NP - 2) + (i - 1);
+}
+
+// The CG-layout position of local index idx (idx < 2^31).
+__device__ __forceinline__ int64_t cg_at(const CgMap& m, int64_t idx) {
+  const unsigned long long e = __umul64hi(static_cast<unsigned long long>(idx), m.magic);
+  const int loc = static_cast<int>(idx - static_cast<int64_t>(e) * m.P);
+  return static_cast<int64_t>(e) * m.P + __ldg(m.perm + loc);
+}
+
 }  // namespace sem
 
 namespace sem {

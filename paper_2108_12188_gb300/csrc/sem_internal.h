@@ -154,6 +154,19 @@ struct GsPlan {
   int64_t total() const { return n[0] + n[1] + n[2] + n[3] + nx; }
 };
 
+// ---- CG layout of the operator's output (k_common.cuh cg_pos) ----
+// In CG mode the FP64-data local operators (FP64, double-float) write w element by element with
+// the element's boundary points (any of i, j, k in {0, N}) first and its interior points after
+// them, each part in the (k, j, i) order of the local layout. The gather-scatter then finds the
+// copies of neighbouring segments next to each other (copies on the i = 0 and i = N faces of
+// consecutive rows are adjacent instead of a row apart, in the same DRAM sector), and the vector
+// update reads w through the same map. Every other vector keeps the local layout.
+struct CgMap {
+  const int* perm = nullptr;      // [P]: position in the CG layout of local point loc
+  int P = 0;
+  unsigned long long magic = 0;   // UINT64_MAX / P + 1: idx / P = umulhi64(idx, magic) for idx < 2^31
+};
+
 // ---- batched CG over a table of solves (k_batch.cu, batch.cpp) ----
 // Several independent FP32 CG solves (the inner iteration of mixed-precision refinement,
 // on-the-fly factors, fused prologue) advance together: each batched kernel strides over the
@@ -218,8 +231,15 @@ struct sem_mesh_s {
   uint8_t* gs_msk[sem::kGsClasses] = {};
   int32_t* gs_xoff = nullptr;
   int32_t* gs_xidx = nullptr;
+  int64_t gs_xidx_count = 0;
   uint8_t* gs_xmsk = nullptr;
   sem::GsPlan gs;
+  // the gather-scatter plan with copy indices in the CG layout (built with the first CG handle)
+  int32_t* gs_cg_rec[sem::kGsClasses] = {};
+  int32_t* gs_cg_xidx = nullptr;
+  int* cg_perm = nullptr;     // [P]
+  sem::GsPlan gs_cg;
+  sem::CgMap cg_map;
   uint8_t* mult = nullptr;    // [n]
   double* minv64 = nullptr;   // lazily built Jacobi inverse
   float* minv32 = nullptr;
@@ -315,7 +335,11 @@ sem_status launch_dssum(sem_prec prec, const GsPlan& g, void* u, int apply_mask,
 // CG variant: with p, also the boundary part of <p, w, c> (the operator added the interior
 // part); with p == nullptr the operator's partials hold the whole product (whole_dot). The
 // last block combines the partials and sets alpha (or a breakdown status).
-inline bool whole_dot(sem_prec prec) { return prec != SEM_F64; }  // FP32 and double-float operators
+inline bool whole_dot(sem_prec) { return true; }  // every CG-mode operator forms the whole <p, w>
+// The CG layout (CgMap) is used for FP64 data (FP64 and double-float operators): their w does not
+// fit in L2 and the gather-scatter is bound by DRAM sectors. FP32 CG keeps the local layout (its
+// w stays in L2, and reading w through the map costs the FP32 update more than it saves).
+inline bool cg_layout(sem_prec prec) { return prec != SEM_F32; }
 // The same operators take the fused CG prologue (AxLaunch::r, minv, x): the update kernel
 // then skips x and z, and after the last iteration launch_cg_flush adds the pending alpha p.
 inline bool fused_cg(sem_prec prec) { return prec != SEM_F64; }
@@ -340,10 +364,15 @@ sem_status launch_glsc3(sem_prec prec, int64_t n, const void* a, const void* b, 
 sem_status launch_cg_init(sem_prec prec, int64_t n, const void* b, const void* ax0, void* r, void* z, void* p,
                           const void* minv, const uint8_t* mult, const double* ctab, CgScalars* st, double* partials,
                           cudaStream_t s);
-// fused (fused_cg): x and z are left to the operator's CG prologue (see AxLaunch::r)
+// fused (fused_cg): x and z are left to the operator's CG prologue (see AxLaunch::r). w is read
+// in the CG layout through `map`.
 sem_status launch_cg_update(sem_prec prec, bool fused, int64_t n, void* x, const void* p, void* r, const void* w,
                             void* z, const void* minv, const uint8_t* mult, const double* ctab, CgScalars* st,
-                            double* partials, cudaStream_t s);
+                            double* partials, const CgMap& map, cudaStream_t s);
+// perm[loc] = cg_pos of local point loc for N + 1 = NP points per direction (P entries).
+sem_status launch_cg_perm(int NP, int* perm, cudaStream_t s);
+// out[q] = the CG-layout position of local index in[q] (negative entries, record padding, copied).
+sem_status launch_map_indices(int64_t count, const int32_t* in, int32_t* out, const CgMap& map, cudaStream_t s);
 // x += alpha p if an update is pending (alpha != 0), then alpha = 0 (fused CG, at the end of
 // a run of iterations)
 sem_status launch_cg_flush(sem_prec prec, int64_t n, void* x, const void* p, CgScalars* st, cudaStream_t s);
