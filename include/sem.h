@@ -154,6 +154,12 @@ sem_status sem_mesh_get_segments(sem_mesh mesh, int32_t* seg_off_host, int32_t* 
  * a copy of the local operator does not arrive; the context stays usable. Synchronises
  * `stream`; *elapsed_ms_host receives the kernel's duration. */
 sem_status sem_probe_bounded_wait(int64_t limit_ns, int issue_copy, double* elapsed_ms_host, void* stream);
+/* Self-test of the bounded grid barrier of the persistent small-mesh CG kernel: a cooperative
+ * launch of a few blocks meets at one barrier. skip_one = 0: all arrive, SEM_OK. skip_one = 1: one
+ * block never arrives, the others give up after the barrier's limit (1 s) and the call returns
+ * SEM_ERR_TIMEOUT, the status a solve reports when a barrier runs out; no fault, the context
+ * stays usable. Synchronises `stream`; *elapsed_ms_host receives the kernel's duration. */
+sem_status sem_probe_grid_barrier(int skip_one, double* elapsed_ms_host, void* stream);
 
 /* Physical coordinates of the local points (trilinear map, Section 5.1):
  * xyz_dev [3][n_local] FP64 (all x, then all y, then all z). Async. */

@@ -688,6 +688,7 @@ struct sem_cg_s {
   double *ax_part = nullptr, *gs_part = nullptr, *upd_part = nullptr, *init_part = nullptr;
   int ax_blocks = 0;
   cudaStream_t cap = nullptr;     // private stream: allocation, graph capture, release
+  unsigned* bar = nullptr;        // grid barrier words of the persistent small-mesh kernel
   std::vector<cudaStream_t> used; // streams the solver's work was enqueued on
   cudaGraphExec_t exec = nullptr;
   int exec_k = 0;
@@ -720,6 +721,7 @@ void cg_free(sem_cg c) {
   dfree(c->upd_part, h);
   dfree(c->init_part, h);
   dfree(c->st, h);
+  dfree(c->bar, h);
   if (h) {
     cudaStreamSynchronize(h);
     cudaStreamDestroy(h);
@@ -766,6 +768,7 @@ sem_status cg_alloc(sem_mesh m, sem_prec prec, sem_ax_variant v, int precond, do
   if (st == SEM_OK) st = dmalloc(&c->upd_part, 2 * kRedMax, nullptr, c->cap);
   if (st == SEM_OK) st = dmalloc(&c->init_part, 3 * kRedMax, nullptr, c->cap);
   if (st == SEM_OK) st = dmalloc(&c->st, 1, nullptr, c->cap);
+  if (st == SEM_OK) st = dmalloc(&c->bar, 2, nullptr, c->cap);
   if (st == SEM_OK && (e = cudaStreamSynchronize(c->cap)) != cudaSuccess) st = cuda_fail(e, "cudaStreamSynchronize");
   if (st != SEM_OK) {
     cg_free(c);
@@ -874,10 +877,57 @@ sem_status cg_enqueue_iteration(sem_cg c, cudaStream_t s) {
   return cg_enqueue_update(c, s);
 }
 
+int host_sm_count() {
+  static const int n = [] {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 1;
+  }();
+  return n;
+}
+
+// FP64 CG with stored factors on a mesh with fewer elements than the device has SMs runs in the
+// persistent kernel (k_cg_small.cu): its per-iteration cost is the operator on one element per
+// SM, which three launches per iteration would otherwise dwarf.
+bool small_path(sem_cg c) {
+  if (c->prec != SEM_F64 || !c->m->G64 || c->m->E >= host_sm_count()) return false;
+  sem_ax_variant v;
+  int shape;
+  resolve_variant(c->m, SEM_F64, c->variant, &v, &shape);
+  return v == SEM_AX_STORED;
+}
+
+sem_status cg_iterate_small(sem_cg c, int k, cudaStream_t s) {
+  sem_mesh m = c->m;
+  SEM_CUDA_TRY(cudaMemsetAsync(c->bar, 0, 2 * sizeof(unsigned), s));
+  SmallCgLaunch a;
+  a.E = m->E;
+  a.n = m->n;
+  a.G = m->G64;
+  a.x = static_cast<double*>(c->x);
+  a.p = static_cast<double*>(c->p);
+  a.r = static_cast<double*>(c->r);
+  a.z = static_cast<double*>(c->z);
+  a.w = static_cast<double*>(c->w);
+  a.minv = static_cast<const double*>(minv_of(c));
+  a.mult = m->mult;
+  a.ctab = m->ctab;
+  a.gs = m->gs;
+  a.st = c->st;
+  a.part = c->init_part;
+  a.bar = c->bar;
+  a.err = m->dev_err;
+  a.iters = k;
+  a.max_blocks = host_sm_count();
+  return launch_cg_small(m->N, a, s);
+}
+
 sem_status cg_iterate(sem_cg c, int k, cudaStream_t s) {
   if (k <= 0) return SEM_OK;
   cg_note(c, s);
   note_stream(c->m, s);
+  if (small_path(c)) return cg_iterate_small(c, k, s);
   if (!c->use_graph) {
     for (int q = 0; q < k; ++q) SEM_TRY(cg_enqueue_iteration(c, s));
     return cg_enqueue_flush(c, s);

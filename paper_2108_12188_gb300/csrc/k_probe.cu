@@ -77,3 +77,54 @@ extern "C" sem_status sem_probe_bounded_wait(int64_t limit_ns, int issue_copy, d
     return fail(SEM_ERR_CUDA, "the probe kernel did not report");
   });
 }
+
+// Self-test of the grid barrier of the persistent CG kernel (k_cg_small.cu): a cooperative launch
+// of a few blocks meets at one bounded barrier. skip_one = 0: every block arrives, SEM_OK.
+// skip_one = 1: the last block never arrives, the others give up after the barrier's limit (1 s)
+// and report SEM_ERR_TIMEOUT; nothing faults and the context stays usable.
+extern "C" sem_status sem_probe_grid_barrier(int skip_one, double* elapsed_ms, void* stream) {
+  using namespace sem;
+  return guarded([&]() -> sem_status {
+    if (!elapsed_ms) return fail(SEM_ERR_ARG, "elapsed_ms is null");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int dev = 0, sms = 0;
+    SEM_CUDA_TRY(cudaGetDevice(&dev));
+    SEM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int blocks = sms < 8 ? sms : 8;
+    if (blocks < 2) return fail(SEM_ERR_UNSUPPORTED, "needs two SMs");
+    unsigned* bar = nullptr;
+    int* status = nullptr;
+    SEM_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&bar), 2 * sizeof(unsigned), s));
+    sem_status st = SEM_OK;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int h = -2;
+    auto step = [&](cudaError_t e, const char* what) {
+      if (st == SEM_OK && e != cudaSuccess) st = cuda_fail(e, what);
+    };
+    step(cudaMallocAsync(reinterpret_cast<void**>(&status), sizeof(int), s), "cudaMallocAsync");
+    step(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s), "cudaMemsetAsync");
+    step(cudaMemsetAsync(status, 0xff, sizeof(int), s), "cudaMemsetAsync");
+    step(cudaEventCreate(&e0), "cudaEventCreate");
+    step(cudaEventCreate(&e1), "cudaEventCreate");
+    if (st == SEM_OK) {
+      cudaEventRecord(e0, s);
+      st = launch_probe_barrier(bar, blocks, skip_one ? blocks - 1 : -1, status, s);
+      cudaEventRecord(e1, s);
+      step(cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync");
+      step(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    }
+    if (st == SEM_OK) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      *elapsed_ms = ms;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (status) cudaFreeAsync(status, s);
+    cudaFreeAsync(bar, s);
+    if (st != SEM_OK) return st;
+    if (h == SEM_OK) return SEM_OK;
+    if (h == SEM_ERR_TIMEOUT) return fail(SEM_ERR_TIMEOUT, "grid barrier gave up (a block never arrived)");
+    return fail(SEM_ERR_CUDA, "the barrier probe did not report");
+  });
+}

@@ -316,6 +316,30 @@ sem_status ensure_jacobi(sem_mesh_s* m, cudaStream_t s);
 // element type of a precision's data: FP64 for SEM_F64 and SEM_F64X
 inline sem_prec data_prec(sem_prec p) { return p == SEM_F32 ? SEM_F32 : SEM_F64; }
 
+// Persistent FP64 CG for small meshes (k_cg_small.cu): `iters` iterations (fewer if the solve
+// ends) in one cooperative launch of at most max_blocks blocks (one per SM), stored FP64 factors,
+// w in the local layout with the plan gs. part: 3 x kRedMax doubles; bar: two words, zero at launch.
+struct SmallCgLaunch {
+  int64_t E = 0, n = 0;
+  const double* G = nullptr;
+  double *x = nullptr, *p = nullptr, *r = nullptr, *z = nullptr, *w = nullptr;
+  const double* minv = nullptr;
+  const uint8_t* mult = nullptr;
+  const double* ctab = nullptr;
+  GsPlan gs;
+  CgScalars* st = nullptr;
+  double* part = nullptr;
+  unsigned* bar = nullptr;
+  int* err = nullptr;
+  int iters = 0;
+  int max_blocks = 0;
+};
+sem_status launch_cg_small(int N, const SmallCgLaunch& a, cudaStream_t s);
+// Self-test of the grid barrier: `blocks` blocks (all resident) meet at one barrier; block
+// skip_block (-1: none) never arrives, so the others' bounded waits run out. status: -1 on entry,
+// then SEM_OK or SEM_ERR_TIMEOUT.
+sem_status launch_probe_barrier(unsigned* bar, int blocks, int skip_block, int* status, cudaStream_t s);
+
 // element geometry (k_mesh.cu)
 sem_status launch_coefficients(int64_t E, const double* X, double* coef64, float* coef32, cudaStream_t s);
 // G64 / G32 (either may be null) are written with element strides gs64 / gs32.

@@ -31,7 +31,7 @@ EXPORTS = [
     "sem_status_string", "sem_server_create", "sem_server_submit", "sem_server_poll", "sem_server_stats",
     "sem_server_destroy", "sem_autotune", "sem_autotune_save", "sem_autotune_load", "sem_mesh_info",
     "sem_server_submit_mesh", "sem_probe_bounded_wait", "sem_cg_solve_batch", "sem_server_default_config",
-    "sem_server_create_config", "sem_server_batch_stats", "sem_autotune_set", "sem_autotune_clear",
+    "sem_server_create_config", "sem_server_batch_stats", "sem_autotune_set", "sem_autotune_clear", "sem_probe_grid_barrier",
 ]
 
 
@@ -116,6 +116,7 @@ def load_library(path: str | None = None):
         "sem_mesh_get_info": [_VP, C.POINTER(MeshInfo)],
         "sem_mesh_info": [_VP, C.POINTER(_I64), C.POINTER(_I64), C.POINTER(_I64)],
         "sem_probe_bounded_wait": [_I64, C.c_int, C.POINTER(C.c_double), _VP],
+        "sem_probe_grid_barrier": [C.c_int, C.POINTER(C.c_double), _VP],
         "sem_mesh_get_glo_num": [_VP, _VP],
         "sem_mesh_get_mask": [_VP, _VP],
         "sem_mesh_get_segments": [_VP, _VP, _VP, _VP],
@@ -257,6 +258,14 @@ def sem_probe_bounded_wait(limit_ns, issue_copy, stream=None):
     """(status, kernel ms) of the bounded-wait self-test; SEM_ERR_TIMEOUT is a result here."""
     ms = C.c_double()
     st = _check(load_library().sem_probe_bounded_wait(int(limit_ns), int(issue_copy), C.byref(ms), _stream(stream)),
+                ok=(SEM_OK, SEM_ERR_TIMEOUT))
+    return st, float(ms.value)
+
+
+def sem_probe_grid_barrier(skip_one, stream=None):
+    """(status, kernel ms) of the grid-barrier self-test; SEM_ERR_TIMEOUT is a result here."""
+    ms = C.c_double()
+    st = _check(load_library().sem_probe_grid_barrier(int(skip_one), C.byref(ms), _stream(stream)),
                 ok=(SEM_OK, SEM_ERR_TIMEOUT))
     return st, float(ms.value)
 

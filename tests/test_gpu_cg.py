@@ -99,6 +99,23 @@ def test_cg_mixed_reliable_updates(sem, c1, inner_variant, graph):
     assert abs(e_gpu - e_ref) <= 5e-4 * e_ref + 1e-11, (e_gpu, e_ref)
 
 
+def test_cg_small_mesh_runs_persistent(sem, c1):
+    """Config 1 (64 elements, fewer than the SMs) with stored FP64 factors runs the persistent
+    kernel: a whole run of check_every iterations is one launch; the oracle gates hold (the
+    parametrized test above) and the launch count shows the path taken."""
+    import torch
+    m, prob, b, ref, mesh = c1
+    bd = torch.empty(prob.n, dtype=torch.float64, device="cuda")
+    sem.sem_rhs_sine(mesh.handle, 1, 1, 1, sem.SEM_F64, bd)
+    x = torch.zeros_like(bd)
+    c0 = sem.sem_launch_count()
+    res = sem.sem_cg_solve(mesh.handle, bd, x, sem.sem_cg_default_opts(rtol=1e-10, check_every=50))
+    launches = sem.sem_launch_count() - c0
+    assert res["status"] == sem.SEM_OK
+    assert launches <= 20, launches  # set-up kernels + one persistent launch per 50 iterations
+    assert _true_rel(prob, b, x.cpu().numpy()) <= 1e-10 * (1 + 1e-3)
+
+
 def test_cg_stateful_and_limits(sem, c1):
     import torch
     m, prob, b, ref, mesh = c1

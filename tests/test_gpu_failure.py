@@ -1,7 +1,8 @@
 """Failure detection on the GPU without a fault: the bounded waits that guard every TMA copy
 give up after their time limit and report SEM_ERR_TIMEOUT (the copy is never issued, so
 nothing arrives), the CUDA context stays usable, and the same wait completes when the copy
-is issued."""
+is issued; likewise the bounded grid barrier of the persistent small-mesh CG kernel (a block
+that never arrives)."""
 import numpy as np
 import pytest
 
@@ -59,13 +60,43 @@ def test_launch_count_matches_the_kernels_run(sem):
     assert (c1 - c0, c2 - c1) == (1, 2)
     b = torch.empty_like(u)
     sem.sem_rhs_sine(mesh.handle, 1, 1, 1, sem.SEM_F64, b)
-    for graph in (0, 1):
+    # three launches per iteration (on-the-fly FP64 operator); with stored factors on a mesh of
+    # fewer elements than SMs the persistent kernel runs the 5 iterations in one launch
+    for variant, graph, want in ((sem.SEM_AX_OTF, 0, 15), (sem.SEM_AX_OTF, 1, 15), (sem.SEM_AX_STORED, 1, 1)):
         x = torch.zeros_like(b)
-        cg = sem.sem_cg_create(mesh.handle, sem.sem_cg_default_opts(rtol=0.0, max_iter=1 << 20, use_graph=graph))
+        cg = sem.sem_cg_create(mesh.handle, sem.sem_cg_default_opts(rtol=0.0, max_iter=1 << 20, use_graph=graph,
+                                                                    variant=variant))
         sem.sem_cg_start(cg, b, x)
         c3 = sem.sem_launch_count()
         sem.sem_cg_iterate(cg, 5)
-        sem.sem_cg_query(cg)
-        assert sem.sem_launch_count() - c3 == 15, graph
+        q = sem.sem_cg_query(cg)
+        assert q["iters"] == 5 and sem.sem_launch_count() - c3 == want, (variant, graph)
         sem.sem_cg_destroy(cg)
+    mesh.close()
+
+
+def test_grid_barrier_completes_when_every_block_arrives(sem):
+    st, ms = sem.sem_probe_grid_barrier(0)
+    assert st == sem.SEM_OK and ms < 100.0, (st, ms)
+
+
+def test_grid_barrier_times_out_and_the_context_survives(sem):
+    """The persistent small-mesh CG kernel meets at bounded grid barriers: a block that never
+    arrives makes the others give up after the limit (1 s) with SEM_ERR_TIMEOUT; then a
+    persistent solve runs normally on the same context."""
+    import torch
+    from oracle import sem_oracle as so
+    st, ms = sem.sem_probe_grid_barrier(1)
+    assert st == sem.SEM_ERR_TIMEOUT
+    assert 990.0 <= ms <= 3000.0, ms
+    m = BoxMesh(2, 2, 2, jitter=0.1, seed=3)
+    prob = so.SemProblem(5, m.vert_xyz, m.elem_verts)
+    b = prob.rhs()
+    mesh = sem.Mesh(5, m.vert_xyz, m.elem_verts)
+    bd = torch.tensor(b.ravel(), device="cuda")
+    x = torch.zeros_like(bd)
+    res = sem.sem_cg_solve(mesh.handle, bd, x, sem.sem_cg_default_opts(rtol=1e-10))
+    assert res["status"] == sem.SEM_OK
+    r = b - prob.ax(x.cpu().numpy().reshape(prob.shape()))
+    assert np.sqrt(so.glsc3(r, r, prob.c) / so.glsc3(b, b, prob.c)) <= 1e-10 * (1 + 1e-3)
     mesh.close()
