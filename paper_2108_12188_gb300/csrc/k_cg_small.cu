@@ -114,7 +114,7 @@ struct SmallCg {
 };
 
 template <int NP>
-__global__ void __launch_bounds__(SmallCg<NP>::kThreads)
+__global__ void __launch_bounds__(SmallCg<NP>::kThreads, 1)
     k_cg_small(const __grid_constant__ GllParam<NP, double> tab, int64_t E, int64_t n, const double* __restrict__ G,
                double* __restrict__ x, double* __restrict__ p, double* __restrict__ r, double* __restrict__ z,
                double* __restrict__ w, const double* __restrict__ minv, const uint8_t* __restrict__ mult,
@@ -142,7 +142,8 @@ __global__ void __launch_bounds__(SmallCg<NP>::kThreads)
   const int la = t % NP, lb = t / NP;                  // line coordinates
   const bool line_thread = tid < 2 * NP2;
   const int64_t gtid = static_cast<int64_t>(blockIdx.x) * T + tid, gstride = static_cast<int64_t>(G_) * T;
-  int status = 0;
+  constexpr int kRunning = -1;  // no decision yet (SEM_OK is 0)
+  int status = kRunning;
   double alpha = 0.0, pw = 0.0, rz = 0.0, rr = 0.0;
   for (int it = 0; it < max_iters; ++it) {
     // ---- phase A: p = z + beta p, w = A_L p, <p, w>
@@ -192,22 +193,30 @@ __global__ void __launch_bounds__(SmallCg<NP>::kThreads)
         }
       }
       __syncthreads();
-      // transposed contractions in place (the two threads of a line read it whole before either
-      // writes; lines of one direction are disjoint)
-      if (line_thread) {
+      // transposed contractions in place: the two threads of a line (lanes 2t, 2t + 1 of one
+      // warp) read it whole before either writes, and lines of one direction are disjoint. Every
+      // thread of the block reaches each warp synchronisation (also threads without a line,
+      // which a warp may hold when 2 (N+1)^2 is not a multiple of 32).
+      {
         double in[NP];
+        if (line_thread) {
 #pragma unroll
-        for (int l = 0; l < NP; ++l) in[l] = sR[Stage<NP>::at(l, la, lb)];
+          for (int l = 0; l < NP; ++l) in[l] = sR[Stage<NP>::at(l, la, lb)];
+        }
         __syncwarp();
-        eo_half<NP>(tab.Dt, in, h, [&](int l, double v) { sR[Stage<NP>::at(l, la, lb)] = v; });
+        if (line_thread) {
+          eo_half<NP>(tab.Dt, in, h, [&](int l, double v) { sR[Stage<NP>::at(l, la, lb)] = v; });
 #pragma unroll
-        for (int l = 0; l < NP; ++l) in[l] = sS[Stage<NP>::at(la, l, lb)];
+          for (int l = 0; l < NP; ++l) in[l] = sS[Stage<NP>::at(la, l, lb)];
+        }
         __syncwarp();
-        eo_half<NP>(tab.Dt, in, h, [&](int l, double v) { sS[Stage<NP>::at(la, l, lb)] = v; });
+        if (line_thread) {
+          eo_half<NP>(tab.Dt, in, h, [&](int l, double v) { sS[Stage<NP>::at(la, l, lb)] = v; });
 #pragma unroll
-        for (int l = 0; l < NP; ++l) in[l] = sT[Stage<NP>::at(la, lb, l)];
+          for (int l = 0; l < NP; ++l) in[l] = sT[Stage<NP>::at(la, lb, l)];
+        }
         __syncwarp();
-        eo_half<NP>(tab.Dt, in, h, [&](int l, double v) { sT[Stage<NP>::at(la, lb, l)] = v; });
+        if (line_thread) eo_half<NP>(tab.Dt, in, h, [&](int l, double v) { sT[Stage<NP>::at(la, lb, l)] = v; });
       }
       __syncthreads();
       if (line_thread) {
@@ -318,7 +327,7 @@ __global__ void __launch_bounds__(SmallCg<NP>::kThreads)
     st->pw = pw;
     st->rz = rz;
     st->rr = rr;
-    if (status != 0) {
+    if (status != kRunning) {
       st->status = status;
       st->done = 1;
     }
