@@ -578,6 +578,8 @@ def run_gpu(args):
     x1 = torch.zeros_like(b1)
     cg_c1 = {}
     for name, o in (("fp64", sem.sem_cg_default_opts(rtol=1e-10)),
+                    ("fp64_persistent", sem.sem_cg_default_opts(rtol=1e-10, use_graph=2)),
+                    ("f64x", sem.sem_cg_default_opts(rtol=1e-10, f64_arith=1)),
                     ("mixed_otf", sem.sem_cg_default_opts(rtol=1e-10, mixed=1, inner_rtol=1e-5)),
                     ("mixed_reliable", sem.sem_cg_default_opts(rtol=1e-10, mixed=2, inner_rtol=0.1))):
         times = []

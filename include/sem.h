@@ -270,7 +270,10 @@ typedef struct {
                        * residual replacements (mixed = 2) */
   int max_outer;      /* refinement steps (mixed = 1) or residual replacements (mixed = 2) limit */
   int check_every;    /* iterations between host reads of the device convergence flag (>= 1) */
-  int use_graph;      /* 1: replay check_every iterations as one captured CUDA graph */
+  int use_graph;      /* 1: replay check_every iterations as one captured CUDA graph; 2: as 1, except that FP64
+                       * CG with stored factors on a mesh with fewer elements than the GPU has SMs runs
+                       * check_every iterations in one persistent cooperative kernel (bounded grid
+                       * barriers, SEM_ERR_TIMEOUT if one runs out); 0: launch every kernel */
   int f64_arith;      /* FP64 operator arithmetic: 0 native FP64, 1 double-float (SEM_F64X; stored variant) */
 } sem_cg_opts;
 

@@ -887,11 +887,10 @@ int host_sm_count() {
   return n;
 }
 
-// FP64 CG with stored factors on a mesh with fewer elements than the device has SMs runs in the
-// persistent kernel (k_cg_small.cu): its per-iteration cost is the operator on one element per
-// SM, which three launches per iteration would otherwise dwarf.
+// use_graph = 2: FP64 CG with stored factors on a mesh with fewer elements than the device has
+// SMs runs in the persistent kernel (k_cg_small.cu), a run of iterations per launch.
 bool small_path(sem_cg c) {
-  if (c->prec != SEM_F64 || !c->m->G64 || c->m->E >= host_sm_count()) return false;
+  if (c->use_graph != 2 || c->prec != SEM_F64 || !c->m->G64 || c->m->E >= host_sm_count()) return false;
   sem_ax_variant v;
   int shape;
   resolve_variant(c->m, SEM_F64, c->variant, &v, &shape);
@@ -983,7 +982,7 @@ sem_status check_opts(const sem_cg_opts* o) {
   if (!(o->rtol >= 0) || o->max_iter < 0 || o->check_every < 1 || (o->precond != 0 && o->precond != 1) ||
       (o->variant < SEM_AX_STORED || o->variant > SEM_AX_OTF_SCALE) ||
       (o->inner_variant < SEM_AX_STORED || o->inner_variant > SEM_AX_OTF_SCALE) ||
-      (o->f64_arith != 0 && o->f64_arith != 1))
+      (o->f64_arith != 0 && o->f64_arith != 1) || o->use_graph < 0 || o->use_graph > 2)
     return fail(SEM_ERR_ARG, "invalid CG options");
   if (o->mixed < 0 || o->mixed > 2) return fail(SEM_ERR_ARG, "mixed must be 0, 1 or 2");
   if (o->mixed && (!(o->inner_rtol > 0 && o->inner_rtol < 1) || o->max_outer < 1))

@@ -52,8 +52,9 @@ def _solve(sem, mesh, prob, opts):
 
 
 @pytest.mark.parametrize("variant,use_graph,check_every,f64_arith", [(0, 1, 50, 0), (1, 1, 17, 0), (0, 0, 1, 0),
-                                                                     (0, 1, 50, 1)],
-                         ids=["stored-graph", "otf-graph", "stored-eager", "stored-doublefloat"])
+                                                                     (0, 1, 50, 1), (0, 2, 50, 0), (0, 2, 7, 0)],
+                         ids=["stored-graph", "otf-graph", "stored-eager", "stored-doublefloat", "stored-persistent",
+                              "stored-persistent-short-runs"])
 def test_cg_fp64_matches_oracle(sem, c1, variant, use_graph, check_every, f64_arith):
     m, prob, b, ref, mesh = c1
     opts = sem.sem_cg_default_opts(rtol=1e-10, variant=variant, use_graph=use_graph, check_every=check_every,
@@ -100,16 +101,16 @@ def test_cg_mixed_reliable_updates(sem, c1, inner_variant, graph):
 
 
 def test_cg_small_mesh_runs_persistent(sem, c1):
-    """Config 1 (64 elements, fewer than the SMs) with stored FP64 factors runs the persistent
-    kernel: a whole run of check_every iterations is one launch; the oracle gates hold (the
-    parametrized test above) and the launch count shows the path taken."""
+    """Config 1 (64 elements, fewer than the SMs) with stored FP64 factors and use_graph = 2 runs
+    the persistent kernel: a whole run of check_every iterations is one launch; the oracle gates
+    hold (the parametrized test above) and the launch count shows the path taken."""
     import torch
     m, prob, b, ref, mesh = c1
     bd = torch.empty(prob.n, dtype=torch.float64, device="cuda")
     sem.sem_rhs_sine(mesh.handle, 1, 1, 1, sem.SEM_F64, bd)
     x = torch.zeros_like(bd)
     c0 = sem.sem_launch_count()
-    res = sem.sem_cg_solve(mesh.handle, bd, x, sem.sem_cg_default_opts(rtol=1e-10, check_every=50))
+    res = sem.sem_cg_solve(mesh.handle, bd, x, sem.sem_cg_default_opts(rtol=1e-10, check_every=50, use_graph=2))
     launches = sem.sem_launch_count() - c0
     assert res["status"] == sem.SEM_OK
     assert launches <= 20, launches  # set-up kernels + one persistent launch per 50 iterations

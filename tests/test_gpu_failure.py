@@ -60,9 +60,11 @@ def test_launch_count_matches_the_kernels_run(sem):
     assert (c1 - c0, c2 - c1) == (1, 2)
     b = torch.empty_like(u)
     sem.sem_rhs_sine(mesh.handle, 1, 1, 1, sem.SEM_F64, b)
-    # three launches per iteration (on-the-fly FP64 operator); with stored factors on a mesh of
-    # fewer elements than SMs the persistent kernel runs the 5 iterations in one launch
-    for variant, graph, want in ((sem.SEM_AX_OTF, 0, 15), (sem.SEM_AX_OTF, 1, 15), (sem.SEM_AX_STORED, 1, 1)):
+    # three launches per iteration, replayed from a graph or not; with use_graph = 2, stored
+    # factors and a mesh of fewer elements than SMs the persistent kernel runs the 5 iterations
+    # in one launch
+    for variant, graph, want in ((sem.SEM_AX_OTF, 0, 15), (sem.SEM_AX_STORED, 1, 15), (sem.SEM_AX_STORED, 2, 1),
+                                 (sem.SEM_AX_OTF, 2, 15)):
         x = torch.zeros_like(b)
         cg = sem.sem_cg_create(mesh.handle, sem.sem_cg_default_opts(rtol=0.0, max_iter=1 << 20, use_graph=graph,
                                                                     variant=variant))
@@ -95,7 +97,7 @@ def test_grid_barrier_times_out_and_the_context_survives(sem):
     mesh = sem.Mesh(5, m.vert_xyz, m.elem_verts)
     bd = torch.tensor(b.ravel(), device="cuda")
     x = torch.zeros_like(bd)
-    res = sem.sem_cg_solve(mesh.handle, bd, x, sem.sem_cg_default_opts(rtol=1e-10))
+    res = sem.sem_cg_solve(mesh.handle, bd, x, sem.sem_cg_default_opts(rtol=1e-10, use_graph=2))
     assert res["status"] == sem.SEM_OK
     r = b - prob.ax(x.cpu().numpy().reshape(prob.shape()))
     assert np.sqrt(so.glsc3(r, r, prob.c) / so.glsc3(b, b, prob.c)) <= 1e-10 * (1 + 1e-3)
