@@ -82,7 +82,7 @@ def measured_peaks():
         return HBM_FALLBACK_GBS, "fallback"
 
 
-KERNEL_SOURCES = ("k_ax.cuh", "k_common.cuh", "k_tma.cuh")  # every source the local operator is built from
+KERNEL_SOURCES = ("k_ax.cuh", "k_common.cuh", "k_tma.cuh", "k_df.cuh")  # every source the local operator is built from
 
 
 def kernel_digest() -> str:
