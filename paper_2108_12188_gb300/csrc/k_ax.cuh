@@ -27,6 +27,8 @@
 // previous iteration's x update and z = M^-1 r (phase 0 below).
 #pragma once
 
+#include <type_traits>
+
 #include "k_common.cuh"
 #include "k_df.cuh"
 #include "k_tma.cuh"
@@ -119,6 +121,86 @@ struct OtfColumn {
     ut = dot3(c2, q);
   }
 };
+
+// FP32: the column polynomials of OtfColumn with every coefficient held twice, (c, c) as one
+// float2, so that two points of the column (gam, gam') are evaluated together by the
+// two-wide FP32 multiply-adds of sm_100 and later. Each lane performs the operations of
+// OtfColumn::det and OtfColumn::apply in the same order.
+struct OtfColumnF2 {
+  float2 c0a[3], c0b[3], c1a[3], c1b[3], c2a[3], c2b[3], c2c[3];
+  float2 da, db, dc;
+
+  __device__ __forceinline__ static float2 dup(float v) { return make_float2(v, v); }
+  __device__ __forceinline__ static void dup3(float2 (&d)[3], const Vec3<float>& v) {
+    d[0] = dup(v.x);
+    d[1] = dup(v.y);
+    d[2] = dup(v.z);
+  }
+  __device__ __forceinline__ void init(const OtfColumn<float>& g) {
+    dup3(c0a, g.c0a);
+    dup3(c0b, g.c0b);
+    dup3(c1a, g.c1a);
+    dup3(c1b, g.c1b);
+    dup3(c2a, g.c2a);
+    dup3(c2b, g.c2b);
+    dup3(c2c, g.c2c);
+    da = dup(g.da);
+    db = dup(g.db);
+    dc = dup(g.dc);
+  }
+  __device__ __forceinline__ float2 det(float2 gam) const {
+    return __ffma2_rn(gam, __ffma2_rn(gam, dc, db), da);
+  }
+  __device__ __forceinline__ void apply(float2 gam, float2 sc, float2& ur, float2& us, float2& ut) const {
+    float2 c0[3], c1[3], c2[3], q[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      c0[d] = __ffma2_rn(gam, c0b[d], c0a[d]);
+      c1[d] = __ffma2_rn(gam, c1b[d], c1a[d]);
+      c2[d] = __ffma2_rn(gam, __ffma2_rn(gam, c2c[d], c2b[d]), c2a[d]);
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+      q[d] = __fmul2_rn(sc, __ffma2_rn(c2[d], ut, __ffma2_rn(c1[d], us, __fmul2_rn(c0[d], ur))));
+    ur = __ffma2_rn(c0[2], q[2], __ffma2_rn(c0[1], q[1], __fmul2_rn(c0[0], q[0])));
+    us = __ffma2_rn(c1[2], q[2], __ffma2_rn(c1[1], q[1], __fmul2_rn(c1[0], q[0])));
+    ut = __ffma2_rn(c2[2], q[2], __ffma2_rn(c2[1], q[1], __fmul2_rn(c2[0], q[0])));
+  }
+};
+
+// Phase 3 of the FP32 on-the-fly operator for the points k < 2 (NP / 2) of a column, two at a
+// time: (rR, rS, rT) <- (w_i w_j w_k / det J) C (C^T (rR, rS, rT)) (GEO 1), or with the stored
+// word per point instead of w_i w_j w_k / det J (GEO 2, scale[base + k NP^2]).
+template <int NP, int GEO>
+__device__ __forceinline__ void otf_pairs(const GllParam<NP, float>& tab, const OtfColumn<float>& geo, float wij,
+                                          bool valid, const float* __restrict__ scale, int64_t base,
+                                          float (&rR)[NP], float (&rS)[NP], float (&rT)[NP]) {
+  constexpr int NP2 = NP * NP;
+  OtfColumnF2 geo2;
+  geo2.init(geo);
+#pragma unroll
+  for (int k = 0; k + 1 < NP; k += 2) {
+    const float2 gam = make_float2(tab.xi[k], tab.xi[k + 1]);
+    float2 sc = make_float2(0.f, 0.f);
+    if (valid) {
+      if constexpr (GEO == 2) {
+        sc = make_float2(scale[base + k * NP2], scale[base + (k + 1) * NP2]);
+      } else {
+        const float2 dt = geo2.det(gam);
+        const float2 wk = __fmul2_rn(OtfColumnF2::dup(wij), make_float2(tab.w[k], tab.w[k + 1]));
+        sc = make_float2(div_fast(wk.x, dt.x), div_fast(wk.y, dt.y));
+      }
+    }
+    float2 vr = make_float2(rR[k], rR[k + 1]), vs = make_float2(rS[k], rS[k + 1]), vt = make_float2(rT[k], rT[k + 1]);
+    geo2.apply(gam, sc, vr, vs, vt);
+    rR[k] = vr.x;
+    rR[k + 1] = vr.y;
+    rS[k] = vs.x;
+    rS[k + 1] = vs.y;
+    rT[k] = vt.x;
+    rT[k + 1] = vt.y;
+  }
+}
 
 // Element stride of the stored factors (the mesh pads each element's [6][P] block to 16 bytes).
 template <int NP, typename T>
@@ -403,8 +485,10 @@ __global__ void __launch_bounds__(NP * NP * EPB)
       rR[k] = sB[at];
       rS[k] = sA[at];
     }
+    constexpr int kPaired = OTF && std::is_same_v<T, float> ? NP / 2 * 2 : 0;  // two points per step
+    if constexpr (kPaired > 0) otf_pairs<NP, GEO>(tab, geo, wij, valid, scale, base, rR, rS, rT);
 #pragma unroll
-    for (int k = 0; k < NP; ++k) {
+    for (int k = kPaired; k < NP; ++k) {
       const T ur = rR[k], us = rS[k], ut = rT[k];
       T vr, vs, vt;
       if constexpr (OTF) {

@@ -30,11 +30,16 @@ namespace sem {
 namespace {
 
 // Even/odd split of D and D^T (EoMat, computed in FP64) with every entry as a float pair.
+// For the two-wide FP32 operations of sm_100 and later, the H x H blocks are also kept
+// interleaved, (E(i,l), O(i,l)) as one float2: C = high parts, NC and NCL = negated high and
+// low parts (eo_apply_df forms the products of both sums at once and carries their error
+// terms negated).
 template <int NP>
 struct DfEo {
   static constexpr int H = NP / 2, HC = (NP + 1) / 2;
   float Eh[H][HC], El[H][HC];
   float Oh[HC][H], Ol[HC][H];
+  float2 C[H][H], NC[H][H], NCL[H][H];
 };
 
 template <int NP>
@@ -56,6 +61,12 @@ DfEo<NP> split_eo(const EoMat<NP, double>& m) {
       d.Oh[a][b] = static_cast<float>(m.O[a][b]);
       d.Ol[a][b] = static_cast<float>(m.O[a][b] - static_cast<double>(d.Oh[a][b]));
     }
+  for (int a = 0; a < H; ++a)
+    for (int b = 0; b < H; ++b) {
+      d.C[a][b] = make_float2(d.Eh[a][b], d.Oh[a][b]);
+      d.NC[a][b] = make_float2(-d.Eh[a][b], -d.Oh[a][b]);
+      d.NCL[a][b] = make_float2(-d.El[a][b], -d.Ol[a][b]);
+    }
   return d;
 }
 
@@ -66,9 +77,51 @@ DfTab<NP> make_df_tab(int N) {
 }
 
 // out = M in in double-float (see EoMat for the split); `in` and `out` may not alias.
+// Even NP: the sums A_i (over the even combinations) and B_i (over the odd ones) have the same
+// number of terms, so both run in the two lanes of float2 operations: each error-free product
+// and each two-sum of the tree is one two-wide instruction per step for both. The error terms
+// are carried negated (ne = p - a b, formed by a multiply-add with the negated constants, so
+// that p itself needs no negation); round-to-nearest is symmetric, so every lane holds exactly
+// the negation of what the scalar steps would hold and the results are the same bit for bit.
 template <int NP>
 __device__ __forceinline__ void eo_apply_df(const DfEo<NP>& M, const df2 (&in)[NP], df2 (&out)[NP]) {
   constexpr int H = NP / 2, N = NP - 1, HA = H + NP % 2;
+  if constexpr (NP % 2 == 0) {
+    float2 X[H], XL[H];  // (even, odd) combinations: high parts, low parts
+#pragma unroll
+    for (int l = 0; l < H; ++l) {
+      const df2 ev = df_add_nr(in[l], in[N - l]);
+      const df2 od = df_add_nr(in[l], df_neg(in[N - l]));
+      X[l] = make_float2(ev.h, od.h);
+      XL[l] = make_float2(ev.l, od.l);
+    }
+#pragma unroll
+    for (int i = 0; i < H; ++i) {
+      float2 pp[H], ne[H];
+#pragma unroll
+      for (int l = 0; l < H; ++l) {
+        pp[l] = __fmul2_rn(M.C[i][l], X[l]);
+        ne[l] = __ffma2_rn(M.NC[i][l], X[l], pp[l]);  // exact: p - ah bh
+        ne[l] = __ffma2_rn(M.NC[i][l], XL[l], ne[l]);
+        ne[l] = __ffma2_rn(M.NCL[i][l], X[l], ne[l]);
+      }
+#pragma unroll
+      for (int wd = 1; wd < H; wd *= 2) {
+#pragma unroll
+        for (int a = 0; a + wd < H; a += 2 * wd) {
+          const float2 sm = __fadd2_rn(pp[a], pp[a + wd]);  // Knuth's two-sum in both lanes
+          const float2 bb = fsub2_rn(sm, pp[a]);
+          const float2 t = __fadd2_rn(fsub2_rn(pp[a], fsub2_rn(sm, bb)), fsub2_rn(pp[a + wd], bb));
+          pp[a] = sm;
+          ne[a] = __fadd2_rn(ne[a], fsub2_rn(ne[a + wd], t));
+        }
+      }
+      const df2 A{pp[0].x, -ne[0].x}, B{pp[0].y, -ne[0].y};
+      out[i] = df_add_nr(A, B);  // unnormalised pairs: exact sums, valid operands downstream
+      out[N - i] = df_add_nr(B, df_neg(A));
+    }
+    return;
+  }
   df2 e[H], o[H];
 #pragma unroll
   for (int l = 0; l < H; ++l) {

@@ -118,11 +118,11 @@ __global__ void __launch_bounds__(NP * NP * EPB)
       rR[k] = sB[at];
       rS[k] = sA[at];
     }
-#pragma unroll
-    for (int k = 0; k < NP; ++k) {
-      const F gam = tab.xi[k];
-      const F sc = valid ? div_fast(wij * tab.w[k], geo.det(gam)) : F(0);
-      geo.apply(gam, sc, rR[k], rS[k], rT[k]);
+    otf_pairs<NP, 1>(tab, geo, wij, valid, nullptr, base, rR, rS, rT);  // two points at a time
+    if constexpr (NP % 2 == 1) {
+      const F gam = tab.xi[NP - 1];
+      const F sc = valid ? div_fast(wij * tab.w[NP - 1], geo.det(gam)) : F(0);
+      geo.apply(gam, sc, rR[NP - 1], rS[NP - 1], rT[NP - 1]);
     }
 #pragma unroll
     for (int k = 0; k < NP; ++k) {

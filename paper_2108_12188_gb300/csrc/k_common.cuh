@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "sem_internal.h"
 
 namespace sem {
@@ -20,8 +22,18 @@ namespace sem {
 // exist for odd NP only (middle index m = H, where M(m,m) = 0). E carries M(i,m) as its last
 // column and O carries M(m,l) as its last row. A line of NP values then costs 2 H^2 + 4 H
 // (+ 2 H) operations instead of NP^2.
+// FP32: the H x H blocks of E and O interleaved, (E(i,l), O(i,l)) as one float2, so that
+// eo_apply forms A_i and B_i together with the two-wide FP32 multiply-add of sm_100 and
+// later (one instruction for both sums, the same roundings as two scalar ones).
 template <int NP, typename T>
-struct EoMat {
+struct EoPairs {};
+template <int NP>
+struct EoPairs<NP, float> {
+  float2 EO[NP / 2 > 0 ? NP / 2 : 1][NP / 2 > 0 ? NP / 2 : 1];
+};
+
+template <int NP, typename T>
+struct EoMat : EoPairs<NP, T> {
   static constexpr int H = NP / 2, HC = (NP + 1) / 2;
   T E[H][HC];
   T O[HC][H];
@@ -48,6 +60,9 @@ inline EoMat<NP, T> make_eo(F m) {
     }
     if (NP % 2) r.E[i][(NP + 1) / 2 - 1] = static_cast<T>(m(i, H));
   }
+  if constexpr (std::is_same_v<T, float>)
+    for (int i = 0; i < H; ++i)
+      for (int l = 0; l < H; ++l) r.EO[i][l] = make_float2(r.E[i][l], r.O[i][l]);
   if (NP % 2)
     for (int l = 0; l < H; ++l) r.O[(NP + 1) / 2 - 1][l] = static_cast<T>(m(H, l));
   return r;
@@ -79,11 +94,21 @@ __device__ __forceinline__ void eo_apply(const EoMat<NP, T>& M, const T (&in)[NP
   }
 #pragma unroll
   for (int i = 0; i < H; ++i) {
-    T a = M.E[i][0] * e[0], b = M.O[i][0] * o[0];
+    T a, b;
+    if constexpr (std::is_same_v<T, float>) {  // both sums in one two-wide multiply-add per l
+      float2 ab = __fmul2_rn(M.EO[i][0], make_float2(e[0], o[0]));
 #pragma unroll
-    for (int l = 1; l < H; ++l) {
-      a += M.E[i][l] * e[l];
-      b += M.O[i][l] * o[l];
+      for (int l = 1; l < H; ++l) ab = __ffma2_rn(M.EO[i][l], make_float2(e[l], o[l]), ab);
+      a = ab.x;
+      b = ab.y;
+    } else {
+      a = M.E[i][0] * e[0];
+      b = M.O[i][0] * o[0];
+#pragma unroll
+      for (int l = 1; l < H; ++l) {
+        a += M.E[i][l] * e[l];
+        b += M.O[i][l] * o[l];
+      }
     }
     if constexpr (NP % 2 == 1) a += M.E[i][H] * in[H];
     out[i] = a + b;

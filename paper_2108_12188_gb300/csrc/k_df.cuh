@@ -49,6 +49,18 @@ __device__ __forceinline__ df2 df_from_double(double x) {
   return r;
 }
 
+// Two-wide FP32 subtraction (sm_100 and later), a - b in each lane, rounded to nearest; the
+// CUDA headers provide the add, multiply and multiply-add forms only.
+__device__ __forceinline__ float2 fsub2_rn(float2 a, float2 b) {
+  unsigned long long ra, rb, rd;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(ra) : "f"(a.x), "f"(a.y));
+  asm("mov.b64 %0, {%1, %2};" : "=l"(rb) : "f"(b.x), "f"(b.y));
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(rd) : "l"(ra), "l"(rb));
+  float2 d;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(d.x), "=f"(d.y) : "l"(rd));
+  return d;
+}
+
 __device__ __forceinline__ double df_to_double(df2 a) {
   return static_cast<double>(a.h) + static_cast<double>(a.l);
 }

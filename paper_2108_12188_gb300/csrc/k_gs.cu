@@ -103,7 +103,7 @@ __global__ void k_dssum(const GsPlan g, T* __restrict__ u, int apply_mask) {
 // The last block adds the operator's partials (and its own), forms <p, w, c> and
 // alpha = rho / <p, w, c> (Algorithm 1 step 8).
 template <typename T, bool DOT>
-__global__ void k_dssum_cg(const GsPlan g, T* __restrict__ w, const T* __restrict__ p, CgScalars* __restrict__ st,
+__global__ void __launch_bounds__(kThreads, 4) k_dssum_cg(const GsPlan g, T* __restrict__ w, const T* __restrict__ p, CgScalars* __restrict__ st,
                            const double* __restrict__ ax_partials, int ax_blocks, double* __restrict__ partials) {
   __shared__ double sRed[kThreads / 32];
   if (st->done) return;
