@@ -502,6 +502,7 @@ def run_gpu(args):
                                         ("stored", sem.SEM_AX_STORED, "f64x", sem.SEM_F64X),
                                         ("stored", sem.SEM_AX_STORED, "f32", sem.SEM_F32),
                                         ("otf", sem.SEM_AX_OTF, "f64", sem.SEM_F64),
+                                        ("otf", sem.SEM_AX_OTF, "f64x", sem.SEM_F64X),
                                         ("otf", sem.SEM_AX_OTF, "f32", sem.SEM_F32),
                                         ("otf_tc", sem.SEM_AX_OTF, "f32", sem.SEM_F32),
                                         ("otfscale", sem.SEM_AX_OTF_SCALE, "f64", sem.SEM_F64),

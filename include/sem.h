@@ -57,9 +57,12 @@ typedef enum {
  * SEM_F64X: FP64 data (double* vectors, FP64 stored factors); the local operator runs in
  * double-float arithmetic (pairs of floats with error-free products and sums, about 47
  * significant bits) on the FP32 pipes, which GB300 issues 64 times faster than FP64. Only
- * sem_ax with SEM_AX_STORED (and the CG options' f64_arith) use it, with the float-pair factors of
- * SEM_MESH_F64X_STORED if the mesh has them, else the FP64 ones; every other call treats
- * SEM_F64X like SEM_F64. Values below 2^-126 in magnitude are flushed to zero inside it. */
+ * sem_ax (and the CG options' f64_arith) use it: with SEM_AX_STORED on the float-pair factors of
+ * SEM_MESH_F64X_STORED if the mesh has them, else the FP64 ones; with SEM_AX_OTF on factors
+ * rebuilt from the element's trilinear coefficients (the per-column polynomial coefficients
+ * in FP64, every point in double-float); SEM_AX_OTF_SCALE gives SEM_ERR_UNSUPPORTED. Every
+ * other call treats SEM_F64X like SEM_F64. Values below 2^-126 in magnitude are flushed to
+ * zero inside it. */
 typedef enum { SEM_F64 = 0, SEM_F32 = 1, SEM_F64X = 2 } sem_prec;
 
 /* Variants of the local operator A_L (Section 5.1):
@@ -274,7 +277,7 @@ typedef struct {
                        * CG with stored factors on a mesh with fewer elements than the GPU has SMs runs
                        * check_every iterations in one persistent cooperative kernel (bounded grid
                        * barriers, SEM_ERR_TIMEOUT if one runs out); 0: launch every kernel */
-  int f64_arith;      /* FP64 operator arithmetic: 0 native FP64, 1 double-float (SEM_F64X; stored variant) */
+  int f64_arith;      /* FP64 operator arithmetic: 0 native FP64, 1 double-float (SEM_F64X; stored or otf) */
 } sem_cg_opts;
 
 typedef struct {

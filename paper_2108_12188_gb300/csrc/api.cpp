@@ -183,7 +183,7 @@ void resolve_variant(sem_mesh m, sem_prec prec, sem_ax_variant v, sem_ax_variant
       r = t.best;
     else
       r = has_factors(m, prec) ? SEM_AX_STORED : SEM_AX_OTF;
-    if (prec == SEM_F64X) r = SEM_AX_STORED;
+    if (prec == SEM_F64X && r == SEM_AX_OTF_SCALE) r = has_factors(m, prec) ? SEM_AX_STORED : SEM_AX_OTF;
   }
   *out_v = r;
   *out_shape = t.valid ? t.shape[vslot(r)] : 0;
@@ -734,8 +734,8 @@ sem_status cg_alloc(sem_mesh m, sem_prec prec, sem_ax_variant v, int precond, do
   *out = nullptr;
   if (v == SEM_AX_STORED && !has_factors(m, prec))
     return fail(SEM_ERR_ARG, "stored factors of this precision were not requested at mesh creation");
-  if (prec == SEM_F64X && (v == SEM_AX_OTF || v == SEM_AX_OTF_SCALE))
-    return fail(SEM_ERR_UNSUPPORTED, "double-float FP64 arithmetic runs the stored-factor variant only");
+  if (prec == SEM_F64X && v == SEM_AX_OTF_SCALE)
+    return fail(SEM_ERR_UNSUPPORTED, "double-float FP64 arithmetic runs the stored and on-the-fly variants");
   if (v == SEM_AX_OTF_SCALE && !has_scales(m))
     return fail(SEM_ERR_ARG, "per-point scales were not requested at mesh creation (SEM_MESH_OTF_SCALE)");
   if (cg_layout(prec)) SEM_TRY(ensure_cg_layout(m, m->home));
@@ -1335,7 +1335,7 @@ extern "C" sem_status sem_autotune(sem_mesh m, sem_prec prec, int reps, sem_tune
     for (const sem_ax_variant v : {SEM_AX_STORED, SEM_AX_OTF, SEM_AX_OTF_SCALE}) {
       if (st != SEM_OK) break;
       if (v == SEM_AX_STORED && !has_factors(m, prec)) continue;
-      if (v != SEM_AX_STORED && prec == SEM_F64X) continue;
+      if (v == SEM_AX_OTF_SCALE && prec == SEM_F64X) continue;
       if (v == SEM_AX_OTF_SCALE && !has_scales(m)) continue;
       for (int shape : {0, 1, kTensorShape}) {
         if (st != SEM_OK) break;

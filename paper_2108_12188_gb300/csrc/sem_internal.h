@@ -308,6 +308,9 @@ constexpr int kTensorShape = 3;
 bool ax_tensor_available(int N, sem_prec prec, sem_ax_variant v);
 sem_status launch_ax_tc(int N, bool cg_mode, const AxLaunch& a, cudaStream_t s);
 sem_status launch_ax_f64x(int N, sem_ax_variant v, bool cg_mode, const AxLaunch& a, cudaStream_t s);
+sem_status launch_ax_f64x_hi(int N, bool cg_mode, const AxLaunch& a, cudaStream_t s);      // stored, N + 1 >= 8
+sem_status launch_ax_f64x_otf_lo(int N, bool cg_mode, const AxLaunch& a, cudaStream_t s);  // on the fly, N + 1 <= 7
+sem_status launch_ax_f64x_otf_hi(int N, bool cg_mode, const AxLaunch& a, cudaStream_t s);  // on the fly, N + 1 >= 8
 // The local operator of a mesh (api.cpp): resolves SEM_AX_AUTO and the block shape, fills the
 // mesh's data pointers into `a` and launches the kernel of the precision.
 sem_status launch_ax_any(sem_mesh_s* m, sem_prec prec, sem_ax_variant v, bool cg, AxLaunch a, cudaStream_t s);

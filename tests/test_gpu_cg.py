@@ -52,9 +52,10 @@ def _solve(sem, mesh, prob, opts):
 
 
 @pytest.mark.parametrize("variant,use_graph,check_every,f64_arith", [(0, 1, 50, 0), (1, 1, 17, 0), (0, 0, 1, 0),
-                                                                     (0, 1, 50, 1), (0, 2, 50, 0), (0, 2, 7, 0)],
-                         ids=["stored-graph", "otf-graph", "stored-eager", "stored-doublefloat", "stored-persistent",
-                              "stored-persistent-short-runs"])
+                                                                     (0, 1, 50, 1), (1, 1, 50, 1), (0, 2, 50, 0),
+                                                                     (0, 2, 7, 0)],
+                         ids=["stored-graph", "otf-graph", "stored-eager", "stored-doublefloat", "otf-doublefloat",
+                              "stored-persistent", "stored-persistent-short-runs"])
 def test_cg_fp64_matches_oracle(sem, c1, variant, use_graph, check_every, f64_arith):
     m, prob, b, ref, mesh = c1
     opts = sem.sem_cg_default_opts(rtol=1e-10, variant=variant, use_graph=use_graph, check_every=check_every,

@@ -105,9 +105,9 @@ def test_geometry(sem, dims, N, jitter, seed):
     np.testing.assert_allclose(_h(xyz), want, rtol=0, atol=4e-15)
 
 
-VARIANTS = [(0, 0, 1e-12), (1, 0, 1e-12), (0, 1, 2e-6), (1, 1, 2e-6), (0, 2, 1e-12), (3, 0, 1e-12),
+VARIANTS = [(0, 0, 1e-12), (1, 0, 1e-12), (0, 1, 2e-6), (1, 1, 2e-6), (0, 2, 1e-12), (1, 2, 1e-12), (3, 0, 1e-12),
             (3, 1, 2e-6)]  # (variant, prec, tol)
-VIDS = ["stored-f64", "otf-f64", "stored-f32", "otf-f32", "stored-f64x", "otfscale-f64", "otfscale-f32"]
+VIDS = ["stored-f64", "otf-f64", "stored-f32", "otf-f32", "stored-f64x", "otf-f64x", "otfscale-f64", "otfscale-f32"]
 
 
 @pytest.mark.parametrize("variant,prec,tol", VARIANTS, ids=VIDS)
@@ -205,9 +205,9 @@ def test_invalid_inputs(sem):
         sem.sem_ax(mesh.handle, sem.SEM_AX_STORED, sem.SEM_F32, u, w)
     assert e.value.status == sem.SEM_ERR_ARG
     u64, w64 = torch.zeros(mesh.n, dtype=torch.float64, device="cuda"), torch.zeros(mesh.n, dtype=torch.float64, device="cuda")
-    with pytest.raises(sem.SemError) as e:  # double-float arithmetic has no on-the-fly variant
-        sem.sem_ax(mesh.handle, sem.SEM_AX_OTF, sem.SEM_F64X, u64, w64)
-    assert e.value.status == sem.SEM_ERR_UNSUPPORTED
+    with pytest.raises(sem.SemError) as e:  # double-float arithmetic has no stored-scale variant
+        sem.sem_ax(mesh.handle, sem.SEM_AX_OTF_SCALE, sem.SEM_F64X, u64, w64)
+    assert e.value.status in (sem.SEM_ERR_UNSUPPORTED, sem.SEM_ERR_ARG)
     u64 = torch.zeros(mesh.n + 1, dtype=torch.float64, device="cuda")
     lib = sem.load_library()
     st = lib.sem_ax(mesh.handle, 0, 0, u64.data_ptr() + 8, u64.data_ptr(), 0, None)  # misaligned
