@@ -495,8 +495,15 @@ def run_gpu(args):
                 "step_bytes_algorithmic": cg_bytes_per_point(NORD) * n,
                 "step_hbm_frac": cg_bytes_per_point(NORD) * n / (ms_step * 1e-3) / 1e9 / hbm_gbs}
 
-    # ---- the local operator alone, per variant (rank 0 reports)
+    # ---- the local operator alone, per variant (rank 0 reports), each FP32 variant at the block
+    # shape the tuner picks on this mesh (what SEM_AX_AUTO runs); FP64 keeps its default shapes
     ax = {}
+    tune32 = sem.sem_autotune(mesh.handle, sem.SEM_F32)
+    otf32_shape = min((c for c in tune32["candidates"] if c["variant"] == sem.SEM_AX_OTF
+                       and c["shape"] != sem.SEM_TENSOR_SHAPE), key=lambda c: c["ms"])["shape"]
+    sem.sem_autotune_set(NORD, sem.SEM_F32, sem.SEM_AX_OTF, otf32_shape)
+    ax["f32_tune"] = [{"variant": c["variant"], "shape": c["shape"], "elements_per_block": c["elements_per_block"],
+                       "ms": c["ms"]} for c in tune32["candidates"]]
     flush = torch.zeros(96 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 384 MB > L2
     for vname, variant, pname, prec in (("stored", sem.SEM_AX_STORED, "f64", sem.SEM_F64),
                                         ("stored", sem.SEM_AX_STORED, "f64x", sem.SEM_F64X),
@@ -523,7 +530,7 @@ def run_gpu(args):
             t_roof = max(byt / (hbm_gbs * 1e9), fl / (peak_tf * 1e12))
         err = ax_error_vs_oracle(sem, mesh, m, variant, prec) if rank == 0 else None
         if vname == "otf_tc":
-            sem.sem_autotune_set(NORD, sem.SEM_F32, sem.SEM_AX_OTF, 0)
+            sem.sem_autotune_set(NORD, sem.SEM_F32, sem.SEM_AX_OTF, otf32_shape)
         ax[f"{pname}_{vname}"] = {
             "ms": med, "ms_min": lo, "ms_max": hi, "gdof_s": n / (med * 1e-3) / 1e9,
             "gflop_s_eq11": fl / (med * 1e-3) / 1e9, "hbm_gbs": byt / (med * 1e-3) / 1e9,

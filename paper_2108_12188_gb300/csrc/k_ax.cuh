@@ -263,8 +263,11 @@ __host__ __device__ constexpr size_t ax_smem_bytes() {
 //   5  column: w = the three sums; stored (CG mode: p.w added, see kWholeDot)
 // with a block barrier between phases. Every thread reads and writes only its own line in
 // the in-place phases.
+// FP32 with the stored scale per point at N = 7: at most 80 registers, so that 12 / EPB blocks
+// share an SM (measured at 32^3: 0.087 -> 0.078 ms; the same cap made the on-the-fly variant
+// slower, so it applies to the scale variant only).
 template <int NP, typename T, int GEO, bool CG, int EPB>
-__global__ void __launch_bounds__(NP * NP * EPB)
+__global__ void __launch_bounds__(NP * NP * EPB, (sizeof(T) == 4 && GEO == 2 && NP == 8) ? 12 / EPB : 1)
     k_ax(const __grid_constant__ GllParam<NP, T> tab, int64_t E, const T* __restrict__ u, T* __restrict__ w,
          const T* __restrict__ G, const T* __restrict__ coef, const T* __restrict__ scale, const T* __restrict__ z,
          T* __restrict__ p, const T* __restrict__ r, const T* __restrict__ minv, T* __restrict__ x,
