@@ -122,83 +122,48 @@ struct OtfColumn {
   }
 };
 
-// FP32: the column polynomials of OtfColumn with every coefficient held twice, (c, c) as one
-// float2, so that two points of the column (gam, gam') are evaluated together by the
-// two-wide FP32 multiply-adds of sm_100 and later. Each lane performs the operations of
-// OtfColumn::det and OtfColumn::apply in the same order.
-struct OtfColumnF2 {
-  float2 c0a[3], c0b[3], c1a[3], c1b[3], c2a[3], c2b[3], c2c[3];
-  float2 da, db, dc;
-
-  __device__ __forceinline__ static float2 dup(float v) { return make_float2(v, v); }
-  __device__ __forceinline__ static void dup3(float2 (&d)[3], const Vec3<float>& v) {
-    d[0] = dup(v.x);
-    d[1] = dup(v.y);
-    d[2] = dup(v.z);
-  }
-  __device__ __forceinline__ void init(const OtfColumn<float>& g) {
-    dup3(c0a, g.c0a);
-    dup3(c0b, g.c0b);
-    dup3(c1a, g.c1a);
-    dup3(c1b, g.c1b);
-    dup3(c2a, g.c2a);
-    dup3(c2b, g.c2b);
-    dup3(c2c, g.c2c);
-    da = dup(g.da);
-    db = dup(g.db);
-    dc = dup(g.dc);
-  }
-  __device__ __forceinline__ float2 det(float2 gam) const {
-    return __ffma2_rn(gam, __ffma2_rn(gam, dc, db), da);
-  }
-  __device__ __forceinline__ void apply(float2 gam, float2 sc, float2& ur, float2& us, float2& ut) const {
-    float2 c0[3], c1[3], c2[3], q[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      c0[d] = __ffma2_rn(gam, c0b[d], c0a[d]);
-      c1[d] = __ffma2_rn(gam, c1b[d], c1a[d]);
-      c2[d] = __ffma2_rn(gam, __ffma2_rn(gam, c2c[d], c2b[d]), c2a[d]);
-    }
-#pragma unroll
-    for (int d = 0; d < 3; ++d)
-      q[d] = __fmul2_rn(sc, __ffma2_rn(c2[d], ut, __ffma2_rn(c1[d], us, __fmul2_rn(c0[d], ur))));
-    ur = __ffma2_rn(c0[2], q[2], __ffma2_rn(c0[1], q[1], __fmul2_rn(c0[0], q[0])));
-    us = __ffma2_rn(c1[2], q[2], __ffma2_rn(c1[1], q[1], __fmul2_rn(c1[0], q[0])));
-    ut = __ffma2_rn(c2[2], q[2], __ffma2_rn(c2[1], q[1], __fmul2_rn(c2[0], q[0])));
-  }
-};
-
-// Phase 3 of the FP32 on-the-fly operator for the points k < 2 (NP / 2) of a column, two at a
-// time: (rR, rS, rT) <- (w_i w_j w_k / det J) C (C^T (rR, rS, rT)) (GEO 1), or with the stored
-// word per point instead of w_i w_j w_k / det J (GEO 2, scale[base + k NP^2]).
+// Phase 3 of the FP32 on-the-fly operator on one column, one point per step:
+// (rR, rS, rT) <- (w_i w_j w_k / det J) C (C^T (rR, rS, rT)) (GEO 1), or with the stored word
+// per point instead of w_i w_j w_k / det J (GEO 2, scale[base + k NP^2]). The nine cofactor
+// entries and det J are evaluated two at a time in the lanes of the two-wide FP32 multiply-add
+// of sm_100 and later, paired by component: (c0_x, c0_y), (c0_z, c1_z), (c1_x, c1_y) (linear in
+// gam) and (c2_x, c2_y), (c2_z, det J) (quadratic), so no coefficient is duplicated; every
+// lane performs the operations of OtfColumn in the same order.
 template <int NP, int GEO>
-__device__ __forceinline__ void otf_pairs(const GllParam<NP, float>& tab, const OtfColumn<float>& geo, float wij,
+__device__ __forceinline__ void otf_lanes(const GllParam<NP, float>& tab, const OtfColumn<float>& geo, float wij,
                                           bool valid, const float* __restrict__ scale, int64_t base,
                                           float (&rR)[NP], float (&rS)[NP], float (&rT)[NP]) {
   constexpr int NP2 = NP * NP;
-  OtfColumnF2 geo2;
-  geo2.init(geo);
+  const float2 la[3] = {make_float2(geo.c0a.x, geo.c0a.y), make_float2(geo.c0a.z, geo.c1a.z),
+                        make_float2(geo.c1a.x, geo.c1a.y)};
+  const float2 lb[3] = {make_float2(geo.c0b.x, geo.c0b.y), make_float2(geo.c0b.z, geo.c1b.z),
+                        make_float2(geo.c1b.x, geo.c1b.y)};
+  const float2 qa[2] = {make_float2(geo.c2a.x, geo.c2a.y), make_float2(geo.c2a.z, geo.da)};
+  const float2 qb[2] = {make_float2(geo.c2b.x, geo.c2b.y), make_float2(geo.c2b.z, geo.db)};
+  const float2 qc[2] = {make_float2(geo.c2c.x, geo.c2c.y), make_float2(geo.c2c.z, geo.dc)};
 #pragma unroll
-  for (int k = 0; k + 1 < NP; k += 2) {
-    const float2 gam = make_float2(tab.xi[k], tab.xi[k + 1]);
-    float2 sc = make_float2(0.f, 0.f);
+  for (int k = 0; k < NP; ++k) {
+    const float gam = tab.xi[k];
+    const float2 g2 = make_float2(gam, gam);
+    float2 l[3], q[2];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) l[a] = __ffma2_rn(g2, lb[a], la[a]);
+#pragma unroll
+    for (int a = 0; a < 2; ++a) q[a] = __ffma2_rn(g2, __ffma2_rn(g2, qc[a], qb[a]), qa[a]);
+    const Vec3<float> c0{l[0].x, l[0].y, l[1].x}, c1{l[2].x, l[2].y, l[1].y}, c2{q[0].x, q[0].y, q[1].x};
+    float sc = 0.f;
     if (valid) {
-      if constexpr (GEO == 2) {
-        sc = make_float2(scale[base + k * NP2], scale[base + (k + 1) * NP2]);
-      } else {
-        const float2 dt = geo2.det(gam);
-        const float2 wk = __fmul2_rn(OtfColumnF2::dup(wij), make_float2(tab.w[k], tab.w[k + 1]));
-        sc = make_float2(div_fast(wk.x, dt.x), div_fast(wk.y, dt.y));
-      }
+      if constexpr (GEO == 2)
+        sc = scale[base + k * NP2];
+      else
+        sc = div_fast(wij * tab.w[k], q[1].y);
     }
-    float2 vr = make_float2(rR[k], rR[k + 1]), vs = make_float2(rS[k], rS[k + 1]), vt = make_float2(rT[k], rT[k + 1]);
-    geo2.apply(gam, sc, vr, vs, vt);
-    rR[k] = vr.x;
-    rR[k + 1] = vr.y;
-    rS[k] = vs.x;
-    rS[k + 1] = vs.y;
-    rT[k] = vt.x;
-    rT[k + 1] = vt.y;
+    const float ur = rR[k], us = rS[k], ut = rT[k];
+    const Vec3<float> qv{sc * (c0.x * ur + c1.x * us + c2.x * ut), sc * (c0.y * ur + c1.y * us + c2.y * ut),
+                         sc * (c0.z * ur + c1.z * us + c2.z * ut)};
+    rR[k] = dot3(c0, qv);
+    rS[k] = dot3(c1, qv);
+    rT[k] = dot3(c2, qv);
   }
 }
 
@@ -263,11 +228,8 @@ __host__ __device__ constexpr size_t ax_smem_bytes() {
 //   5  column: w = the three sums; stored (CG mode: p.w added, see kWholeDot)
 // with a block barrier between phases. Every thread reads and writes only its own line in
 // the in-place phases.
-// FP32 with the stored scale per point at N = 7: at most 80 registers, so that 12 / EPB blocks
-// share an SM (measured at 32^3: 0.087 -> 0.078 ms; the same cap made the on-the-fly variant
-// slower, so it applies to the scale variant only).
 template <int NP, typename T, int GEO, bool CG, int EPB>
-__global__ void __launch_bounds__(NP * NP * EPB, (sizeof(T) == 4 && GEO == 2 && NP == 8) ? 12 / EPB : 1)
+__global__ void __launch_bounds__(NP * NP * EPB)
     k_ax(const __grid_constant__ GllParam<NP, T> tab, int64_t E, const T* __restrict__ u, T* __restrict__ w,
          const T* __restrict__ G, const T* __restrict__ coef, const T* __restrict__ scale, const T* __restrict__ z,
          T* __restrict__ p, const T* __restrict__ r, const T* __restrict__ minv, T* __restrict__ x,
@@ -488,10 +450,10 @@ __global__ void __launch_bounds__(NP * NP * EPB, (sizeof(T) == 4 && GEO == 2 && 
       rR[k] = sB[at];
       rS[k] = sA[at];
     }
-    constexpr int kPaired = OTF && std::is_same_v<T, float> ? NP / 2 * 2 : 0;  // two points per step
-    if constexpr (kPaired > 0) otf_pairs<NP, GEO>(tab, geo, wij, valid, scale, base, rR, rS, rT);
+    constexpr bool kLanes = OTF && std::is_same_v<T, float>;  // FP32: otf_lanes does the column
+    if constexpr (kLanes) otf_lanes<NP, GEO>(tab, geo, wij, valid, scale, base, rR, rS, rT);
 #pragma unroll
-    for (int k = kPaired; k < NP; ++k) {
+    for (int k = kLanes ? NP : 0; k < NP; ++k) {
       const T ur = rR[k], us = rS[k], ut = rT[k];
       T vr, vs, vt;
       if constexpr (OTF) {

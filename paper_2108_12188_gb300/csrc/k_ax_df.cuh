@@ -369,6 +369,10 @@ __global__ void __launch_bounds__(NP * NP * ax_epb<NP>(), (CG && NP == 8) ? 4 : 
     const int64_t e0 = static_cast<int64_t>(blockIdx.x) * EPB;
     prefetch_factors<NP>(sG, G, e0, static_cast<int>(E - e0 < EPB ? E - e0 : EPB), bar);
   }
+  // CG: bulk L2 prefetches of the vectors need 16-byte aligned element blocks (the library's
+  // own vectors are; P even makes every block's offset a multiple of 16 bytes)
+  const bool vec_l2 = CG && ((reinterpret_cast<uintptr_t>(p) | reinterpret_cast<uintptr_t>(x) |
+                              reinterpret_cast<uintptr_t>(r) | reinterpret_cast<uintptr_t>(minv)) & 15u) == 0;
   const int slot = threadIdx.x / NP2, tid = threadIdx.x % NP2;
   const int i = tid % NP, j = tid / NP;  // column (i, j); i-row (j, k) = (i, j); j-line (i, k) = (i, j)
   df2* sA = sA0 + slot * SZ;
@@ -514,9 +518,21 @@ __global__ void __launch_bounds__(NP * NP * ax_epb<NP>(), (CG && NP == 8) ? 4 : 
       }
     }
     __syncthreads();  // the factors are consumed
-    if (!OTF && threadIdx.x == 0 && grp + gridDim.x < n_groups) {
+    if (threadIdx.x == 0 && grp + gridDim.x < n_groups) {
       const int64_t e0 = (grp + gridDim.x) * EPB;
-      prefetch_factors<NP>(sG, G, e0, static_cast<int>(E - e0 < EPB ? E - e0 : EPB), bar);
+      const int cnt = static_cast<int>(E - e0 < EPB ? E - e0 : EPB);
+      if constexpr (!OTF) prefetch_factors<NP>(sG, G, e0, cnt, bar);
+      if constexpr (CG && P % 2 == 0) {  // the next group's p, x, r, M^-1 into L2 (phase 0 reads them)
+        if (vec_l2) {
+          for (int q = 0; q < cnt; ++q) {
+            const int64_t off = (e0 + q) * P;
+            l2_prefetch(p + off, P * sizeof(double));
+            l2_prefetch(x + off, P * sizeof(double));
+            l2_prefetch(r + off, P * sizeof(double));
+            if (minv) l2_prefetch(minv + off, P * sizeof(double));
+          }
+        }
+      }
     }
     // phase 4
     df2 rW[NP];

@@ -118,12 +118,7 @@ __global__ void __launch_bounds__(NP * NP * EPB)
       rR[k] = sB[at];
       rS[k] = sA[at];
     }
-    otf_pairs<NP, 1>(tab, geo, wij, valid, nullptr, base, rR, rS, rT);  // two points at a time
-    if constexpr (NP % 2 == 1) {
-      const F gam = tab.xi[NP - 1];
-      const F sc = valid ? div_fast(wij * tab.w[NP - 1], geo.det(gam)) : F(0);
-      geo.apply(gam, sc, rR[NP - 1], rS[NP - 1], rT[NP - 1]);
-    }
+    otf_lanes<NP, 1>(tab, geo, wij, valid, nullptr, base, rR, rS, rT);
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
       const int at = Stage<NP>::at(i, j, k);
