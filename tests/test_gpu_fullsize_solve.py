@@ -46,6 +46,7 @@ SOLVERS = {
     "fp64-cg": dict(variant=0),
     "mixed-reliable-otf": dict(mixed=2, variant=0, inner_variant=1, inner_rtol=0.1),
     "double-float-cg": dict(variant=0, f64_arith=1),
+    "double-float-otf-cg": dict(variant=1, f64_arith=1),
 }
 
 
