@@ -226,8 +226,8 @@ sem_status sem_rhs_sine(sem_mesh mesh, int a, int b, int c, sem_prec prec, void*
  * sem_autotune times every candidate implementation of A_L on this mesh (stored, on-the-fly
  * or on-the-fly with per-point scale where available, times two block shapes: elements per
  * thread block; the per-point-scale variant has one shape; for FP32 on the fly at N = 7 also
- * shape 3, the line contractions on the tensor cores: mma.sync TF32 with split operands)
- * with CUDA events over `reps` launches each, and records the fastest for the mesh's order
+ * shape 3, the line contractions on the tensor cores: mma.sync TF32 with split operands;
+ * for SEM_F64X stored and on the fly, one shape each) with CUDA events over `reps` launches each, and records the fastest for the mesh's order
  * and the precision, process-wide; SEM_AX_AUTO then uses it, and explicit variants use the
  * faster block shape. Synchronises `stream`. sem_autotune_save / sem_autotune_load write and
  * read the table as text, keyed by the GPU name (a table from another GPU model is refused
