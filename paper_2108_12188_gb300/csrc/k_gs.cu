@@ -97,11 +97,11 @@ __global__ void k_dssum(const GsPlan g, T* __restrict__ u, int apply_mask) {
 
 // CG step 7. DOT: also the boundary part of <p, w, c>: after the sum, all copies of a
 // segment hold the same w and the same p, and their weights c = 1/multiplicity add up to
-// one, so the segment contributes p * w once. Without DOT the operator has already formed
-// the whole product over the unassembled w (sum over local points of p_i (A_L p)_i equals
-// <p, QQ^T A_L p, c> because p has one value per global node and is 0 on Dirichlet nodes).
-// The last block adds the operator's partials (and its own), forms <p, w, c> and
-// alpha = rho / <p, w, c> (Algorithm 1 step 8).
+// one, so the segment contributes p * w once; the last block adds the operator's partials and
+// its own, forms <p, w, c> and alpha = rho / <p, w, c> (Algorithm 1 step 8). Without DOT the
+// operator has already formed the whole product over the unassembled w (sum over local points
+// of p_i (A_L p)_i equals <p, QQ^T A_L p, c> because p has one value per global node and is 0
+// on Dirichlet nodes), the update kernel forms alpha, and this kernel reduces nothing.
 template <typename T, bool DOT>
 __global__ void __launch_bounds__(kThreads, 4) k_dssum_cg(const GsPlan g, T* __restrict__ w, const T* __restrict__ p, CgScalars* __restrict__ st,
                            const double* __restrict__ ax_partials, int ax_blocks, double* __restrict__ partials) {
@@ -129,19 +129,21 @@ __global__ void __launch_bounds__(kThreads, 4) k_dssum_cg(const GsPlan g, T* __r
     for (int o = o0; o < o1; ++o) w[g.xidx[o]] = s;
     if constexpr (DOT) dot.add(p[first], s);
   }
-  const double v[1] = {block_sum(dot.value(), sRed)};
-  if (publish_partials<1>(v, partials, &st->ticket[0])) {
-    const double a = sum_partials(ax_partials, ax_blocks, 1, 0, sRed);
-    const double b = sum_partials(partials, gridDim.x, 1, 0, sRed);
-    if (threadIdx.x == 0) {
-      const double pw = a + b;
-      st->pw = pw;
-      if (!(pw > 0.0) || !isfinite(pw)) {
-        st->status = SEM_ERR_BREAKDOWN;
-        st->done = 1;
-        st->alpha = 0.0;  // x is not advanced along this p (fused CG: nothing left to flush)
-      } else {
-        st->alpha = st->rho / pw;
+  if constexpr (DOT) {  // without DOT the update kernel forms alpha: nothing to reduce here
+    const double v[1] = {block_sum(dot.value(), sRed)};
+    if (publish_partials<1>(v, partials, &st->ticket[0])) {
+      const double a = sum_partials(ax_partials, ax_blocks, 1, 0, sRed);
+      const double b = sum_partials(partials, gridDim.x, 1, 0, sRed);
+      if (threadIdx.x == 0) {
+        const double pw = a + b;
+        st->pw = pw;
+        if (!(pw > 0.0) || !isfinite(pw)) {
+          st->status = SEM_ERR_BREAKDOWN;
+          st->done = 1;
+          st->alpha = 0.0;  // x is not advanced along this p (fused CG: nothing left to flush)
+        } else {
+          st->alpha = st->rho / pw;
+        }
       }
     }
   }
