@@ -859,10 +859,8 @@ sem_status cg_enqueue_gs(sem_cg c, cudaStream_t s) {
 }
 
 sem_status cg_enqueue_update(sem_cg c, cudaStream_t s) {
-  const bool whole = whole_dot(c->prec);  // alpha from the operator's partials, in the update
   return launch_cg_update(data_prec(c->prec), fused_cg(c->prec), c->m->n, c->x, c->p, c->r, c->w, c->z, minv_of(c),
-                          c->m->mult, c->m->ctab, c->st, c->upd_part, c->m->cg_map, whole ? c->ax_part : nullptr,
-                          whole ? c->ax_blocks : 0, s);
+                          c->m->mult, c->m->ctab, c->st, c->upd_part, c->m->cg_map, s);
 }
 
 // fused_cg: the x update of the last iteration run (a no-op if there is none)

@@ -134,42 +134,13 @@ template <typename T, bool FUSED>
 __global__ void k_cg_update(int64_t n, T* __restrict__ x, const T* __restrict__ p, T* __restrict__ r,
                             const T* __restrict__ w, T* __restrict__ z, const T* __restrict__ minv,
                             const uint8_t* __restrict__ mult, const double* __restrict__ ctab, CgScalars* st,
-                            double* __restrict__ partials, const CgMap map, const double* __restrict__ ax_partials,
-                            int ax_blocks) {
+                            double* __restrict__ partials, const CgMap map) {
   __shared__ double sRed[kThreads / 32];
   if (st->done) return;
   using VT = typename Vec16<T>::type;
   using MT = typename Vec16<T>::mtype;
   constexpr int V = Vec16<T>::V;
-  T alpha;
-  if (ax_partials) {
-    // Algorithm 1 step 8: alpha = rho / <p, w, c> from the operator's block partials (it formed
-    // the whole <p, w>), summed in the same fixed order by every block, so all blocks hold the
-    // same alpha; block 0 records it (and a breakdown) for the host and the next launches.
-    // Every block reads rho before it publishes its partials below, so before the last block
-    // replaces rho.
-    __shared__ double sAlpha;
-    __shared__ int sBad;
-    const double pw = sum_partials(ax_partials, ax_blocks, 1, 0, sRed);
-    if (threadIdx.x == 0) {
-      const bool bad = !(pw > 0.0) || !isfinite(pw);
-      sBad = bad;
-      sAlpha = bad ? 0.0 : st->rho / pw;
-      if (blockIdx.x == 0) {
-        st->pw = pw;
-        st->alpha = sAlpha;  // 0 on a breakdown: x is not advanced along this p
-        if (bad) {
-          st->status = SEM_ERR_BREAKDOWN;
-          st->done = 1;
-        }
-      }
-    }
-    __syncthreads();
-    if (sBad) return;
-    alpha = static_cast<T>(sAlpha);
-  } else {
-    alpha = static_cast<T>(st->alpha);  // formed by the gather-scatter's last block
-  }
+  const T alpha = static_cast<T>(st->alpha);
   const int64_t t0 = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   const int64_t nv = n / V;
@@ -345,8 +316,7 @@ sem_status launch_cg_init(sem_prec prec, int64_t n, const void* b, const void* a
 
 sem_status launch_cg_update(sem_prec prec, bool fused, int64_t n, void* x, const void* p, void* r, const void* w,
                             void* z, const void* minv, const uint8_t* mult, const double* ctab, CgScalars* st,
-                            double* partials, const CgMap& map, const double* ax_partials, int ax_blocks,
-                            cudaStream_t s) {
+                            double* partials, const CgMap& map, cudaStream_t s) {
   const int grid = vec_grid(n, prec != SEM_F64 ? resident_blocks<k_cg_update<float, true>>(kThreads)
                                : fused         ? resident_blocks<k_cg_update<double, true>>(kThreads)
                                                : resident_blocks<k_cg_update<double, false>>(kThreads));
@@ -358,17 +328,15 @@ sem_status launch_cg_update(sem_prec prec, bool fused, int64_t n, void* x, const
     auto* zd = static_cast<double*>(z);
     auto* md = static_cast<const double*>(minv);
     if (fused)
-      k_cg_update<double, true><<<grid, kThreads, 0, s>>>(n, xd, pd, rd, wd, zd, md, mult, ctab, st, partials, map,
-                                                          ax_partials, ax_blocks);
+      k_cg_update<double, true><<<grid, kThreads, 0, s>>>(n, xd, pd, rd, wd, zd, md, mult, ctab, st, partials, map);
     else
-      k_cg_update<double, false><<<grid, kThreads, 0, s>>>(n, xd, pd, rd, wd, zd, md, mult, ctab, st, partials, map,
-                                                           ax_partials, ax_blocks);
+      k_cg_update<double, false><<<grid, kThreads, 0, s>>>(n, xd, pd, rd, wd, zd, md, mult, ctab, st, partials, map);
   } else {
     if (!fused) return fail(SEM_ERR_UNSUPPORTED, "the FP32 CG update runs with the fused operator prologue only");
     k_cg_update<float, true><<<grid, kThreads, 0, s>>>(n, static_cast<float*>(x), static_cast<const float*>(p),
                                                        static_cast<float*>(r), static_cast<const float*>(w),
                                                        static_cast<float*>(z), static_cast<const float*>(minv), mult,
-                                                       ctab, st, partials, map, ax_partials, ax_blocks);
+                                                       ctab, st, partials, map);
   }
   count_launch();
   SEM_CUDA_TRY(cudaGetLastError());

@@ -101,12 +101,29 @@ __global__ void k_dssum(const GsPlan g, T* __restrict__ u, int apply_mask) {
 // its own, forms <p, w, c> and alpha = rho / <p, w, c> (Algorithm 1 step 8). Without DOT the
 // operator has already formed the whole product over the unassembled w (sum over local points
 // of p_i (A_L p)_i equals <p, QQ^T A_L p, c> because p has one value per global node and is 0
-// on Dirichlet nodes), the update kernel forms alpha, and this kernel reduces nothing.
+// on Dirichlet nodes): block 0 sums the operator's partials (complete at this launch) in a
+// fixed order and forms alpha before its share of the segments, and no block reduces anything
+// else (no ticket, no last block).
 template <typename T, bool DOT>
 __global__ void __launch_bounds__(kThreads, 4) k_dssum_cg(const GsPlan g, T* __restrict__ w, const T* __restrict__ p, CgScalars* __restrict__ st,
                            const double* __restrict__ ax_partials, int ax_blocks, double* __restrict__ partials) {
   __shared__ double sRed[kThreads / 32];
   if (st->done) return;
+  if constexpr (!DOT) {
+    if (blockIdx.x == 0) {
+      const double pw = sum_partials(ax_partials, ax_blocks, 1, 0, sRed);
+      if (threadIdx.x == 0) {
+        st->pw = pw;
+        if (!(pw > 0.0) || !isfinite(pw)) {
+          st->status = SEM_ERR_BREAKDOWN;
+          st->done = 1;
+          st->alpha = 0.0;  // x is not advanced along this p (fused CG: nothing left to flush)
+        } else {
+          st->alpha = st->rho / pw;
+        }
+      }
+    }
+  }
   const int64_t t0 = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   DotAcc<T> dot;
@@ -129,7 +146,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_dssum_cg(const GsPlan g, T* __r
     for (int o = o0; o < o1; ++o) w[g.xidx[o]] = s;
     if constexpr (DOT) dot.add(p[first], s);
   }
-  if constexpr (DOT) {  // without DOT the update kernel forms alpha: nothing to reduce here
+  if constexpr (DOT) {  // without DOT block 0 has formed alpha: nothing to reduce here
     const double v[1] = {block_sum(dot.value(), sRed)};
     if (publish_partials<1>(v, partials, &st->ticket[0])) {
       const double a = sum_partials(ax_partials, ax_blocks, 1, 0, sRed);

@@ -392,13 +392,10 @@ sem_status launch_cg_init(sem_prec prec, int64_t n, const void* b, const void* a
                           const void* minv, const uint8_t* mult, const double* ctab, CgScalars* st, double* partials,
                           cudaStream_t s);
 // fused (fused_cg): x and z are left to the operator's CG prologue (see AxLaunch::r). w is read
-// in the CG layout through `map`. ax_partials (ax_blocks of them): the operator's partials of
-// the whole <p, w>, from which every block forms alpha; null: alpha was formed by the
-// gather-scatter (launch_dssum_cg with p).
+// in the CG layout through `map`.
 sem_status launch_cg_update(sem_prec prec, bool fused, int64_t n, void* x, const void* p, void* r, const void* w,
                             void* z, const void* minv, const uint8_t* mult, const double* ctab, CgScalars* st,
-                            double* partials, const CgMap& map, const double* ax_partials, int ax_blocks,
-                            cudaStream_t s);
+                            double* partials, const CgMap& map, cudaStream_t s);
 // perm[loc] = cg_pos of local point loc for N + 1 = NP points per direction (P entries).
 sem_status launch_cg_perm(int NP, int* perm, cudaStream_t s);
 // out[q] = the CG-layout position of local index in[q] (negative entries, record padding, copied).
