@@ -360,8 +360,9 @@ sem_status launch_cast(int64_t n, const double* in, float* out, cudaStream_t s);
 // gather-scatter (k_gs.cu)
 sem_status launch_dssum(sem_prec prec, const GsPlan& g, void* u, int apply_mask, cudaStream_t s);
 // CG variant: with p, also the boundary part of <p, w, c> (the operator added the interior
-// part); with p == nullptr the operator's partials hold the whole product (whole_dot). The
-// last block combines the partials and sets alpha (or a breakdown status).
+// part), and the last block combines the partials and sets alpha (or a breakdown status);
+// with p == nullptr the operator's partials hold the whole product (whole_dot) and block 0
+// sums them and sets alpha before its share of the segments.
 inline bool whole_dot(sem_prec) { return true; }  // every CG-mode operator forms the whole <p, w>
 // The CG layout (CgMap) is used for FP64 data (FP64 and double-float operators): their w does not
 // fit in L2 and the gather-scatter is bound by DRAM sectors. FP32 CG keeps the local layout (its
