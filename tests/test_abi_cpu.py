@@ -159,3 +159,44 @@ def test_probe_argument_errors(sem):
     assert lib.sem_probe_bounded_wait(10, 0, sem.C.byref(ms), None) == sem.SEM_ERR_ARG  # below 1 ms
     assert lib.sem_probe_bounded_wait(3_000_000_000, 0, sem.C.byref(ms), None) == sem.SEM_ERR_ARG
     assert lib.sem_probe_bounded_wait(20_000_000, 0, None, None) == sem.SEM_ERR_ARG
+
+
+def test_tuner_table_rules(sem):
+    """sem_autotune_set validates on the host: shape 1 is not offered for double-float or the
+    per-point-scale variant, shape 3 only where the tensor-core operator is compiled (FP32 on
+    the fly, N = 7); double-float takes the stored and on-the-fly variants."""
+    lib = sem.load_library()
+    try:
+        assert lib.sem_autotune_set(7, sem.SEM_F64X, sem.SEM_AX_OTF, 0) == sem.SEM_OK
+        assert lib.sem_autotune_set(7, sem.SEM_F64X, sem.SEM_AX_STORED, 0) == sem.SEM_OK
+        assert lib.sem_autotune_set(7, sem.SEM_F64X, sem.SEM_AX_OTF, 1) == sem.SEM_ERR_ARG
+        assert lib.sem_autotune_set(7, sem.SEM_F32, sem.SEM_AX_OTF_SCALE, 1) == sem.SEM_ERR_ARG
+        assert lib.sem_autotune_set(7, sem.SEM_F32, sem.SEM_AX_OTF, sem.SEM_TENSOR_SHAPE) == sem.SEM_OK
+        assert lib.sem_autotune_set(5, sem.SEM_F32, sem.SEM_AX_OTF, sem.SEM_TENSOR_SHAPE) == sem.SEM_ERR_ARG
+        assert lib.sem_autotune_set(7, sem.SEM_F64, sem.SEM_AX_STORED, sem.SEM_TENSOR_SHAPE) == sem.SEM_ERR_ARG
+        assert lib.sem_autotune_set(0, sem.SEM_F64, sem.SEM_AX_STORED, 0) == sem.SEM_ERR_UNSUPPORTED
+        assert lib.sem_autotune_set(7, sem.SEM_F64, 9, 0) == sem.SEM_ERR_ARG
+    finally:
+        assert lib.sem_autotune_clear() == sem.SEM_OK
+
+
+def test_batch_and_server_config_argument_errors(sem):
+    """The batched solver and the server configuration check their arguments on the host,
+    before any device call."""
+    lib = sem.load_library()
+    opts = sem.sem_cg_default_opts(mixed=2, inner_rtol=0.1)
+    res = (sem.CgResult * 2)()
+    ptrs = (sem.C.c_void_p * 2)(None, None)
+    assert lib.sem_cg_solve_batch(0, ptrs, ptrs, ptrs, sem.C.byref(opts), res, None) == sem.SEM_ERR_ARG
+    assert lib.sem_cg_solve_batch(257, ptrs, ptrs, ptrs, sem.C.byref(opts), res, None) == sem.SEM_ERR_ARG
+    assert lib.sem_cg_solve_batch(1, None, ptrs, ptrs, sem.C.byref(opts), res, None) == sem.SEM_ERR_ARG
+    assert lib.sem_cg_solve_batch(1, ptrs, ptrs, ptrs, sem.C.byref(opts), res, None) == sem.SEM_ERR_ARG  # null mesh
+    cfg = sem.sem_server_default_config(1 << 30, 4)
+    assert cfg.batch_max_points == 2097152 and cfg.batch_round_iters == 20 and cfg.size_priorities == 1
+    out = sem.C.c_void_p()
+    for field, value in (("max_slots", 0), ("max_slots", 257), ("hbm_budget_bytes", 0), ("batch_max_solves", 0),
+                         ("batch_max_solves", 257), ("batch_round_iters", 0), ("batch_max_points", -1)):
+        bad = sem.sem_server_default_config(1 << 30, 4)
+        setattr(bad, field, value)
+        assert lib.sem_server_create_config(sem.C.byref(bad), sem.C.byref(out)) == sem.SEM_ERR_ARG, field
+        assert out.value is None
