@@ -338,11 +338,13 @@ __device__ __forceinline__ void prefetch_factors(double* sG, const double* G, in
 //   2 j-lines of A -> us in place;  3 column: G (ur, us, ut);  4 D^T on rows, lines, column;
 //   5 column: w = sum of the three, converted to FP64 and stored.
 // GK: the factors (kGkF64 / kGkPairs: stored, staged by TMA; kGkOtf: rebuilt from coef).
-// Minimum blocks per SM: four at N = 7 (128 registers; on the fly 0.748 -> 0.707 ms against a
-// minimum of 1); elsewhere on the fly the compiler's default (0), stored 1 (the default took
-// fewer registers there but ran 4% slower at N = 7).
+// Minimum blocks per SM: four at N = 7 in CG mode and for the stored plain kernel (128
+// registers; 0.429 -> 0.414 ms against a minimum of 1); on the fly otherwise the compiler's
+// default (0: 128 registers at N = 7, 0.748 -> 0.707 ms against a minimum of 1); stored
+// otherwise 1 (the default took fewer registers there but ran 4% slower at N = 7).
 template <int NP, bool CG, int GK>
-__global__ void __launch_bounds__(NP * NP * ax_epb<NP>(), NP == 8 ? 4 : GK == kGkOtf ? 0 : 1)
+__global__ void __launch_bounds__(NP * NP * ax_epb<NP>(),
+                                  (NP == 8 && (CG || GK != kGkOtf)) ? 4 : GK == kGkOtf ? 0 : 1)
     k_ax_df(const __grid_constant__ DfTab<NP> tab, int64_t E, const double* __restrict__ u, double* __restrict__ w,
             const double* __restrict__ G, const double* __restrict__ coef, const double* __restrict__ r,
             double* __restrict__ p,
